@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Lax-Wendroff Teukolsky stepper: grid-point updates per second.
+
+One benchmark step is one outer time step dt = 0.25 dr* of the double-double workload
+(M = 1, a = 0.9, s = -2, m = 2, r* in [-100, 400] x 2048 nodes, theta x 128 cells), i.e.
+88 Lax-Wendroff iterations (Eqs. lw1, lw2 of arXiv:1006.0663) plus the waveform sample at
+r* = 300. A grid-point update is one point advanced by one Lax-Wendroff iteration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload (the problem
+does not shard across GPUs here), value = all ranks' updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/sec (FP64, dd, qd) & % of FP64/HBM roofline at stated error"
+UNIT = "grid-point updates/s"
+WORKLOAD = "c2"
+
+# FP64 pipe operations (add, mul and fma count one each) per grid point for one launch of
+# each kernel, from the operation list of the scheme in each arithmetic ("Work
+# per point"). half = Eq. lw1 kernel, full = Eq. lw2 kernel.
+OPS_HALF = {1: 52, 2: 512, 4: 7632}
+OPS_FULL = {1: 50, 2: 508, 4: 7620}
+# Algorithmic DRAM bytes per grid point per launch: state rows read once, half rows written
+# once (half kernel) / read once and state written once (full kernel), 8 folded coefficients.
+BYTES_HALF = {w: (4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
+BYTES_FULL = {w: (4 + 4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
+DTYPE = {1: "f64", 2: "f64x2 (double-double)", 4: "f64x4 (quad-double)"}
+TOL = {1: 1e-12, 2: 1e-26, 4: 1e-55}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP64 / qd side figures")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+def start_clock_sampler():
+    path = os.path.join(tempfile.gettempdir(), f"teuk_clocks_{os.getpid()}.csv")
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                              "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+        return p, f, path
+    except Exception:
+        return None, None, path
+
+
+def stop_clock_sampler(p, f, path, device_index):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(device_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax = float(parts[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    os.unlink(path)
+    sm.sort()
+    med = sm[len(sm) // 2] if sm else None
+    return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=True):
+    """Device-resident timing of `steps` outer steps; returns a dict of measurements."""
+    g = teuk.Teuk.from_problem(prob, precision=words)
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    g.set_observer(prob.rstar_obs, capacity=steps + warmup + 1)
+    for _ in range(warmup):
+        g.step(1)
+    g.sync()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    launches0 = g.kernel_launches
+    if with_timing:
+        g.timing(True)
+    torch.cuda.synchronize()
+    for t in range(steps):
+        flush.zero_()  # L2 flush between timed steps (outside the timed interval)
+        evs[t][0].record(stream)
+        g.step(1)
+        evs[t][1].record(stream)
+    torch.cuda.synchronize()
+    g.sync()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    kt = g.kernel_times() if with_timing else (0, 0, 0, 0)
+    out = dict(ms_total=sum(ms), ms=ms, launches=g.kernel_launches - launches0, kernel_times=kt,
+               points=prob.n_r * prob.n_theta, substeps=prob.substeps)
+    wf = g.read_waveform()
+    out["waveform_samples"] = int(wf.shape[0])
+    g.close()
+    return out
+
+
+def run_e2e(prob, words, steps, torch, teuk):
+    """Through the public API with host buffers: per step H2D of the state from pinned host
+    memory, one outer step, D2H of the observer row."""
+    import numpy as np
+    g = teuk.Teuk.from_problem(prob, precision=words)
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    state = g.get_state()
+    pinned = torch.empty(state.shape, dtype=torch.float64, pin_memory=True)
+    host = pinned.numpy()
+    host[...] = state
+    g.step(1)  # warm-up
+    g.observe(prob.rstar_obs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.set_state(host)
+        g.step(1)
+        obs, _ = g.observe(prob.rstar_obs)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    g.close()
+    upd = prob.n_r * prob.n_theta * prob.substeps * steps
+    return dict(value=upd / dt, unit=UNIT, h2d_bytes_per_step=int(state.nbytes),
+                d2h_bytes_per_step=int(obs.nbytes))
+
+
+def cpu_baseline(prob, words, seconds_target=15.0):
+    """The oracle (256-bit MPFR for dd/qd workloads, FP64 for FP64) on all host cores, on a
+    window of rows of the same workload for a bounded number of iterations."""
+    import oracle
+    oracle.build()
+    bits = 53 if words == 1 else 256
+    rows = 24 if words > 1 else 512
+    ic = int(round((prob.center - prob.rstar_min) / prob.dr))
+    lo = max(0, ic - rows // 2)
+    o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
+                      rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=prob.dt,
+                      substeps=prob.substeps, parity=prob.parity, row_lo=lo,
+                      row_hi=min(prob.n_r - 1, lo + rows - 1), bits=bits)
+    ar, ai = prob.amps
+    o.pulse(prob.center, prob.width, ar, ai, prob.ell)
+    done, t0 = 0, time.perf_counter()
+    n = 1
+    while time.perf_counter() - t0 < seconds_target:
+        o.step(n)
+        done += n
+        n = min(n * 2, 64)
+    dt = time.perf_counter() - t0
+    upd = o.nrow * prob.n_theta * done
+    return dict(value=upd / dt, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
+                sample=f"{o.nrow} r* rows x {prob.n_theta} theta of {prob.name}, {done} "
+                       f"Lax-Wendroff iterations, {bits}-bit oracle, {dt:.1f} s")
+
+
+# ---------------------------------------------------------------------------------------------
+def reference_arm(args):
+    from paper_1006_0663_gb300 import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob = workloads.CONFIGS[WORKLOAD]
+    per_step_s = 4.0
+    # warm-up and K timed steps, each a bounded sample of the workload
+    for _ in range(args.warmup):
+        cpu_baseline(prob, prob.words, seconds_target=0.5)
+    vals = [cpu_baseline(prob, prob.words, seconds_target=per_step_s) for _ in range(args.steps)]
+    tot_upd = sum(v["value"] * per_step_s for v in vals)
+    value = sum(v["value"] for v in vals) / len(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[prob.words], "data": "synthetic",
+        "config": {"workload": describe(prob)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": f"{tot_upd:.3g} updates timed",
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def describe(prob):
+    return (f"{prob.name}: {DTYPE[prob.words]}, M={prob.M}, a={prob.a}, s={prob.s}, m={prob.m}, "
+            f"r* in [{prob.rstar_min}, {prob.rstar_max}] x {prob.n_r} nodes, theta x {prob.n_theta} "
+            f"cells, 10th-order theta, dt=0.25 dr* with {prob.substeps} Lax-Wendroff iterations "
+            f"per step, Gaussian pulse (center {prob.center}, width {prob.width}, seed "
+            f"{prob.seed}), waveform at r*={prob.rstar_obs} every step")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1006_0663_gb300 import teuk, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prob = workloads.CONFIGS[WORKLOAD]
+    W = prob.words
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = start_clock_sampler()
+    res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush)
+    clocks = stop_clock_sampler(*sampler, device_index=local)
+    torch.cuda.synchronize()
+    t_local = res["ms_total"]
+    if world > 1:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    else:
+        t_max = t_local
+    updates_per_rank = res["points"] * res["substeps"] * args.steps
+    value = world * updates_per_rank / (t_max * 1e-3)
+
+    out = None
+    if rank == 0:
+        ms_h, ms_f, n_h, n_f = res["kernel_times"]
+        pts_h = (prob.n_r - 1) * prob.n_theta
+        pts_f = (prob.n_r - 2) * prob.n_theta
+        avg_h = ms_h / max(n_h, 1)
+        avg_f = ms_f / max(n_f, 1)
+        dom = "half" if ms_h >= ms_f else "full"
+        ops = (OPS_HALF[W] * pts_h if dom == "half" else OPS_FULL[W] * pts_f)
+        avg = avg_h if dom == "half" else avg_f
+        peak = teuk.fp64_peak()
+        achieved = ops / (avg * 1e-3)
+        traffic_note = None
+        roofline = {
+            "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": f"{dom}_kernel<{W}>", "avg_launch_ms": avg,
+            "ops_per_point": OPS_HALF[W] if dom == "half" else OPS_FULL[W],
+            "peak_source": "measured in this run: FP64 FMA chain on every SM (teuk_fp64_peak)",
+            "op_unit": "FP64 pipe operations (add, mul, fma count one each)",
+            "hbm_achieved_gbs": (BYTES_HALF[W] * pts_h if dom == "half" else BYTES_FULL[W] * pts_f)
+            / (avg * 1e-3) / 1e9,
+            "fraction_of_step_in_dominant_kernel": (ms_h if dom == "half" else ms_f)
+            / max(res["ms_total"], 1e-9),
+        }
+        e2e = run_e2e(prob, W, max(3, args.steps // 2), torch, teuk)
+        variants = {}
+        if not args.no_variants:
+            for name, w in (("c1", 1), ("c5", 1), ("c3", 4), ("c5", 2)):
+                p = workloads.CONFIGS[name]
+                r = run_workload(p, w, 2, 1, torch, teuk, flush, with_timing=False)
+                variants[f"{name}/{DTYPE[w].split(' ')[0]}"] = {
+                    "updates_per_s": p.n_r * p.n_theta * p.substeps * 2 / (r["ms_total"] * 1e-3),
+                    "ms_per_step": r["ms_total"] / 2}
+        cpu = None if args.no_cpu else cpu_baseline(prob, W)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[W], "data": "synthetic",
+            "config": {"workload": describe(prob),
+                       "l2": "256 MiB buffer written between timed steps (outside the timed "
+                             "interval); the 100 MB working set is L2-resident within a step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": res["launches"],
+            "clocks": clocks,
+            "per_precision": variants,
+            "tolerance_vs_256bit_oracle": TOL[W],
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,140 @@
+/* teuk.h -- C ABI of the GB300 Lax-Wendroff Teukolsky stepper.
+ *
+ * One handle holds one problem: a spin-weight-s, azimuthal-m perturbation of a Kerr black
+ * hole (mass M, spin a) on an (r*, theta) grid, evolved by the two-step Lax-Wendroff
+ * scheme of Ginjupalli & Khanna, "High-Precision Numerical Simulations of Rotating Black
+ * Holes Accelerated by CUDA" (arXiv:1006.0663): the Teukolsky equation (Eq. 1) reduced with
+ * Psi = e^{i m phi~} r^3 Phi (Eq. psiphi) to the first-order system u_t + D u_{r*} = S for
+ * u = {Phi_R, Phi_I, Pi_R, Pi_I} (Sec. 3.B, Eqs. new_teu2, d_matrix), advanced by Eqs. lw1
+ * and lw2, with 10th-order centred theta differences (Sec. 3.D), Phi = Pi = 0 on the r*
+ * boundaries and axis parity conditions (Sec. 3.B). Arithmetic is FP64, double-double or
+ * quad-double (Sec. 3.D "double, quadruple and octal precision").
+ *
+ * Conventions
+ *  - Every call returns 0 on success or a negative TEUK_ERR_* code; teuk_strerror() gives
+ *    a message, teuk_last_error() the detail of the last failure on a handle.
+ *  - Host buffers are owned by the caller and are only read or written during the call
+ *    (the call synchronises the handle's stream before returning host data).
+ *  - Multi-word values are passed as word planes: a real in precision p (words w = p) is the
+ *    exact sum of w doubles, stored plane by plane. A field array [C][w][n_r][n_theta] holds
+ *    component c, word k, row i, column j at ((c*w + k)*n_r + i)*n_theta + j; the components
+ *    of the state are Phi_R, Phi_I, Pi_R, Pi_I.
+ *  - All double parameters are taken as exact binary values in every precision.
+ *  - A handle is not thread-safe; all its work is queued on its CUDA stream in order.
+ *  - No call uses more than the one CUDA device that is current when the handle is created.
+ */
+#ifndef TEUK_H
+#define TEUK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { TEUK_FP64 = 1, TEUK_DD = 2, TEUK_QD = 4 } teuk_precision; /* = words per real */
+
+enum {
+  TEUK_OK = 0,
+  TEUK_ERR_INVALID_ARG = -1,   /* a parameter is out of range (message in teuk_last_error) */
+  TEUK_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  TEUK_ERR_OOM = -3,           /* device or host allocation failed */
+  TEUK_ERR_NONFINITE = -4,     /* the evolution produced Inf/NaN (instability) */
+  TEUK_ERR_STATE_MISMATCH = -5,/* a state or observer request does not fit this handle */
+  TEUK_ERR_NO_DEVICE = -6      /* no CUDA device is available */
+};
+
+/* Grid and time stepping (Sec. 3.B: r* nodes r*_i = rstar_min + i dr*, i = 0..n_r-1,
+ * dr* = (rstar_max - rstar_min)/(n_r - 1); cell-centred theta_j = (j + 1/2) pi / n_theta).
+ * dt is the outer (sampling) step; each outer step is `substeps` Lax-Wendroff iterations
+ * of dt/substeps (the explicit scheme needs several iterations per dt = 0.25 dr* to stay
+ * stable with 10th-order theta differences near the poles). */
+typedef struct {
+  double rstar_min, rstar_max;
+  int32_t n_r;          /* >= 3 */
+  int32_t n_theta;      /* 6 .. 1024 */
+  double dt;            /* outer step; 0 selects 0.25 dr* */
+  int32_t substeps;     /* >= 1 */
+  int32_t theta_order;  /* 10 (Sec. 3.D, default if 0) or 2 (Sec. 3.B) */
+  int32_t parity;       /* sign of the axis reflection of Phi and Pi: 0 selects (-1)^(m+s);
+                           +1 / -1 explicit (the paper's rule is +1 for even |m|, -1 for odd) */
+  int32_t reserved;     /* must be 0 */
+} teuk_grid;
+
+typedef struct teuk_s* teuk_t;
+
+/* Creates a problem and evaluates its coefficients on the device (tortoise inversion r(r*)
+ * and the system coefficients at every node and half node, in the target precision).
+ * M > 0, |a| < M, stream = a cudaStream_t or NULL for a stream owned by the handle.
+ * Allocates about (4 + 4 + 4*8) * w * n_r * n_theta doubles of device memory. */
+int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* grid,
+                teuk_precision precision, void* cuda_stream);
+int teuk_destroy(teuk_t h);
+
+/* Initial data from host word planes phi_pi[4][w][n_r][n_theta] (copied to the device).
+ * Rows 0 and n_r-1 are set to zero (Sec. 3.B). Resets the step counter. */
+int teuk_set_initial(teuk_t h, const double* phi_pi);
+/* Gaussian pulse Phi = A exp(-((r* - center)/width)^2) sY_{ell m}(theta) with A = amp_re +
+ * i amp_im, zero initial time derivative (Pi = b Phi_{r*}), evaluated on the device in the
+ * target precision; sY is the spin-weighted harmonic without its normalisation constant.
+ * ell >= max(|m|, |s|). */
+int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re, double amp_im,
+                           int ell);
+
+/* Advances n outer steps (n * substeps Lax-Wendroff iterations), asynchronously on the
+ * handle's stream. The observer ring (if any) gets one sample per outer step. */
+int teuk_step(teuk_t h, int64_t n_outer_steps);
+/* Advances n single Lax-Wendroff iterations of dt/substeps (no observer samples). */
+int teuk_substep(teuk_t h, int64_t n_iterations);
+/* Waits for the handle's stream; returns TEUK_ERR_NONFINITE if any Inf/NaN was produced. */
+int teuk_sync(teuk_t h);
+
+/* Phi at the node nearest rstar_obs (ties toward the lower index): out[2][w][n_theta]. */
+int teuk_observe(teuk_t h, double rstar_obs, double* out_phi, double* rstar_used);
+/* Records Phi(i_obs, .) after every outer step into a device ring of `capacity` samples. */
+int teuk_set_observer(teuk_t h, double rstar_obs, int64_t capacity);
+/* Copies the recorded samples, oldest first: out[n][2][w][n_theta], n = min(recorded,
+ * capacity) returned in *n_samples. out may be NULL to query n only. */
+int teuk_read_waveform(teuk_t h, double* out, int64_t* n_samples);
+
+/* Whole state as host word planes [4][w][n_r][n_theta], and the substep counter. */
+int teuk_get_state(teuk_t h, double* planes, int64_t* substeps_done);
+int teuk_set_state(teuk_t h, const double* planes, int64_t substeps_done);
+/* Same, device to device (a caller-owned device buffer of the same layout). */
+int teuk_get_state_device(teuk_t h, double* dev_planes);
+
+/* The raw system coefficients (b, c_R, c_I, Re B/S^2, Im B/S^2, Delta/S^2, Re V/S^2,
+ * Im V/S^2) at nodes (which = 0, [8][w][n_r][n_theta]) or half nodes (which = 1,
+ * [8][w][n_r-1][n_theta]), and the grid tables x = r - r+ at nodes / half nodes ([w][rows]). */
+int teuk_get_coeffs(teuk_t h, int which, double* out);
+int teuk_get_tortoise(teuk_t h, int which, double* x_out);
+
+/* Sizes: words per real, rows, columns, substeps, outer dt (rounded to double). */
+int teuk_info(teuk_t h, int* words, int* n_r, int* n_theta, int* substeps, double* dt_outer);
+
+/* Number of step kernels launched by this handle so far (two per Lax-Wendroff iteration). */
+int64_t teuk_kernel_launches(teuk_t h);
+
+/* Per-kernel timing with CUDA events on the handle's stream: enable = 1 starts recording
+ * the duration of every half-step and full-step launch; teuk_kernel_times() waits for the
+ * stream and returns (and clears) the summed milliseconds and launch counts. */
+int teuk_timing(teuk_t h, int enable);
+int teuk_kernel_times(teuk_t h, double* ms_half, double* ms_full, int64_t* n_half, int64_t* n_full);
+
+/* Measured FP64 pipe throughput of the current device (a chain of independent FMAs on every
+ * SM): operations per second, counting one per FMA. */
+int teuk_fp64_peak(double* ops_per_second);
+
+const char* teuk_strerror(int code);
+const char* teuk_last_error(teuk_t h);
+
+/* Multi-word arithmetic self-test: applies op (0 add, 1 sub, 2 mul, 3 div, 4 sqrt, 5 exp,
+ * 6 log, 7 dot-accumulate a*b + out) elementwise to n values of precision w, on the host
+ * (device = 0) or the current CUDA device (device = 1). a, b, out: [w][n] host arrays. */
+int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out,
+                 int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

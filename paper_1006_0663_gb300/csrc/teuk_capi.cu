@@ -1,0 +1,441 @@
+// C ABI of the teuk library (include/teuk.h): argument checking, device memory, the
+// per-outer-step launch sequence and host <-> device transfers.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "teuk_internal.h"
+
+namespace {
+
+int dispatch_setup(teuk_s* h) {
+  switch (h->W) {
+    case 1: return teuk::setup_w1(h);
+    case 2: return teuk::setup_w2(h);
+    default: return teuk::setup_w4(h);
+  }
+}
+int dispatch_substep(teuk_s* h, bool record, int64_t slot) {
+  switch (h->W) {
+    case 1: return teuk::substep_w1(h, record, slot);
+    case 2: return teuk::substep_w2(h, record, slot);
+    default: return teuk::substep_w4(h, record, slot);
+  }
+}
+
+int invalid(teuk_s* h, const char* msg) {
+  if (h) h->last_error = msg;
+  return TEUK_ERR_INVALID_ARG;
+}
+
+void free_all(teuk_s* h) {
+  double** bufs[] = {&h->u, &h->uh, &h->cn_raw, &h->ch_raw, &h->cn, &h->ch, &h->wts, &h->sin_th,
+                     &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring};
+  for (double** b : bufs) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  if (h->status) cudaFree(h->status);
+  h->status = nullptr;
+}
+
+// Copies a [C][W][rows][n_th] host array to / from the pitched device layout.
+int copy_planes(teuk_s* h, double* dev, const double* host_in, double* host_out, int comps, int rows) {
+  const size_t planes = (size_t)comps * h->W;
+  const size_t dpitch = (size_t)h->pitch * sizeof(double), hpitch = (size_t)h->n_th * sizeof(double);
+  const size_t height = planes * rows;
+  if (host_in) {
+    TEUK_CUDA(h, cudaMemcpy2DAsync(dev, dpitch, host_in, hpitch, hpitch, height, cudaMemcpyHostToDevice,
+                                   h->stream));
+  } else {
+    TEUK_CUDA(h, cudaMemcpy2DAsync(host_out, hpitch, dev, dpitch, hpitch, height, cudaMemcpyDeviceToHost,
+                                   h->stream));
+  }
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+int observer_row(const teuk_s* h, double rstar_obs) {
+  // nearest node, ties toward the lower index, computed in FP64
+  const double q = (rstar_obs - h->rsmin_d) / h->dr_d;
+  int i = (int)std::ceil(q - 0.5);
+  if (i < 0) i = 0;
+  if (i > h->n_r - 1) i = h->n_r - 1;
+  return i;
+}
+
+__global__ void fp64_peak_kernel(double* out, double a, double b, int iters) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int it = 0; it < iters; ++it) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+void drain_timing(teuk_s* h) {
+  if (h->pending.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& p : h->pending) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      h->ms[p.kind] += t;
+      h->n_timed[p.kind] += 1;
+    }
+    h->free_events.push_back(p.a);
+    h->free_events.push_back(p.b);
+  }
+  h->pending.clear();
+}
+
+}  // namespace
+
+namespace teuk {
+cudaEvent_t take_event(teuk_s* h) {
+  if (!h->free_events.empty()) {
+    cudaEvent_t e = h->free_events.back();
+    h->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+void time_begin(teuk_s* h, cudaEvent_t* a) {
+  if (!h->timing) return;
+  *a = take_event(h);
+  cudaEventRecord(*a, h->stream);
+}
+void time_end(teuk_s* h, int kind, cudaEvent_t a) {
+  if (!h->timing || !a) return;
+  cudaEvent_t b = take_event(h);
+  cudaEventRecord(b, h->stream);
+  h->pending.push_back(teuk_s::EvPair{kind, a, b});
+  if (h->pending.size() > 4096) drain_timing(h);
+}
+}  // namespace teuk
+
+extern "C" {
+
+const char* teuk_strerror(int code) {
+  switch (code) {
+    case TEUK_OK: return "ok";
+    case TEUK_ERR_INVALID_ARG: return "invalid argument";
+    case TEUK_ERR_CUDA: return "CUDA runtime error";
+    case TEUK_ERR_OOM: return "out of memory";
+    case TEUK_ERR_NONFINITE: return "non-finite value in the evolution";
+    case TEUK_ERR_STATE_MISMATCH: return "state does not match the handle";
+    case TEUK_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown error";
+  }
+}
+
+const char* teuk_last_error(teuk_t h) { return h ? h->last_error.c_str() : ""; }
+
+int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* grid,
+                teuk_precision precision, void* cuda_stream) {
+  if (!out || !grid) return TEUK_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int W = (int)precision;
+  if (W != 1 && W != 2 && W != 4) return TEUK_ERR_INVALID_ARG;
+  if (!(M > 0) || !(std::fabs(a) < M) || !std::isfinite(M) || !std::isfinite(a)) return TEUK_ERR_INVALID_ARG;
+  if (s < -2 || s > 2) return TEUK_ERR_INVALID_ARG;
+  const teuk_grid& g = *grid;
+  if (g.n_r < 3 || g.n_theta < 6 || g.n_theta > 1024 || g.substeps < 1 || g.reserved != 0)
+    return TEUK_ERR_INVALID_ARG;
+  if (!(g.rstar_max > g.rstar_min) || !std::isfinite(g.rstar_min) || !std::isfinite(g.rstar_max))
+    return TEUK_ERR_INVALID_ARG;
+  if (g.dt < 0 || !std::isfinite(g.dt)) return TEUK_ERR_INVALID_ARG;
+  const int order = g.theta_order == 0 ? 10 : g.theta_order;
+  if (order != 10 && order != 2) return TEUK_ERR_INVALID_ARG;
+  if (g.parity != 0 && g.parity != 1 && g.parity != -1) return TEUK_ERR_INVALID_ARG;
+  if ((int64_t)g.n_r * g.n_theta > (int64_t)1 << 31) return TEUK_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TEUK_ERR_NO_DEVICE;
+
+  teuk_s* h = new (std::nothrow) teuk_s;
+  if (!h) return TEUK_ERR_OOM;
+  h->M = M;
+  h->a = a;
+  h->s = s;
+  h->m = m;
+  h->grid = g;
+  h->W = W;
+  h->n_r = g.n_r;
+  h->n_th = g.n_theta;
+  h->pitch = ((g.n_theta + 15) / 16) * 16;
+  h->parity = g.parity != 0 ? g.parity : (((m + s) % 2 == 0) ? 1 : -1);
+  h->radius = order == 10 ? 5 : 1;
+  h->k = g.substeps;
+  cudaGetDevice(&h->device);
+  int rc = TEUK_OK;
+  auto fail = [&](int code) {
+    free_all(h);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return code;
+  };
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(TEUK_ERR_CUDA);
+    h->own_stream = true;
+  }
+  const size_t P = h->pitch, nr = h->n_r, nh = h->n_r - 1;
+  struct Alloc { double** p; size_t n; } allocs[] = {
+      {&h->u, 4 * W * nr * P},      {&h->uh, 4 * W * nh * P},     {&h->cn_raw, 8 * W * nr * P},
+      {&h->ch_raw, 8 * W * nh * P}, {&h->cn, 8 * W * nr * P},     {&h->ch, 8 * W * nh * P},
+      {&h->wts, (size_t)(2 * h->radius + 1) * W * h->n_th},     {&h->sin_th, (size_t)W * h->n_th},
+      {&h->cos_th, (size_t)W * h->n_th}, {&h->x_node, W * nr},  {&h->x_half, W * nh},
+      {&h->rs_node, W * nr},        {&h->prof, (size_t)W * h->n_th}};
+  for (auto& al : allocs) {
+    if (cudaMalloc(al.p, al.n * sizeof(double)) != cudaSuccess) return fail(TEUK_ERR_OOM);
+    if (cudaMemsetAsync(*al.p, 0, al.n * sizeof(double), h->stream) != cudaSuccess) return fail(TEUK_ERR_CUDA);
+  }
+  if (cudaMalloc(&h->status, sizeof(unsigned int)) != cudaSuccess) return fail(TEUK_ERR_OOM);
+  cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream);
+  rc = dispatch_setup(h);
+  if (rc != TEUK_OK) return fail(rc);
+  *out = h;
+  return TEUK_OK;
+}
+
+int teuk_destroy(teuk_t h) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  drain_timing(h);
+  for (cudaEvent_t e : h->free_events) cudaEventDestroy(e);
+  h->free_events.clear();
+  free_all(h);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return TEUK_OK;
+}
+
+int teuk_info(teuk_t h, int* words, int* n_r, int* n_theta, int* substeps, double* dt_outer) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (words) *words = h->W;
+  if (n_r) *n_r = h->n_r;
+  if (n_theta) *n_theta = h->n_th;
+  if (substeps) *substeps = h->k;
+  if (dt_outer) *dt_outer = h->dt_outer;
+  return TEUK_OK;
+}
+
+int64_t teuk_kernel_launches(teuk_t h) { return h ? h->launches : -1; }
+
+int teuk_set_initial(teuk_t h, const double* phi_pi) {
+  if (!h || !phi_pi) return invalid(h, "null argument");
+  int rc = copy_planes(h, h->u, phi_pi, nullptr, 4, h->n_r);
+  if (rc) return rc;
+  // Phi = Pi = 0 on the r* boundary rows (Sec. 3.B)
+  const size_t ws = (size_t)h->n_r * h->pitch;
+  for (int p = 0; p < 4 * h->W; ++p) {
+    TEUK_CUDA(h, cudaMemsetAsync(h->u + p * ws, 0, h->pitch * sizeof(double), h->stream));
+    TEUK_CUDA(h, cudaMemsetAsync(h->u + p * ws + (size_t)(h->n_r - 1) * h->pitch, 0, h->pitch * sizeof(double),
+                                 h->stream));
+  }
+  h->substeps_done = 0;
+  h->n_recorded = 0;
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re, double amp_im, int ell) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (ell < std::abs(h->m) || ell < std::abs(h->s) || !(width > 0) || !std::isfinite(center))
+    return invalid(h, "pulse: need ell >= max(|m|, |s|), width > 0");
+  int rc;
+  switch (h->W) {
+    case 1: rc = teuk::pulse_w1(h, center, width, amp_re, amp_im, ell); break;
+    case 2: rc = teuk::pulse_w2(h, center, width, amp_re, amp_im, ell); break;
+    default: rc = teuk::pulse_w4(h, center, width, amp_re, amp_im, ell); break;
+  }
+  h->substeps_done = 0;
+  h->n_recorded = 0;
+  return rc;
+}
+
+int teuk_substep(teuk_t h, int64_t n) {
+  if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
+  for (int64_t t = 0; t < n; ++t) {
+    int rc = dispatch_substep(h, false, 0);
+    if (rc) return rc;
+    ++h->substeps_done;
+  }
+  return TEUK_OK;
+}
+
+int teuk_step(teuk_t h, int64_t n) {
+  if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
+  for (int64_t t = 0; t < n; ++t) {
+    for (int q = 0; q < h->k; ++q) {
+      const bool last = q == h->k - 1;
+      const bool record = last && h->ring != nullptr;
+      const int64_t slot = record ? h->n_recorded % h->ring_cap : 0;
+      int rc = dispatch_substep(h, record, slot);
+      if (rc) return rc;
+      ++h->substeps_done;
+    }
+    if (h->ring) ++h->n_recorded;
+  }
+  return TEUK_OK;
+}
+
+int teuk_sync(teuk_t h) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  unsigned int st = 0;
+  TEUK_CUDA(h, cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st & 1u) {
+    h->last_error = "non-finite value produced by the Lax-Wendroff step";
+    return TEUK_ERR_NONFINITE;
+  }
+  return TEUK_OK;
+}
+
+int teuk_observe(teuk_t h, double rstar_obs, double* out_phi, double* rstar_used) {
+  if (!h || !out_phi || !std::isfinite(rstar_obs)) return TEUK_ERR_INVALID_ARG;
+  const int i = observer_row(h, rstar_obs);
+  const size_t ws = (size_t)h->n_r * h->pitch;
+  for (int p = 0; p < 2 * h->W; ++p)
+    TEUK_CUDA(h, cudaMemcpyAsync(out_phi + (size_t)p * h->n_th, h->u + p * ws + (size_t)i * h->pitch,
+                                 h->n_th * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (rstar_used) *rstar_used = h->rsmin_d + i * h->dr_d;
+  return TEUK_OK;
+}
+
+int teuk_set_observer(teuk_t h, double rstar_obs, int64_t capacity) {
+  if (!h || capacity < 1 || !std::isfinite(rstar_obs)) return TEUK_ERR_INVALID_ARG;
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->ring) cudaFree(h->ring);
+  h->ring = nullptr;
+  const size_t n = (size_t)capacity * 2 * h->W * h->n_th;
+  TEUK_CUDA(h, cudaMalloc(&h->ring, n * sizeof(double)));
+  TEUK_CUDA(h, cudaMemsetAsync(h->ring, 0, n * sizeof(double), h->stream));
+  h->ring_cap = capacity;
+  h->i_obs = observer_row(h, rstar_obs);
+  h->n_recorded = 0;
+  return TEUK_OK;
+}
+
+int teuk_read_waveform(teuk_t h, double* out, int64_t* n_samples) {
+  if (!h || !n_samples) return TEUK_ERR_INVALID_ARG;
+  if (!h->ring) return TEUK_ERR_STATE_MISMATCH;
+  const int64_t n = h->n_recorded < h->ring_cap ? h->n_recorded : h->ring_cap;
+  *n_samples = n;
+  if (!out || n == 0) return TEUK_OK;
+  const size_t per = (size_t)2 * h->W * h->n_th;
+  const int64_t first = h->n_recorded - n;  // oldest sample kept
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t slot = (first + t) % h->ring_cap;
+    TEUK_CUDA(h, cudaMemcpyAsync(out + t * per, h->ring + slot * per, per * sizeof(double),
+                                 cudaMemcpyDeviceToHost, h->stream));
+  }
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+int teuk_get_state(teuk_t h, double* planes, int64_t* substeps_done) {
+  if (!h || !planes) return TEUK_ERR_INVALID_ARG;
+  int rc = copy_planes(h, h->u, nullptr, planes, 4, h->n_r);
+  if (substeps_done) *substeps_done = h->substeps_done;
+  return rc;
+}
+
+int teuk_set_state(teuk_t h, const double* planes, int64_t substeps_done) {
+  if (!h || !planes || substeps_done < 0) return TEUK_ERR_INVALID_ARG;
+  int rc = copy_planes(h, h->u, planes, nullptr, 4, h->n_r);
+  if (rc) return rc;
+  h->substeps_done = substeps_done;
+  return TEUK_OK;
+}
+
+int teuk_get_state_device(teuk_t h, double* dev_planes) {
+  if (!h || !dev_planes) return TEUK_ERR_INVALID_ARG;
+  const size_t dpitch = (size_t)h->pitch * sizeof(double), hpitch = (size_t)h->n_th * sizeof(double);
+  TEUK_CUDA(h, cudaMemcpy2DAsync(dev_planes, hpitch, h->u, dpitch, hpitch, (size_t)4 * h->W * h->n_r,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+  return TEUK_OK;
+}
+
+int teuk_get_coeffs(teuk_t h, int which, double* out) {
+  if (!h || !out || (which != 0 && which != 1)) return TEUK_ERR_INVALID_ARG;
+  return copy_planes(h, which ? h->ch_raw : h->cn_raw, nullptr, out, 8, which ? h->n_r - 1 : h->n_r);
+}
+
+int teuk_get_tortoise(teuk_t h, int which, double* x_out) {
+  if (!h || !x_out || (which != 0 && which != 1)) return TEUK_ERR_INVALID_ARG;
+  const size_t rows = which ? h->n_r - 1 : h->n_r;
+  TEUK_CUDA(h, cudaMemcpyAsync(x_out, which ? h->x_half : h->x_node, rows * h->W * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+int teuk_timing(teuk_t h, int enable) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  drain_timing(h);
+  h->timing = enable != 0;
+  h->ms[0] = h->ms[1] = 0;
+  h->n_timed[0] = h->n_timed[1] = 0;
+  return TEUK_OK;
+}
+
+int teuk_kernel_times(teuk_t h, double* ms_half, double* ms_full, int64_t* n_half, int64_t* n_full) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  drain_timing(h);
+  if (ms_half) *ms_half = h->ms[0];
+  if (ms_full) *ms_full = h->ms[1];
+  if (n_half) *n_half = h->n_timed[0];
+  if (n_full) *n_full = h->n_timed[1];
+  h->ms[0] = h->ms[1] = 0;
+  h->n_timed[0] = h->n_timed[1] = 0;
+  return TEUK_OK;
+}
+
+int teuk_fp64_peak(double* ops_per_second) {
+  if (!ops_per_second) return TEUK_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TEUK_ERR_NO_DEVICE;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = sms * 8, iters = 4096;
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, (size_t)threads * blocks * sizeof(double)) != cudaSuccess) return TEUK_ERR_OOM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    fp64_peak_kernel<<<blocks, threads>>>(buf, 0.999999, 1e-7, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (err != cudaSuccess) return TEUK_ERR_CUDA;
+  *ops_per_second = (double)threads * blocks * iters * 8 / (best * 1e-3);
+  return TEUK_OK;
+}
+
+int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out, int64_t n) {
+  if (!a || !b || !out || n < 0 || op < 0 || op > 7) return TEUK_ERR_INVALID_ARG;
+  switch (words) {
+    case 1: return teuk::mw_eval_w1(op, device, a, b, out, n);
+    case 2: return teuk::mw_eval_w2(op, device, a, b, out, n);
+    case 4: return teuk::mw_eval_w4(op, device, a, b, out, n);
+    default: return TEUK_ERR_INVALID_ARG;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal state of a teuk handle, shared by the C ABI layer and the per-precision units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/teuk.h"
+
+struct teuk_s {
+  // problem (Sec. 3.A-3.B)
+  double M = 1, a = 0;
+  int s = 0, m = 0;
+  teuk_grid grid{};
+  int W = 1;            // words per real
+  int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;
+  double dt_outer = 0;  // leading word of the outer step
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // device buffers
+  double* u = nullptr;       // [4][W][n_r][pitch]
+  double* uh = nullptr;      // [4][W][n_r-1][pitch]   half-step scratch
+  double* cn_raw = nullptr;  // [8][W][n_r][pitch]
+  double* ch_raw = nullptr;  // [8][W][n_r-1][pitch]
+  double* cn = nullptr;      // folded node tables
+  double* ch = nullptr;      // folded half tables
+  double* wts = nullptr;     // [2*radius+1][W][n_th]
+  double* sin_th = nullptr;  // [W][n_th]
+  double* cos_th = nullptr;  // [W][n_th]
+  double* x_node = nullptr;  // [W][n_r]
+  double* x_half = nullptr;  // [W][n_r-1]
+  double* rs_node = nullptr; // [W][n_r]
+  double* prof = nullptr;    // [W][n_th]
+  unsigned int* status = nullptr;
+  // observer ring
+  int i_obs = -1;
+  int64_t ring_cap = 0;
+  double* ring = nullptr;    // [cap][2][W][n_th]
+  int64_t n_recorded = 0;
+  // per-kernel event timing (kind 0 = half step, 1 = full step)
+  bool timing = false;
+  struct EvPair { int kind; cudaEvent_t a, b; };
+  std::vector<EvPair> pending;
+  std::vector<cudaEvent_t> free_events;
+  double ms[2] = {0, 0};
+  int64_t n_timed[2] = {0, 0};
+  // counters
+  int64_t substeps_done = 0;
+  int64_t launches = 0;
+  // target-precision scalars kept as words
+  double h4_w[4] = {0, 0, 0, 0}, h2_w[4] = {0, 0, 0, 0}, ln2_w[4] = {0, 0, 0, 0};
+  double dr_d = 0, rsmin_d = 0;
+  std::string last_error;
+};
+
+namespace teuk {
+// per-precision entry points (teuk_prec.cu compiled with TEUK_WORDS = 1, 2, 4)
+int setup_w1(teuk_s* h);
+int setup_w2(teuk_s* h);
+int setup_w4(teuk_s* h);
+int pulse_w1(teuk_s* h, double center, double width, double ar, double ai, int ell);
+int pulse_w2(teuk_s* h, double center, double width, double ar, double ai, int ell);
+int pulse_w4(teuk_s* h, double center, double width, double ar, double ai, int ell);
+int substep_w1(teuk_s* h, bool record, int64_t slot);
+int substep_w2(teuk_s* h, bool record, int64_t slot);
+int substep_w4(teuk_s* h, bool record, int64_t slot);
+int mw_eval_w1(int op, int device, const double* a, const double* b, double* out, int64_t n);
+int mw_eval_w2(int op, int device, const double* a, const double* b, double* out, int64_t n);
+int mw_eval_w4(int op, int device, const double* a, const double* b, double* out, int64_t n);
+
+// Event pair around one launch when timing is on (records nothing otherwise).
+cudaEvent_t take_event(teuk_s* h);
+void time_begin(teuk_s* h, cudaEvent_t* a);
+void time_end(teuk_s* h, int kind, cudaEvent_t a);
+
+inline int cuda_fail(teuk_s* h, cudaError_t e, const char* what) {
+  if (h) h->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? TEUK_ERR_OOM : TEUK_ERR_CUDA;
+}
+}  // namespace teuk
+
+#define TEUK_CUDA(h, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return teuk::cuda_fail(h, e_, #call); \
+  } while (0)

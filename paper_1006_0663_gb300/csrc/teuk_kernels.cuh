@@ -1,0 +1,528 @@
+// Device kernels of the Lax-Wendroff Teukolsky step (arXiv:1006.0663, Sec. 3.B-3.D), one
+// template per arithmetic: W = 1 (FP64), 2 (double-double), 4 (quad-double).
+//
+// Data layout in HBM ("SoA word planes"): a field with C components on R rows is stored as
+// [C][W][R][pitch] doubles, theta fastest, pitch = n_theta rounded up to 16 doubles (128 B),
+// so every warp access along theta is one coalesced 128-byte line per word plane.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mw_func.cuh"
+
+namespace teuk {
+
+template <int W> struct RT;
+template <> struct RT<1> { using T = double; };
+template <> struct RT<2> { using T = mw::dd; };
+template <> struct RT<4> { using T = mw::qd; };
+
+// ---- word-plane access -------------------------------------------------------------------
+template <class R> __device__ __forceinline__ R ld_r(const double* __restrict__ p, size_t ws);
+template <> __device__ __forceinline__ double ld_r<double>(const double* __restrict__ p, size_t) {
+  return __ldg(p);
+}
+template <> __device__ __forceinline__ mw::dd ld_r<mw::dd>(const double* __restrict__ p, size_t ws) {
+  return mw::dd{__ldg(p), __ldg(p + ws)};
+}
+template <> __device__ __forceinline__ mw::qd ld_r<mw::qd>(const double* __restrict__ p, size_t ws) {
+  return mw::qd{__ldg(p), __ldg(p + ws), __ldg(p + 2 * ws), __ldg(p + 3 * ws)};
+}
+// plain (non-__ldg) loads for buffers written earlier in the same kernel
+template <class R> __device__ __forceinline__ R ld_s(const double* p, size_t ws);
+template <> __device__ __forceinline__ double ld_s<double>(const double* p, size_t) { return p[0]; }
+template <> __device__ __forceinline__ mw::dd ld_s<mw::dd>(const double* p, size_t ws) {
+  return mw::dd{p[0], p[ws]};
+}
+template <> __device__ __forceinline__ mw::qd ld_s<mw::qd>(const double* p, size_t ws) {
+  return mw::qd{p[0], p[ws], p[2 * ws], p[3 * ws]};
+}
+__device__ __forceinline__ void st_r(double* p, size_t, double v) { p[0] = v; }
+__device__ __forceinline__ void st_r(double* p, size_t ws, mw::dd v) { p[0] = v.h; p[ws] = v.l; }
+__device__ __forceinline__ void st_r(double* p, size_t ws, mw::qd v) {
+  p[0] = v.x0; p[ws] = v.x1; p[2 * ws] = v.x2; p[3 * ws] = v.x3;
+}
+template <class R> __host__ __device__ __forceinline__ R from_words(const double* w);
+template <> __host__ __device__ __forceinline__ double from_words<double>(const double* w) { return w[0]; }
+template <> __host__ __device__ __forceinline__ mw::dd from_words<mw::dd>(const double* w) { return mw::dd{w[0], w[1]}; }
+template <> __host__ __device__ __forceinline__ mw::qd from_words<mw::qd>(const double* w) {
+  return mw::qd{w[0], w[1], w[2], w[3]};
+}
+__host__ __device__ __forceinline__ void to_words(double v, double* w) { w[0] = v; w[1] = w[2] = w[3] = 0.0; }
+__host__ __device__ __forceinline__ void to_words(mw::dd v, double* w) { w[0] = v.h; w[1] = v.l; w[2] = w[3] = 0.0; }
+__host__ __device__ __forceinline__ void to_words(mw::qd v, double* w) { w[0] = v.x0; w[1] = v.x1; w[2] = v.x2; w[3] = v.x3; }
+
+// ---- hot-path arithmetic ---------------------------------------------------------------------
+__host__ __device__ __forceinline__ double v_add(double a, double b) { return a + b; }
+__host__ __device__ __forceinline__ double v_sub(double a, double b) { return a - b; }
+__host__ __device__ __forceinline__ double v_half(double a) { return 0.5 * a; }
+__host__ __device__ __forceinline__ double v_neg(double a) { return -a; }
+__host__ __device__ __forceinline__ mw::dd v_add(mw::dd a, mw::dd b) { return mw::dd_add_accurate(a, b); }
+__host__ __device__ __forceinline__ mw::dd v_sub(mw::dd a, mw::dd b) { return mw::dd_add_accurate(a, mw::dd_neg(b)); }
+__host__ __device__ __forceinline__ mw::dd v_half(mw::dd a) { return mw::dd_scale2(a, 0.5); }
+__host__ __device__ __forceinline__ mw::dd v_neg(mw::dd a) { return mw::dd_neg(a); }
+__host__ __device__ __forceinline__ mw::qd v_add(mw::qd a, mw::qd b) { return mw::qd_add(a, b); }
+__host__ __device__ __forceinline__ mw::qd v_sub(mw::qd a, mw::qd b) { return mw::qd_add(a, mw::qd_neg(b)); }
+__host__ __device__ __forceinline__ mw::qd v_half(mw::qd a) { return mw::qd_scale2(a, 0.5); }
+__host__ __device__ __forceinline__ mw::qd v_neg(mw::qd a) { return mw::qd_neg(a); }
+
+// Dot-product accumulators: acc = x0 + sum_k c_k v_k.
+//   FP64: one FMA per term.
+//   dd: Ogita-Rump-Oishi "Dot2" (SIAM J. Sci. Comput. 26, 2005) extended to double-word
+//       operands: each product's leading part is formed exactly by TwoProd, the cross terms
+//       c.h v.l + c.l v.h go into its error, the leading parts are summed by TwoSum and all
+//       errors are gathered in one low-order word; one final TwoSum renormalises.
+//   qd: quad-double multiply-add per term.
+template <class R> struct Acc;
+template <> struct Acc<double> {
+  double s;
+  __host__ __device__ __forceinline__ explicit Acc(double x0) : s(x0) {}
+  __host__ __device__ __forceinline__ void mac(double c, double v) { s = mw::fma_(c, v, s); }
+  __host__ __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<mw::dd> {
+  double s, e;
+  __host__ __device__ __forceinline__ explicit Acc(mw::dd x0) : s(x0.h), e(x0.l) {}
+  __host__ __device__ __forceinline__ void mac(mw::dd c, mw::dd v) {
+    double p, pe, t;
+    mw::two_prod(c.h, v.h, p, pe);
+    pe = mw::fma_(c.h, v.l, pe);
+    pe = mw::fma_(c.l, v.h, pe);
+    mw::two_sum_ord(s, p, s, t);
+    e = mw::add_(e, mw::add_(t, pe));
+  }
+  __host__ __device__ __forceinline__ mw::dd get() const {
+    mw::dd r;
+    mw::two_sum_ord(s, e, r.h, r.l);
+    return r;
+  }
+};
+template <> struct Acc<mw::qd> {
+  mw::qd s;
+  __host__ __device__ __forceinline__ explicit Acc(mw::qd x0) : s(x0) {}
+  __host__ __device__ __forceinline__ void mac(mw::qd c, mw::qd v) { s = mw::qd_add(s, mw::qd_mul(c, v)); }
+  __host__ __device__ __forceinline__ mw::qd get() const { return s; }
+};
+
+// ---- kernel argument blocks ---------------------------------------------------------------
+struct Geom {
+  int n_r, n_th, pitch, parity;
+};
+
+struct SetupArgs {
+  Geom g;
+  int W;
+  double M, a;
+  int s, m;
+  double rp[4], rm[4], tort_A[4], tort_B[4], ln2[4], ln2M[4], rsmin[4], dr[4];
+  double dts[4], lambda[4];  // substep dt and dt/dr
+  const double* sin_th;      // [W][n_th]
+  const double* cos_th;      // [W][n_th]
+  double* x_node;            // [W][n_r]
+  double* x_half;            // [W][n_r-1]
+  double* rs_node;           // [W][n_r]
+  double* cn_raw;            // [8][W][n_r][pitch]
+  double* ch_raw;            // [8][W][n_r-1][pitch]
+  double* cn;                // folded node coefficients
+  double* ch;                // folded half coefficients
+};
+
+// ---- set-up kernels ---------------------------------------------------------------------------
+// Tortoise inversion (Sec. 3.B): r*(x) = r+ + x + A ln(x/2M) + B ln((x + r+ - r-)/2M) with
+// x = r - r+; solved for x at every node and half node by Newton's method in xi = ln x,
+// started from a bisection in double precision.
+template <int W>
+__global__ void tortoise_kernel(SetupArgs a) {
+  using R = typename RT<W>::T;
+  const int n_nodes = a.g.n_r, n_half = a.g.n_r - 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_nodes + n_half) return;
+  const bool half = t >= n_nodes;
+  const int i = half ? t - n_nodes : t;
+  const R rp = from_words<R>(a.rp), rm = from_words<R>(a.rm);
+  const R A = from_words<R>(a.tort_A), B = from_words<R>(a.tort_B);
+  const R ln2 = from_words<R>(a.ln2), ln2M = from_words<R>(a.ln2M);
+  const R dr = from_words<R>(a.dr);
+  const double fi = half ? double(i) + 0.5 : double(i);  // exact
+  const R target = mw::r_add(from_words<R>(a.rsmin), mw::r_mul_d(dr, fi));
+  const R twoM = mw::r_from<R>(2.0 * a.M);
+  // double-precision bracket
+  const double td = mw::lead(target), rpd = mw::lead(rp), rmd = mw::lead(rm);
+  const double Ad = mw::lead(A), Bd = mw::lead(B), l2M = std::log(2.0 * a.M);
+  double lo = -745.0, hi = 45.0;
+  for (int it = 0; it < 120; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double x = exp(mid);
+    const double F = rpd + x + Ad * (mid - l2M) + Bd * log((x + rpd - rmd) / (2.0 * a.M)) - td;
+    if (F < 0) lo = mid; else hi = mid;
+  }
+  R xi = mw::r_from<R>(0.5 * (lo + hi));
+  const int nit = W == 1 ? 3 : (W == 2 ? 3 : 4);
+  R x = mw::r_exp(xi, ln2);
+  for (int it = 0; it < nit; ++it) {
+    const R q = mw::r_add(x, mw::r_sub(rp, rm));
+    const R F = mw::r_sub(mw::r_add(mw::r_add(rp, x),
+                                    mw::r_add(mw::r_mul(A, mw::r_sub(xi, ln2M)),
+                                              mw::r_mul(B, mw::r_log(mw::r_div(q, twoM), ln2)))),
+                          target);
+    const R dF = mw::r_add(mw::r_add(x, A), mw::r_div(mw::r_mul(B, x), q));
+    xi = mw::r_sub(xi, mw::r_div(F, dF));
+    x = mw::r_exp(xi, ln2);
+  }
+  double w[4];
+  to_words(x, w);
+  double* out = half ? a.x_half : a.x_node;
+  const int rows = half ? n_half : n_nodes;
+  for (int k = 0; k < W; ++k) out[(size_t)k * rows + i] = w[k];
+  if (!half) {
+    to_words(target, w);
+    for (int k = 0; k < W; ++k) a.rs_node[(size_t)k * n_nodes + i] = w[k];
+  }
+}
+
+// Coefficients of the first-order system at (x = r - r+, theta_j), from the Teukolsky
+// equation (Eq. 1) with Psi = e^{i m phi~} r^3 Phi and Pi = Phi_t + b Phi' (Sec. 3.B):
+//   R = r^2 + a^2, Delta = x (x + r+ - r-), Sigma^2 = R^2 - a^2 Delta sin^2 th, b = R/Sigma,
+//   B = 4 i M a m r + 2 s [Delta (r + i a cos th) - M (r^2 - a^2)],
+//   C = 2 r Delta + 2 s (r - M) R + 2 i m a R,
+//   V = R^2 f''/f + C f'/f + 4 i s m a (r - M) + Delta [s - (m + s cos th)^2 / sin^2 th],
+//   f'/f = 3 Delta/(r R), f''/f = 6 Delta [(r - M) r R + a^2 Delta]/(r^2 R^3),
+//   c = a^2 Delta sin^2 th [R (r - M) - 2 r Delta]/Sigma^4 - (b B + 6 R Delta/r + C)/Sigma^2.
+// Stored: b, c_R, c_I, Re B/S^2, Im B/S^2, Delta/S^2, Re V/S^2, Im V/S^2.
+template <class R>
+__device__ void system_coeffs(const SetupArgs& a, R x, R sn, R cs, R out[8]) {
+  using namespace mw;
+  const R M = r_from<R>(a.M), av = r_from<R>(a.a);
+  const double s = a.s, m = a.m;
+  const R rp = from_words<R>(a.rp), rm = from_words<R>(a.rm);
+  const R r = r_add(rp, x);
+  const R Delta = r_mul(x, r_add(x, r_sub(rp, rm)));
+  const R a2 = r_mul(av, av);
+  const R r2 = r_mul(r, r);
+  const R Rr = r_add(r2, a2);
+  const R sn2 = r_mul(sn, sn);
+  const R Sig2 = r_sub(r_mul(Rr, Rr), r_mul(r_mul(a2, Delta), sn2));
+  const R b = r_div(Rr, r_sqrt(Sig2));
+  const R rR = r_mul(r, Rr);
+  const R fp = r_div(r_mul_d(Delta, 3.0), rR);
+  const R rmM = r_sub(r, M);
+  const R fpp = r_div(r_mul_d(r_mul(Delta, r_add(r_mul(rmM, rR), r_mul(a2, Delta))), 6.0),
+                      r_mul(r_mul(rR, rR), Rr));
+  const R B_R = r_mul_d(r_sub(r_mul(Delta, r), r_mul(M, r_sub(r2, a2))), 2.0 * s);
+  const R B_I = r_add(r_mul_d(r_mul(r_mul(M, av), r), 4.0 * m), r_mul_d(r_mul(r_mul(av, Delta), cs), 2.0 * s));
+  const R C_R = r_add(r_mul_d(r_mul(r, Delta), 2.0), r_mul_d(r_mul(rmM, Rr), 2.0 * s));
+  const R C_I = r_mul_d(r_mul(av, Rr), 2.0 * m);
+  const R msc = r_add(r_from<R>(m), r_mul_d(cs, s));
+  const R pot = r_mul(Delta, r_sub(r_from<R>(s), r_div(r_mul(msc, msc), sn2)));
+  const R V_R = r_add(r_add(r_mul(r_mul(Rr, Rr), fpp), r_mul(C_R, fp)), pot);
+  const R V_I = r_add(r_mul(C_I, fp), r_mul_d(r_mul(av, rmM), 4.0 * s * m));
+  const R bbp = r_div(r_mul(r_mul(r_mul(a2, Delta), sn2), r_sub(r_mul(Rr, rmM), r_mul_d(r_mul(r, Delta), 2.0))),
+                      r_mul(Sig2, Sig2));
+  const R c_R = r_sub(bbp, r_div(r_add(r_add(r_mul(b, B_R), r_mul_d(r_div(r_mul(Rr, Delta), r), 6.0)), C_R), Sig2));
+  const R c_I = r_neg(r_div(r_add(r_mul(b, B_I), C_I), Sig2));
+  out[0] = b;
+  out[1] = c_R;
+  out[2] = c_I;
+  out[3] = r_div(B_R, Sig2);
+  out[4] = r_div(B_I, Sig2);
+  out[5] = r_div(Delta, Sig2);
+  out[6] = r_div(V_R, Sig2);
+  out[7] = r_div(V_I, Sig2);
+}
+
+// Raw coefficients at every node / half node, and the per-substep folded tables:
+//   half node:  H0 = l b/2, H1 = -h c_R/(2dr), H2 = h c_I/(2dr), H3 = 1/2 - h bR/4,
+//               H4 = h bI/4, H5 = h g/4, H6 = h nR/4, H7 = h nI/4
+//   node:       N0 = l b,   N1 = -h c_R/dr,    N2 = h c_I/dr,    N3 = -h bR/2,
+//               N4 = h bI/2, N5 = h g/2, N6 = h nR/2, N7 = h nI/2
+// with h = dt/k, l = h/dr, bR + i bI = B/Sigma^2, g = Delta/Sigma^2, nR + i nI = V/Sigma^2.
+template <int W>
+__global__ void coeff_kernel(SetupArgs a, int half) {
+  using R = typename RT<W>::T;
+  using namespace mw;
+  const int rows = half ? a.g.n_r - 1 : a.g.n_r;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= a.g.n_th || i >= rows) return;
+  const double* xs = half ? a.x_half : a.x_node;
+  double w[4] = {0, 0, 0, 0};
+  for (int k = 0; k < W; ++k) w[k] = xs[(size_t)k * rows + i];
+  const R x = from_words<R>(w);
+  for (int k = 0; k < W; ++k) w[k] = a.sin_th[(size_t)k * a.g.n_th + j];
+  const R sn = from_words<R>(w);
+  for (int k = 0; k < W; ++k) w[k] = a.cos_th[(size_t)k * a.g.n_th + j];
+  const R cs = from_words<R>(w);
+  R c[8];
+  system_coeffs<R>(a, x, sn, cs, c);
+  const size_t ws = (size_t)rows * a.g.pitch;
+  const size_t base = (size_t)i * a.g.pitch + j;
+  double* raw = half ? a.ch_raw : a.cn_raw;
+  for (int q = 0; q < 8; ++q) st_r(raw + (size_t)q * W * ws + base, ws, c[q]);
+  const R h = from_words<R>(a.dts), lam = from_words<R>(a.lambda);
+  const R hdr = r_div(h, from_words<R>(a.dr));
+  R f[8];
+  if (half) {
+    f[0] = r_scale2(r_mul(lam, c[0]), 0.5);
+    f[1] = r_neg(r_scale2(r_mul(hdr, c[1]), 0.5));
+    f[2] = r_scale2(r_mul(hdr, c[2]), 0.5);
+    f[3] = r_sub(r_from<R>(0.5), r_scale2(r_mul(h, c[3]), 0.25));
+    f[4] = r_scale2(r_mul(h, c[4]), 0.25);
+    f[5] = r_scale2(r_mul(h, c[5]), 0.25);
+    f[6] = r_scale2(r_mul(h, c[6]), 0.25);
+    f[7] = r_scale2(r_mul(h, c[7]), 0.25);
+  } else {
+    f[0] = r_mul(lam, c[0]);
+    f[1] = r_neg(r_mul(hdr, c[1]));
+    f[2] = r_mul(hdr, c[2]);
+    f[3] = r_neg(r_scale2(r_mul(h, c[3]), 0.5));
+    f[4] = r_scale2(r_mul(h, c[4]), 0.5);
+    f[5] = r_scale2(r_mul(h, c[5]), 0.5);
+    f[6] = r_scale2(r_mul(h, c[6]), 0.5);
+    f[7] = r_scale2(r_mul(h, c[7]), 0.5);
+  }
+  double* fold = half ? a.ch : a.cn;
+  for (int q = 0; q < 8; ++q) st_r(fold + (size_t)q * W * ws + base, ws, f[q]);
+}
+
+struct PulseArgs {
+  Geom g;
+  double center, width, amp_re, amp_im;
+  double ln2[4];
+  const double* rs_node;  // [W][n_r]
+  const double* prof;     // [W][n_th] angular profile sY(theta_j)
+  const double* cn_raw;   // b at nodes = plane 0
+  double* u;              // [4][W][n_r][pitch]
+};
+
+// Initial data: Phi = A exp(-((r* - c)/w)^2) sY(theta), zero time derivative so that
+// Pi = b Phi_{r*} = b A G'(r*) sY(theta), G' = -2 (r* - c)/w^2 G. Boundary rows stay zero.
+template <int W>
+__global__ void pulse_kernel(PulseArgs a) {
+  using R = typename RT<W>::T;
+  using namespace mw;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= a.g.n_th || i >= a.g.n_r) return;
+  const size_t ws = (size_t)a.g.n_r * a.g.pitch;
+  const size_t idx = (size_t)i * a.g.pitch + j;
+  if (i == 0 || i == a.g.n_r - 1) {
+    for (int c = 0; c < 4; ++c) st_r(a.u + (size_t)c * W * ws + idx, ws, r_from<R>(0.0));
+    return;
+  }
+  double w[4] = {0, 0, 0, 0};
+  for (int k = 0; k < W; ++k) w[k] = a.rs_node[(size_t)k * a.g.n_r + i];
+  const R rs = from_words<R>(w);
+  for (int k = 0; k < W; ++k) w[k] = a.prof[(size_t)k * a.g.n_th + j];
+  const R Y = from_words<R>(w);
+  const R z = r_div_d(r_sub(rs, r_from<R>(a.center)), a.width);
+  const R G = r_exp(r_neg(r_mul(z, z)), from_words<R>(a.ln2));
+  const R Gp = r_mul(r_neg(r_div_d(r_scale2(z, 2.0), a.width)), G);
+  const R b = ld_r<R>(a.cn_raw + idx, ws);
+  const R GY = r_mul(G, Y), GpY = r_mul(Gp, Y);
+  st_r(a.u + 0 * W * ws + idx, ws, r_mul_d(GY, a.amp_re));
+  st_r(a.u + 1 * W * ws + idx, ws, r_mul_d(GY, a.amp_im));
+  st_r(a.u + 2 * W * ws + idx, ws, r_mul(b, r_mul_d(GpY, a.amp_re)));
+  st_r(a.u + 3 * W * ws + idx, ws, r_mul(b, r_mul_d(GpY, a.amp_im)));
+}
+
+// ---- the Lax-Wendroff substep ----------------------------------------------------------------
+struct StepArgs {
+  Geom g;
+  const double* u_in;      // [4][W][n_r][pitch], level n
+  double* u_out;           // same layout, level n+1 (may alias u_in)
+  double* uh;              // [4][W][n_r-1][pitch] half-step scratch
+  const double* cn;        // folded node tables [8][W][n_r][pitch]
+  const double* ch;        // folded half tables [8][W][n_r-1][pitch]
+  const double* wts;       // theta stencil weights [11][W][n_th]
+  double h4[4], h2[4];     // dt/(4k), dt/(2k)
+  int radius;              // 5 (10th order) or 1 (2nd order)
+  int record;              // write Phi(i_obs, .) to the ring after this substep
+  int i_obs;
+  long long ring_slot;
+  double* ring;            // [cap][2][W][n_th]
+  unsigned int* status;    // bit 0: non-finite value produced
+};
+
+// Centred theta operator at column j on a ghosted shared-memory row (index j + radius is
+// column j): sum_q w[q][j] f[j + q], combined second-derivative and cot(th) first-derivative
+// weights (Sec. 3.D, 11-point 10th-order stencil; 3-point for 2nd order).
+template <class R, int W>
+__device__ __forceinline__ R theta_op(const double* srow, int gstride, const double* __restrict__ wts,
+                                      int n_th, int radius, int j) {
+  const int nq = 2 * radius + 1;
+  const size_t wws = (size_t)n_th;
+  R c0 = ld_r<R>(wts + (size_t)0 * W * wws + j, wws);
+  R v0 = ld_s<R>(srow + j, gstride);
+  Acc<R> acc(mw::r_from<R>(0.0));
+  acc.mac(c0, v0);
+  for (int q = 1; q < nq; ++q) {
+    const R cq = ld_r<R>(wts + (size_t)q * W * wws + j, wws);
+    const R vq = ld_s<R>(srow + j + q, gstride);
+    acc.mac(cq, vq);
+  }
+  return acc.get();
+}
+
+// Writes value v of ghosted row column j, and its parity images across the poles.
+template <class R>
+__device__ __forceinline__ void put_ghosted(double* srow, int gstride, int n_th, int radius, int parity,
+                                            int j, R v) {
+  st_r(srow + j + radius, gstride, v);
+  const R pv = parity > 0 ? v : v_neg(v);
+  if (j < radius) st_r(srow + (radius - 1 - j), gstride, pv);               // column -1-j
+  if (j >= n_th - radius) st_r(srow + (2 * n_th - 1 - j) + radius, gstride, pv);  // column 2n-1-j
+}
+
+// Eq. lw1 at half nodes h = 0 .. n_r-2:
+//   u^{n+1/2}_{h} = (u_{h+1} + u_h)/2 - dt/2 [D (u_{h+1} - u_h)/dr - S(ubar, du)],
+// written with the folded tables and s = u_{h+1} + u_h, d = u_{h+1} - u_h:
+//   Phi_h  = s_Phi/2 - H0 d_Phi + (h/4) s_Pi,
+//   Pi_h,R = H3 s_PiR + H4 s_PiI + H0 d_PiR + H1 d_PhiR + H2 d_PhiI + H5 L(s_Phi)_R + H6 s_PhiR - H7 s_PhiI,
+//   Pi_h,I = H3 s_PiI - H4 s_PiR + H0 d_PiI + H1 d_PhiI - H2 d_PhiR + H5 L(s_Phi)_I + H6 s_PhiI + H7 s_PhiR.
+template <int W>
+__global__ void __launch_bounds__(256) half_kernel(StepArgs a) {
+  using R = typename RT<W>::T;
+  extern __shared__ double sm[];
+  const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
+  const int gstride = n_th + 2 * rad;             // one ghosted word row
+  const int h = blockIdx.x * blockDim.y + threadIdx.y;
+  const bool ok = h < n_r - 1;
+  double* sR = sm + (size_t)threadIdx.y * 2 * W * gstride;
+  double* sI = sR + (size_t)W * gstride;
+  const size_t ws = (size_t)n_r * pitch;          // state word-plane stride
+  const size_t hs = (size_t)(n_r - 1) * pitch;    // half word-plane stride
+  const double* u = a.u_in;
+  if (ok) {
+    for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+      const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
+      const R sPR = v_add(ld_s<R>(u + 0 * W * ws + i1, ws), ld_s<R>(u + 0 * W * ws + i0, ws));
+      const R sPI = v_add(ld_s<R>(u + 1 * W * ws + i1, ws), ld_s<R>(u + 1 * W * ws + i0, ws));
+      put_ghosted<R>(sR, gstride, n_th, rad, a.g.parity, j, sPR);
+      put_ghosted<R>(sI, gstride, n_th, rad, a.g.parity, j, sPI);
+    }
+  }
+  __syncthreads();
+  if (!ok) return;
+  const R h4 = from_words<R>(a.h4);
+  for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+    const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
+    const R uPR0 = ld_s<R>(u + 0 * W * ws + i0, ws), uPR1 = ld_s<R>(u + 0 * W * ws + i1, ws);
+    const R uPI0 = ld_s<R>(u + 1 * W * ws + i0, ws), uPI1 = ld_s<R>(u + 1 * W * ws + i1, ws);
+    const R uQR0 = ld_s<R>(u + 2 * W * ws + i0, ws), uQR1 = ld_s<R>(u + 2 * W * ws + i1, ws);
+    const R uQI0 = ld_s<R>(u + 3 * W * ws + i0, ws), uQI1 = ld_s<R>(u + 3 * W * ws + i1, ws);
+    const R sPR = ld_s<R>(sR + j + rad, gstride), sPI = ld_s<R>(sI + j + rad, gstride);
+    const R dPR = v_sub(uPR1, uPR0), dPI = v_sub(uPI1, uPI0);
+    const R sQR = v_add(uQR1, uQR0), sQI = v_add(uQI1, uQI0);
+    const R dQR = v_sub(uQR1, uQR0), dQI = v_sub(uQI1, uQI0);
+    const R LR = theta_op<R, W>(sR, gstride, a.wts, n_th, rad, j);
+    const R LI = theta_op<R, W>(sI, gstride, a.wts, n_th, rad, j);
+    const size_t ci = (size_t)h * pitch + j;
+    const R H0 = ld_r<R>(a.ch + 0 * W * hs + ci, hs), H1 = ld_r<R>(a.ch + 1 * W * hs + ci, hs);
+    const R H2 = ld_r<R>(a.ch + 2 * W * hs + ci, hs), H3 = ld_r<R>(a.ch + 3 * W * hs + ci, hs);
+    const R H4 = ld_r<R>(a.ch + 4 * W * hs + ci, hs), H5 = ld_r<R>(a.ch + 5 * W * hs + ci, hs);
+    const R H6 = ld_r<R>(a.ch + 6 * W * hs + ci, hs), H7 = ld_r<R>(a.ch + 7 * W * hs + ci, hs);
+    Acc<R> pr(v_half(sPR));
+    pr.mac(v_neg(H0), dPR);
+    pr.mac(h4, sQR);
+    Acc<R> pi(v_half(sPI));
+    pi.mac(v_neg(H0), dPI);
+    pi.mac(h4, sQI);
+    Acc<R> qr(mw::r_from<R>(0.0));
+    qr.mac(H3, sQR); qr.mac(H4, sQI); qr.mac(H0, dQR); qr.mac(H1, dPR); qr.mac(H2, dPI);
+    qr.mac(H5, LR); qr.mac(H6, sPR); qr.mac(v_neg(H7), sPI);
+    Acc<R> qi(mw::r_from<R>(0.0));
+    qi.mac(H3, sQI); qi.mac(v_neg(H4), sQR); qi.mac(H0, dQI); qi.mac(H1, dPI); qi.mac(v_neg(H2), dPR);
+    qi.mac(H5, LI); qi.mac(H6, sPI); qi.mac(H7, sPR);
+    st_r(a.uh + 0 * W * hs + ci, hs, pr.get());
+    st_r(a.uh + 1 * W * hs + ci, hs, pi.get());
+    st_r(a.uh + 2 * W * hs + ci, hs, qr.get());
+    st_r(a.uh + 3 * W * hs + ci, hs, qi.get());
+  }
+}
+
+__device__ __forceinline__ bool nonfinite(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+}
+__device__ __forceinline__ double lead_of(double x) { return x; }
+__device__ __forceinline__ double lead_of(mw::dd x) { return x.h; }
+__device__ __forceinline__ double lead_of(mw::qd x) { return x.x0; }
+
+// Eq. lw2 at nodes i = 1 .. n_r-2 (rows 0 and n_r-1 stay zero, Sec. 3.B):
+//   u^{n+1}_i = u^n_i - dt [D (u_{i+1/2} - u_{i-1/2})/dr - S(ubar, du)],
+// with s = u_{i+1/2} + u_{i-1/2}, d = u_{i+1/2} - u_{i-1/2} and the folded node tables:
+//   Phi'  = Phi - N0 d_Phi + (h/2) s_Pi,
+//   Pi'_R = Pi_R + N0 d_PiR + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L(s_Phi)_R + N6 s_PhiR - N7 s_PhiI,
+//   Pi'_I = Pi_I + N0 d_PiI + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L(s_Phi)_I + N6 s_PhiI + N7 s_PhiR.
+template <int W>
+__global__ void __launch_bounds__(256) full_kernel(StepArgs a) {
+  using R = typename RT<W>::T;
+  extern __shared__ double sm[];
+  const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
+  const int gstride = n_th + 2 * rad;
+  const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
+  const bool ok = i < n_r - 1;
+  double* sR = sm + (size_t)threadIdx.y * 2 * W * gstride;
+  double* sI = sR + (size_t)W * gstride;
+  const size_t ws = (size_t)n_r * pitch;
+  const size_t hs = (size_t)(n_r - 1) * pitch;
+  const double* uh = a.uh;
+  if (ok) {
+    for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+      const size_t p = (size_t)i * pitch + j, m = p - pitch;  // half rows i+1/2 and i-1/2
+      const R sPR = v_add(ld_s<R>(uh + 0 * W * hs + p, hs), ld_s<R>(uh + 0 * W * hs + m, hs));
+      const R sPI = v_add(ld_s<R>(uh + 1 * W * hs + p, hs), ld_s<R>(uh + 1 * W * hs + m, hs));
+      put_ghosted<R>(sR, gstride, n_th, rad, a.g.parity, j, sPR);
+      put_ghosted<R>(sI, gstride, n_th, rad, a.g.parity, j, sPI);
+    }
+  }
+  __syncthreads();
+  if (!ok) return;
+  const R h2 = from_words<R>(a.h2);
+  bool bad = false;
+  for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+    const size_t p = (size_t)i * pitch + j, m = p - pitch;
+    const R hPR1 = ld_s<R>(uh + 0 * W * hs + p, hs), hPR0 = ld_s<R>(uh + 0 * W * hs + m, hs);
+    const R hPI1 = ld_s<R>(uh + 1 * W * hs + p, hs), hPI0 = ld_s<R>(uh + 1 * W * hs + m, hs);
+    const R hQR1 = ld_s<R>(uh + 2 * W * hs + p, hs), hQR0 = ld_s<R>(uh + 2 * W * hs + m, hs);
+    const R hQI1 = ld_s<R>(uh + 3 * W * hs + p, hs), hQI0 = ld_s<R>(uh + 3 * W * hs + m, hs);
+    const R sPR = ld_s<R>(sR + j + rad, gstride), sPI = ld_s<R>(sI + j + rad, gstride);
+    const R dPR = v_sub(hPR1, hPR0), dPI = v_sub(hPI1, hPI0);
+    const R sQR = v_add(hQR1, hQR0), sQI = v_add(hQI1, hQI0);
+    const R dQR = v_sub(hQR1, hQR0), dQI = v_sub(hQI1, hQI0);
+    const R LR = theta_op<R, W>(sR, gstride, a.wts, n_th, rad, j);
+    const R LI = theta_op<R, W>(sI, gstride, a.wts, n_th, rad, j);
+    const size_t ci = (size_t)i * pitch + j;
+    const R N0 = ld_r<R>(a.cn + 0 * W * ws + ci, ws), N1 = ld_r<R>(a.cn + 1 * W * ws + ci, ws);
+    const R N2 = ld_r<R>(a.cn + 2 * W * ws + ci, ws), N3 = ld_r<R>(a.cn + 3 * W * ws + ci, ws);
+    const R N4 = ld_r<R>(a.cn + 4 * W * ws + ci, ws), N5 = ld_r<R>(a.cn + 5 * W * ws + ci, ws);
+    const R N6 = ld_r<R>(a.cn + 6 * W * ws + ci, ws), N7 = ld_r<R>(a.cn + 7 * W * ws + ci, ws);
+    const R PR = ld_s<R>(a.u_in + 0 * W * ws + ci, ws), PI = ld_s<R>(a.u_in + 1 * W * ws + ci, ws);
+    const R QR = ld_s<R>(a.u_in + 2 * W * ws + ci, ws), QI = ld_s<R>(a.u_in + 3 * W * ws + ci, ws);
+    Acc<R> pr(PR);
+    pr.mac(v_neg(N0), dPR);
+    pr.mac(h2, sQR);
+    Acc<R> pi(PI);
+    pi.mac(v_neg(N0), dPI);
+    pi.mac(h2, sQI);
+    Acc<R> qr(QR);
+    qr.mac(N0, dQR); qr.mac(N1, dPR); qr.mac(N2, dPI); qr.mac(N3, sQR); qr.mac(N4, sQI);
+    qr.mac(N5, LR); qr.mac(N6, sPR); qr.mac(v_neg(N7), sPI);
+    Acc<R> qi(QI);
+    qi.mac(N0, dQI); qi.mac(N1, dPI); qi.mac(v_neg(N2), dPR); qi.mac(N3, sQI); qi.mac(v_neg(N4), sQR);
+    qi.mac(N5, LI); qi.mac(N6, sPI); qi.mac(N7, sPR);
+    const R oPR = pr.get(), oPI = pi.get(), oQR = qr.get(), oQI = qi.get();
+    st_r(a.u_out + 0 * W * ws + ci, ws, oPR);
+    st_r(a.u_out + 1 * W * ws + ci, ws, oPI);
+    st_r(a.u_out + 2 * W * ws + ci, ws, oQR);
+    st_r(a.u_out + 3 * W * ws + ci, ws, oQI);
+    bad |= nonfinite(lead_of(oPR)) | nonfinite(lead_of(oPI)) | nonfinite(lead_of(oQR)) | nonfinite(lead_of(oQI));
+    if (a.record && i == a.i_obs) {
+      double* slot = a.ring + (size_t)a.ring_slot * 2 * W * n_th;
+      st_r(slot + 0 * W * n_th + j, n_th, oPR);
+      st_r(slot + 1 * W * n_th + j, n_th, oPI);
+    }
+  }
+  if (bad) atomicOr(a.status, 1u);
+}
+
+}  // namespace teuk

@@ -1,0 +1,288 @@
+// Per-precision set-up and launchers of the teuk library. Compiled once per arithmetic with
+// -DTEUK_WORDS=1 (FP64), 2 (double-double) or 4 (quad-double).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "teuk_internal.h"
+#include "teuk_kernels.cuh"
+
+#ifndef TEUK_WORDS
+#error "TEUK_WORDS must be 1, 2 or 4"
+#endif
+
+#define TEUK_CAT2(a, b) a##b
+#define TEUK_CAT(a, b) TEUK_CAT2(a, b)
+#define TEUK_SUFFIX(name) TEUK_CAT(name, TEUK_WORDS)
+
+namespace teuk {
+// one named namespace per arithmetic: the three units are built from the same file
+namespace TEUK_SUFFIX(prec_w) {
+
+constexpr int W = TEUK_WORDS;
+using R = typename RT<W>::T;
+using namespace mw;
+
+void put(double* dst, R v) { to_words(v, dst); }
+
+// Host-side word planes of a 1D table in the target precision: out[k * n + j].
+void store_plane(std::vector<double>& out, int n, int j, R v) {
+  double w[4];
+  to_words(v, w);
+  for (int k = 0; k < W; ++k) out[(size_t)k * n + j] = w[k];
+}
+
+// 10th-order (Sec. 3.D) and 2nd-order (Sec. 3.B) centred weights on a uniform grid,
+// scaled to integers: d2 / 25200 and d1 / 2520 for the 11-point stencil.
+const double kD2_10[11] = {8, -125, 1000, -6000, 42000, -73766, 42000, -6000, 1000, -125, 8};
+const double kD1_10[11] = {-2, 25, -150, 600, -2100, 0, 2100, -600, 150, -25, 2};
+const double kD2_2[3] = {1, -2, 1};
+const double kD1_2[3] = {-1, 0, 1};
+
+int setup_impl(teuk_s* h) {
+  const teuk_grid& g = h->grid;
+  const int n_r = h->n_r, n_th = h->n_th, pitch = h->pitch;
+  const R M = r_from<R>(h->M), a = r_from<R>(h->a);
+  const R root = r_sqrt(r_sub(r_mul(M, M), r_mul(a, a)));
+  const R rp = r_add(M, root);
+  const R rm = r_div(r_mul(a, a), rp);  // r+ r- = a^2
+  const R twoM = r_from<R>(2.0 * h->M);
+  const R A = r_div(r_mul(twoM, rp), r_sub(rp, rm));
+  const R B = r_neg(r_div(r_mul(twoM, rm), r_sub(rp, rm)));
+  const R pi = r_pi<R>();
+  const R ln2 = r_ln2<R>();
+  const R ln2M = r_log(twoM, ln2);
+  const R rsmin = r_from<R>(g.rstar_min);
+  const R dr = r_div(r_sub(r_from<R>(g.rstar_max), rsmin), r_from<R>(double(n_r - 1)));
+  const R dt = g.dt > 0 ? r_from<R>(g.dt) : r_scale2(dr, 0.25);
+  const R dts = r_div(dt, r_from<R>(double(h->k)));
+  const R lambda = r_div(dts, dr);
+  h->dt_outer = lead(dt);
+  h->dr_d = lead(dr);
+  h->rsmin_d = g.rstar_min;
+  put(h->h4_w, r_scale2(dts, 0.25));
+  put(h->h2_w, r_scale2(dts, 0.5));
+  put(h->ln2_w, ln2);
+
+  // theta grid (cell centred), sin, cos and the combined stencil weights
+  const R dth = r_div(pi, r_from<R>(double(n_th)));
+  const int rad = h->radius, nq = 2 * rad + 1;
+  const double* d2 = rad == 5 ? kD2_10 : kD2_2;
+  const double* d1 = rad == 5 ? kD1_10 : kD1_2;
+  const R A2 = rad == 5 ? r_div(r_from<R>(1.0), r_mul_d(r_mul(dth, dth), 25200.0))
+                        : r_div(r_from<R>(1.0), r_mul(dth, dth));
+  const R A1 = rad == 5 ? r_div(r_from<R>(1.0), r_mul_d(dth, 2520.0))
+                        : r_div(r_from<R>(1.0), r_mul_d(dth, 2.0));
+  std::vector<double> sn((size_t)W * n_th), cs((size_t)W * n_th), wt((size_t)nq * W * n_th);
+  for (int j = 0; j < n_th; ++j) {
+    const R th = r_mul_d(dth, double(j) + 0.5);
+    R s, c;
+    r_sincos(th, pi, s, c);
+    store_plane(sn, n_th, j, s);
+    store_plane(cs, n_th, j, c);
+    const R cot = r_div(c, s);
+    for (int q = 0; q < nq; ++q) {
+      const R wq = r_add(r_mul_d(A2, d2[q]), r_mul(r_mul_d(A1, d1[q]), cot));
+      double w[4];
+      to_words(wq, w);
+      for (int k = 0; k < W; ++k) wt[((size_t)q * W + k) * n_th + j] = w[k];
+    }
+  }
+  TEUK_CUDA(h, cudaMemcpyAsync(h->sin_th, sn.data(), sn.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  TEUK_CUDA(h, cudaMemcpyAsync(h->cos_th, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  TEUK_CUDA(h, cudaMemcpyAsync(h->wts, wt.data(), wt.size() * 8, cudaMemcpyHostToDevice, h->stream));
+
+  SetupArgs sa{};
+  sa.g = Geom{n_r, n_th, pitch, h->parity};
+  sa.W = W;
+  sa.M = h->M;
+  sa.a = h->a;
+  sa.s = h->s;
+  sa.m = h->m;
+  put(sa.rp, rp); put(sa.rm, rm); put(sa.tort_A, A); put(sa.tort_B, B);
+  put(sa.ln2, ln2); put(sa.ln2M, ln2M); put(sa.rsmin, rsmin); put(sa.dr, dr);
+  put(sa.dts, dts); put(sa.lambda, lambda);
+  sa.sin_th = h->sin_th;
+  sa.cos_th = h->cos_th;
+  sa.x_node = h->x_node;
+  sa.x_half = h->x_half;
+  sa.rs_node = h->rs_node;
+  sa.cn_raw = h->cn_raw;
+  sa.ch_raw = h->ch_raw;
+  sa.cn = h->cn;
+  sa.ch = h->ch;
+  const int rows_total = 2 * n_r - 1;
+  tortoise_kernel<W><<<(rows_total + 63) / 64, 64, 0, h->stream>>>(sa);
+  TEUK_CUDA(h, cudaGetLastError());
+  dim3 blk(64);
+  coeff_kernel<W><<<dim3((n_th + 63) / 64, n_r), blk, 0, h->stream>>>(sa, 0);
+  TEUK_CUDA(h, cudaGetLastError());
+  coeff_kernel<W><<<dim3((n_th + 63) / 64, n_r - 1), blk, 0, h->stream>>>(sa, 1);
+  TEUK_CUDA(h, cudaGetLastError());
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+double binom(int n, int k) {
+  if (k < 0 || n < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int t = 1; t <= k; ++t) r = r * (n - k + t) / t;
+  return std::round(r);
+}
+
+int pulse_impl(teuk_s* h, double center, double width, double ar, double ai, int ell) {
+  const int n_th = h->n_th, s = h->s, m = h->m;
+  const R pi = r_pi<R>();
+  const R dth = r_div(pi, r_from<R>(double(n_th)));
+  // sY_{ell m}(theta) without its normalisation (Goldberg et al. 1967 sum):
+  //   sum_r (-1)^(l-r-s) C(l-s, r) C(l+s, r+s-m) sin(th/2)^(2l-2r-s+m) cos(th/2)^(2r+s-m)
+  std::vector<double> prof((size_t)W * n_th);
+  for (int j = 0; j < n_th; ++j) {
+    const R half_th = r_scale2(r_mul_d(dth, double(j) + 0.5), 0.5);
+    R sh, ch;
+    r_sincos(half_th, pi, sh, ch);
+    R sum = r_from<R>(0.0);
+    for (int r = 0; r <= ell - s; ++r) {
+      const double c = binom(ell - s, r) * binom(ell + s, r + s - m);
+      if (c == 0.0) continue;
+      R term = r_from<R>(((ell - r - s) % 2 == 0) ? c : -c);
+      for (int e = 0; e < 2 * ell - 2 * r - s + m; ++e) term = r_mul(term, sh);
+      for (int e = 0; e < 2 * r + s - m; ++e) term = r_mul(term, ch);
+      sum = r_add(sum, term);
+    }
+    store_plane(prof, n_th, j, sum);
+  }
+  TEUK_CUDA(h, cudaMemcpyAsync(h->prof, prof.data(), prof.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  PulseArgs pa{};
+  pa.g = Geom{h->n_r, n_th, h->pitch, h->parity};
+  pa.center = center;
+  pa.width = width;
+  pa.amp_re = ar;
+  pa.amp_im = ai;
+  std::memcpy(pa.ln2, h->ln2_w, sizeof(pa.ln2));
+  pa.rs_node = h->rs_node;
+  pa.prof = h->prof;
+  pa.cn_raw = h->cn_raw;
+  pa.u = h->u;
+  pulse_kernel<W><<<dim3((n_th + 63) / 64, h->n_r), 64, 0, h->stream>>>(pa);
+  TEUK_CUDA(h, cudaGetLastError());
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+// Launch shape of the step kernels: threads along theta (x), rows (y), ~256 threads.
+void step_shape(int n_th, dim3& blk) {
+  int tx = ((n_th + 31) / 32) * 32;
+  if (tx > 256) tx = 256;
+  int ty = 256 / tx;
+  if (ty < 1) ty = 1;
+  blk = dim3(tx, ty);
+}
+
+int substep_impl(teuk_s* h, bool record, int64_t slot) {
+  StepArgs sa{};
+  sa.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
+  sa.u_in = h->u;
+  sa.u_out = h->u;
+  sa.uh = h->uh;
+  sa.cn = h->cn;
+  sa.ch = h->ch;
+  sa.wts = h->wts;
+  std::memcpy(sa.h4, h->h4_w, sizeof(sa.h4));
+  std::memcpy(sa.h2, h->h2_w, sizeof(sa.h2));
+  sa.radius = h->radius;
+  sa.record = record ? 1 : 0;
+  sa.i_obs = h->i_obs;
+  sa.ring_slot = slot;
+  sa.ring = h->ring;
+  sa.status = h->status;
+  dim3 blk;
+  step_shape(h->n_th, blk);
+  const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
+  const int nh = h->n_r - 1, nf = h->n_r - 2;
+  if (smem > 48 * 1024) {  // above the default dynamic limit (quad-double, n_theta > 700)
+    TEUK_CUDA(h, cudaFuncSetAttribute(half_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TEUK_CUDA(h, cudaFuncSetAttribute(full_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  cudaEvent_t ev = nullptr;
+  time_begin(h, &ev);
+  half_kernel<W><<<(nh + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  time_end(h, 0, ev);
+  time_begin(h, &ev);
+  full_kernel<W><<<(nf + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  time_end(h, 1, ev);
+  h->launches += 2;
+  TEUK_CUDA(h, cudaGetLastError());
+  return TEUK_OK;
+}
+
+// ---- multi-word self test ---------------------------------------------------------------------
+template <class RR>
+__host__ __device__ RR apply_op(int op, RR x, RR y, RR acc, RR ln2) {
+  switch (op) {
+    case 0: return v_add(x, y);
+    case 1: return v_sub(x, y);
+    case 2: return r_mul(x, y);
+    case 3: return r_div(x, y);
+    case 4: return r_sqrt(x);
+    case 5: return r_exp(x, ln2);
+    case 6: return r_log(x, ln2);
+    default: {
+      Acc<RR> ac(acc);
+      ac.mac(x, y);
+      return ac.get();
+    }
+  }
+}
+
+__global__ void mw_eval_kernel(int op, const double* a, const double* b, double* out, int64_t n, R ln2) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0};
+  for (int k = 0; k < W; ++k) { wa[k] = a[k * n + t]; wb[k] = b[k * n + t]; wo[k] = out[k * n + t]; }
+  const R r = apply_op<R>(op, from_words<R>(wa), from_words<R>(wb), from_words<R>(wo), ln2);
+  to_words(r, wo);
+  for (int k = 0; k < W; ++k) out[k * n + t] = wo[k];
+}
+
+int mw_eval_impl(int op, int device, const double* a, const double* b, double* out, int64_t n) {
+  const R ln2 = r_ln2<R>();
+  if (!device) {
+    for (int64_t t = 0; t < n; ++t) {
+      double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0};
+      for (int k = 0; k < W; ++k) { wa[k] = a[k * n + t]; wb[k] = b[k * n + t]; wo[k] = out[k * n + t]; }
+      const R r = apply_op<R>(op, from_words<R>(wa), from_words<R>(wb), from_words<R>(wo), ln2);
+      to_words(r, wo);
+      for (int k = 0; k < W; ++k) out[k * n + t] = wo[k];
+    }
+    return TEUK_OK;
+  }
+  double *da = nullptr, *db = nullptr, *dout = nullptr;
+  const size_t bytes = (size_t)W * n * sizeof(double);
+  TEUK_CUDA(nullptr, cudaMalloc(&da, bytes));
+  TEUK_CUDA(nullptr, cudaMalloc(&db, bytes));
+  TEUK_CUDA(nullptr, cudaMalloc(&dout, bytes));
+  cudaMemcpy(da, a, bytes, cudaMemcpyHostToDevice);
+  cudaMemcpy(db, b, bytes, cudaMemcpyHostToDevice);
+  cudaMemcpy(dout, out, bytes, cudaMemcpyHostToDevice);
+  mw_eval_kernel<<<(unsigned)((n + 127) / 128), 128>>>(op, da, db, dout, n, ln2);
+  cudaError_t e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dout);
+  return e == cudaSuccess ? TEUK_OK : TEUK_ERR_CUDA;
+}
+
+}  // namespace prec_wN
+using namespace TEUK_SUFFIX(prec_w);
+
+int TEUK_SUFFIX(setup_w)(teuk_s* h) { return setup_impl(h); }
+int TEUK_SUFFIX(pulse_w)(teuk_s* h, double center, double width, double ar, double ai, int ell) {
+  return pulse_impl(h, center, width, ar, ai, ell);
+}
+int TEUK_SUFFIX(substep_w)(teuk_s* h, bool record, int64_t slot) { return substep_impl(h, record, slot); }
+int TEUK_SUFFIX(mw_eval_w)(int op, int device, const double* a, const double* b, double* out, int64_t n) {
+  return mw_eval_impl(op, device, a, b, out, n);
+}
+
+}  // namespace teuk

@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA library against the CPU oracle (256-bit MPFR unless stated).
+
+Tolerances (max-norm relative error over all compared points and the four components):
+FP64 1e-12, double-double 1e-26, quad-double 1e-55. Grids span several thread blocks and a
+ragged theta tail (n_theta not a multiple of the warp width or of the 16-double pitch).
+"""
+import numpy as np
+import pytest
+
+from paper_1006_0663_gb300 import teuk, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 1e-12, 2: 1e-26, 4: 1e-55}
+COEF_TOL = {1: 1e-13, 2: 1e-28, 4: 1e-57}
+
+
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    _cuda()
+
+
+def small(**kw):
+    base = dict(M=1.0, a=0.9, s=-2, m=2, rstar_min=-30.0, rstar_max=50.0, n_r=41, n_theta=24,
+                dt=0.0, substeps=4, theta_order=10, parity=0)
+    base.update(kw)
+    return base
+
+
+def make_pair(oracle_mod, p, W, bits=256, row_lo=0, row_hi=None):
+    g = teuk.Teuk(precision=W, **p)
+    dt = g.info()["dt"]
+    par = p["parity"] or workloads.parity_of(p["m"], p["s"])
+    o = oracle_mod.Oracle(M=p["M"], a=p["a"], s=p["s"], m=p["m"], rstar_min=p["rstar_min"],
+                          rstar_max=p["rstar_max"], n_r=p["n_r"], n_theta=p["n_theta"], dt=dt,
+                          substeps=p["substeps"], theta_order=p["theta_order"], parity=par,
+                          row_lo=row_lo, row_hi=row_hi, bits=bits)
+    return g, o
+
+
+def word_diff(gw, ow):
+    """(sum of gw words) - (sum of ow words), summed from the smallest words up."""
+    diff = 0.0
+    for k in reversed(range(max(gw.shape[0], ow.shape[0]))):
+        a = gw[k] if k < gw.shape[0] else 0.0
+        b = ow[k] if k < ow.shape[0] else 0.0
+        diff = diff + (a - b)
+    return diff
+
+
+def coef_err(gc, oc, W):
+    """max over components of max|gpu - oracle| / max|oracle| (exact word sums in mpmath-free
+    form: the difference of the leading words plus the difference of the tails)."""
+    worst = 0.0
+    for c in range(gc.shape[0]):
+        diff = np.zeros(gc.shape[2:])
+        # sum word differences from the smallest: exact enough for a tolerance check
+        for k in reversed(range(max(W, oc.shape[1]))):
+            gw = gc[c, k] if k < W else 0.0
+            ow = oc[c, k] if k < oc.shape[1] else 0.0
+            diff = diff + (gw - ow)
+        scale = np.abs(oc[c, 0]).max()
+        if scale > 0:
+            worst = max(worst, np.abs(diff).max() / scale)
+    return worst
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+def test_mw_device_matches_host(W):
+    rng = np.random.default_rng(3)
+    n = 1000
+    a = np.zeros((W, n)); b = np.zeros((W, n))
+    a[0] = rng.uniform(0.5, 2, n) * 2.0 ** rng.integers(-20, 20, n)
+    b[0] = rng.uniform(-2, 2, n) * 2.0 ** rng.integers(-20, 20, n)
+    for k in range(1, W):
+        a[k] = a[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -53
+        b[k] = b[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -53
+    for op in (0, 1, 2, 3, 4, 7):
+        c = np.zeros_like(a); c[0] = rng.uniform(-1, 1, n)
+        h = teuk.mw_eval(op, W, a, b, out=c, device=False)
+        d = teuk.mw_eval(op, W, a, b, out=c, device=True)
+        np.testing.assert_array_equal(h, d, err_msg=f"op {op}")
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+def test_tortoise_and_coefficients(oracle_mod, W):
+    p = small(n_r=37, n_theta=20, rstar_min=-120.0, rstar_max=300.0)
+    g, o = make_pair(oracle_mod, p, W)
+    grid = o.grid(words=5)
+    for which, key in ((0, "x_node"), (1, "x_half")):
+        xg = g.tortoise_x(which)
+        xo = grid[key]
+        rel = np.abs(word_diff(xg, xo)) / np.abs(xo[0])
+        assert rel.max() < COEF_TOL[W], (which, rel.max())
+    for which in (0, 1):
+        err = coef_err(g.coeffs(which), o.coeffs(which, words=5), W)
+        assert err < COEF_TOL[W], (which, err)
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+def test_initial_pulse(oracle_mod, W):
+    p = small()
+    g, o = make_pair(oracle_mod, p, W)
+    g.set_initial_pulse(10.0, 4.0, 0.7, 0.6, 2)
+    o.pulse(10.0, 4.0, 0.7, 0.6, 2)
+    err, umax = o.max_rel_err(g.get_state())
+    assert umax > 0.1 and err < TOL[W] / 10, err
+
+
+CASES = [
+    dict(),                                                    # s=-2, m=2, parity +1
+    dict(a=0.6, s=-1, m=2, n_theta=40, n_r=53),                # odd parity (m+s odd)
+    dict(a=0.99, s=0, m=0, n_theta=17, n_r=35, substeps=2),    # scalar field, tiny ragged theta
+    dict(a=0.5, s=-2, m=1, theta_order=2, n_theta=30),         # 2nd-order theta operator
+]
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_evolution_parity(oracle_mod, W, case):
+    p = small(**CASES[case])
+    g, o = make_pair(oracle_mod, p, W)
+    ell = max(abs(p["m"]), abs(p["s"]))
+    g.set_initial_pulse(12.0, 4.0, 0.8, 0.55, ell)
+    o.pulse(12.0, 4.0, 0.8, 0.55, ell)
+    outer = 3
+    g.step(outer)
+    g.sync()
+    o.step(outer * p["substeps"])
+    err, umax = o.max_rel_err(g.get_state())
+    assert umax > 0.05
+    assert err < TOL[W], err
+
+
+@pytest.mark.parametrize("W,name,nsub", [(2, "c2", 12), (4, "c3", 8), (1, "c5", 40), (1, "c1", 60)])
+def test_full_size_sampled_parity(oracle_mod, W, name, nsub):
+    """Workload at its full size in the benchmark's launch configuration; the oracle
+    computes a window of rows, exact in its interior after nsub iterations (one row per
+    iteration of domain of dependence)."""
+    prob = workloads.CONFIGS[name]
+    p = dict(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
+             rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
+             substeps=prob.substeps, theta_order=10, parity=0)
+    # sample where the pulse is, and a window that contains the inner boundary row
+    ic = int(round((prob.center - prob.rstar_min) / prob.dr))
+    windows = [(ic - 12, ic + 12), (0, 16)]
+    bits = 53 if W == 1 else 256
+    g = teuk.Teuk(precision=W, **p)
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    g.substep(nsub)
+    g.sync()
+    full = g.get_state()
+    dt = g.info()["dt"]
+    for lo, hi in windows:
+        wlo, whi = max(0, lo - nsub - 1), min(prob.n_r - 1, hi + nsub + 1)
+        o = oracle_mod.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
+                              rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=dt,
+                              substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi,
+                              bits=bits)
+        o.pulse(prob.center, prob.width, ar, ai, prob.ell)
+        o.step(nsub)
+        planes = np.ascontiguousarray(full[:, :, wlo:whi + 1])
+        err, umax = o.max_rel_err(planes, lo - wlo, hi - wlo)
+        tol = TOL[W] if bits > 53 else 1e-11  # FP64 oracle without FMA vs FMA kernel
+        assert umax > 0 or lo == 0
+        assert err < tol, (lo, hi, err)
+
+
+def test_waveform_ring_matches_observe():
+    p = small(n_r=61, n_theta=32)
+    g = teuk.Teuk(precision=2, **p)
+    g.set_initial_pulse(5.0, 4.0, 0.7, 0.6, 2)
+    g.set_observer(20.0, capacity=4)
+    outs = []
+    for _ in range(6):
+        g.step(1)
+        obs, used = g.observe(20.0)
+        outs.append(obs)
+    wf = g.read_waveform()
+    assert wf.shape == (4, 2, 2, 32)
+    for t in range(4):
+        np.testing.assert_array_equal(wf[t], outs[2 + t])
+    assert abs(used - 20.0) <= 1.0
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+def test_conjugation_symmetry_bitwise(W):
+    p = small()
+    g1 = teuk.Teuk(precision=W, **p)
+    g2 = teuk.Teuk(precision=W, **dict(p, a=-p["a"]))
+    g1.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+    g2.set_initial_pulse(10.0, 4.0, 0.8, -0.6, 2)
+    g1.step(2)
+    g2.step(2)
+    u1, u2 = g1.get_state(), g2.get_state()
+    np.testing.assert_array_equal(u1[0], u2[0])
+    np.testing.assert_array_equal(u1[1], -u2[1])
+    np.testing.assert_array_equal(u1[2], u2[2])
+    np.testing.assert_array_equal(u1[3], -u2[3])
+
+
+@pytest.mark.parametrize("W", [1, 2])
+def test_checkpoint_resume_bitwise(W):
+    p = small()
+    g1 = teuk.Teuk(precision=W, **p)
+    g1.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+    g1.step(4)
+    ref = g1.get_state()
+    g2 = teuk.Teuk(precision=W, **p)
+    g2.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+    g2.step(2)
+    snap = g2.get_state()
+    g3 = teuk.Teuk(precision=W, **p)
+    g3.set_state(snap, 8)
+    g3.step(2)
+    np.testing.assert_array_equal(g3.get_state(), ref)
+
+
+def test_nonfinite_guard_reports_error():
+    p = small()
+    g = teuk.Teuk(precision=1, **p)
+    g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+    u = g.get_state()
+    u[2, 0, 20, 5] = np.nan  # a corrupted state made on the host
+    g.set_state(u)
+    g.step(1)
+    with pytest.raises(teuk.TeukError) as e:
+        g.sync()
+    assert e.value.code == teuk.ERR_NONFINITE

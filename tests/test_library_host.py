@@ -1,0 +1,129 @@
+"""Host-side checks of the CUDA library: it builds, loads, exports every symbol declared in
+include/teuk.h, refuses bad arguments, and its multi-word arithmetic (the same header the
+kernels use, compiled for the host) meets the error bounds of the published algorithms."""
+import ctypes
+import os
+import re
+
+import mpmath as mpm
+import numpy as np
+import pytest
+
+from paper_1006_0663_gb300 import teuk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "teuk.h")).read()
+    return sorted(set(re.findall(r"\b(teuk_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = teuk.lib()
+    names = declared_symbols()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) <= set(teuk.SYMBOLS) | {"teuk_create"}
+
+
+def test_strerror_and_invalid_arguments():
+    L = teuk.lib()
+    assert L.teuk_strerror(0) == b"ok"
+    assert b"invalid" in L.teuk_strerror(teuk.ERR_INVALID_ARG)
+    g = teuk.TeukGrid(-10.0, 10.0, 2, 16, 0.0, 1, 10, 0, 0)  # n_r < 3
+    h = ctypes.c_void_p()
+    rc = L.teuk_create(ctypes.byref(h), 1.0, 0.5, -2, 2, ctypes.byref(g), 1, None)
+    assert rc == teuk.ERR_INVALID_ARG
+    g = teuk.TeukGrid(-10.0, 10.0, 64, 16, 0.0, 1, 10, 0, 0)
+    assert L.teuk_create(ctypes.byref(h), 1.0, 1.0, -2, 2, ctypes.byref(g), 1, None) == teuk.ERR_INVALID_ARG
+    assert L.teuk_create(ctypes.byref(h), 1.0, 0.5, -2, 2, ctypes.byref(g), 3, None) == teuk.ERR_INVALID_ARG
+    g = teuk.TeukGrid(-10.0, 10.0, 64, 16, 0.0, 1, 4, 0, 0)  # theta order 4 unsupported
+    assert L.teuk_create(ctypes.byref(h), 1.0, 0.5, -2, 2, ctypes.byref(g), 1, None) == teuk.ERR_INVALID_ARG
+
+
+def _rand_words(rng, words, n, spread=True):
+    """Random normalised expansions with leading words of mixed sign and magnitude."""
+    mpm.mp.prec = 400
+    vals, out = [], np.zeros((words, n))
+    for t in range(n):
+        e = rng.integers(-30, 30) if spread else 0
+        v = mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** int(e)
+        for k in range(1, 6):
+            v += mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** (int(e) - 53 * k)
+        rest = v
+        for k in range(words):
+            out[k, t] = float(rest)
+            rest -= out[k, t]
+        vals.append(sum(mpm.mpf(float(x)) for x in out[:, t]))
+    return out, vals
+
+
+def _words_value(w, t):
+    return sum(mpm.mpf(float(x)) for x in w[:, t])
+
+
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "sqrt": 4, "exp": 5, "log": 6, "acc": 7}
+# relative error bounds used: dd ~ 2^-104 (JMP17: <= 4u^2 for mul, 3u^2 for accurate add),
+# qd ~ 2^-205 (HLB01 quad-double bounds with margin)
+BOUND = {2: 2.0 ** -101, 4: 2.0 ** -200}
+
+
+@pytest.mark.parametrize("words", [2, 4])
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div", "sqrt", "exp", "log"])
+def test_multiword_host_vs_mpmath(words, op):
+    rng = np.random.default_rng(7 + words + OPS[op])
+    n = 200
+    a, av = _rand_words(rng, words, n)
+    b, bv = _rand_words(rng, words, n)
+    if op in ("sqrt", "log"):
+        a = a * np.sign(a[0])[None, :]
+        av = [abs(v) for v in av]
+    if op == "exp":
+        a = a / 2.0 ** 30 * 40  # |x| up to ~40
+        a[0] = np.clip(a[0], -700, 700)
+        av = [_words_value(a, t) for t in range(n)]
+    out = teuk.mw_eval(OPS[op], words, a, b, device=False)
+    mpm.mp.prec = 400
+    worst = 0.0
+    for t in range(n):
+        x, y = _words_value(a, t), _words_value(b, t)
+        want = {"add": lambda: x + y, "sub": lambda: x - y, "mul": lambda: x * y,
+                "div": lambda: x / y, "sqrt": lambda: mpm.sqrt(x), "exp": lambda: mpm.exp(x),
+                "log": lambda: mpm.log(x)}[op]()
+        got = _words_value(out, t)
+        scale = abs(want)
+        if op in ("add", "sub"):
+            scale = abs(x) + abs(y)  # qd add is the sloppy variant (error relative to |x|+|y|)
+        if op == "log":
+            scale = max(abs(want), 1)
+        worst = max(worst, float(abs(got - want) / scale))
+    assert worst < BOUND[words] * (64 if op in ("exp", "log") else 1), worst
+
+
+@pytest.mark.parametrize("words", [2, 4])
+def test_dot_accumulator_host(words):
+    """acc + a*b through the step kernels' accumulator: error ~ u^2 of |acc| + |a b|."""
+    rng = np.random.default_rng(11 + words)
+    n = 200
+    a, _ = _rand_words(rng, words, n)
+    b, _ = _rand_words(rng, words, n)
+    c, _ = _rand_words(rng, words, n)
+    out = teuk.mw_eval(OPS["acc"], words, a, b, out=c, device=False)
+    worst = 0.0
+    for t in range(n):
+        x, y, z = _words_value(a, t), _words_value(b, t), _words_value(c, t)
+        want = z + x * y
+        got = _words_value(out, t)
+        worst = max(worst, float(abs(got - want) / (abs(z) + abs(x * y))))
+    assert worst < BOUND[words], worst
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(teuk.TeukError) as e:
+        teuk.Teuk(M=1.0, a=0.5, s=-2, m=2, rstar_min=-10, rstar_max=10, n_r=16, n_theta=16)
+    assert e.value.code in (teuk.ERR_NO_DEVICE, teuk.ERR_CUDA)
