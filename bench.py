@@ -167,7 +167,7 @@ def cpu_baseline(prob, words, seconds_target=15.0):
     ic = int(round((prob.center - prob.rstar_min) / prob.dr))
     lo = max(0, ic - rows // 2)
     o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
-                      rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=prob.dt,
+                      rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                       substeps=prob.substeps, parity=prob.parity, row_lo=lo,
                       row_hi=min(prob.n_r - 1, lo + rows - 1), bits=bits)
     ar, ai = prob.amps
@@ -240,6 +240,8 @@ def main():
     prob = workloads.CONFIGS[WORKLOAD]
     W = prob.words
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # the library handles are created on this stream
 
     if world > 1:
         dist.barrier()

@@ -109,7 +109,7 @@ struct oracle_params {
   int32_t s, m;
   double rstar_min, rstar_max;
   int32_t n_r, n_theta;
-  double dt;            // outer step; the oracle integrates with substeps of dt/substeps
+  double dt;            // outer step (0: 0.25 dr*); integrated with substeps of dt/substeps
   int32_t substeps;     // k >= 1
   int32_t theta_order;  // 10 (Sec. 3.D) or 2 (Sec. 3.B)
   int32_t parity;       // +1 or -1: sign of the reflection of Phi, Pi across each pole
@@ -226,7 +226,7 @@ struct Solver {
     if (p.theta_order != 10 && p.theta_order != 2) return -1;
     if (p.parity != 1 && p.parity != -1) return -1;
     if (p.row_lo < 0 || p.row_hi >= p.n_r || p.row_hi - p.row_lo < 2) return -1;
-    if (!(p.rstar_max > p.rstar_min) || !(p.dt > 0)) return -1;
+    if (!(p.rstar_max > p.rstar_min) || !(p.dt >= 0)) return -1;
     nrow = p.row_hi - p.row_lo + 1;
     nth = p.n_theta;
     M = T(p.M);
@@ -238,7 +238,7 @@ struct Solver {
     tort_B = -(T(2.0) * M * rm) / (rp - rm);
     rsmin = T(p.rstar_min);
     dr = (T(p.rstar_max) - rsmin) / T(double(p.n_r - 1));
-    dt = T(p.dt);
+    dt = p.dt > 0 ? T(p.dt) : dr * T(0.25);  // dt = 0 selects 0.25 dr* in this precision
     dts = dt / T(double(p.substeps));
     const T pi = pi_<T>();
     dth = pi / T(double(nth));

@@ -104,11 +104,17 @@ def _check(rc, handle=None):
         raise TeukError(rc, msg)
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
 def _current_stream():
+    """torch's current CUDA stream as a cudaStream_t; the default stream (handle 0) is passed
+    as cudaStreamLegacy so that the library does not create a stream of its own."""
     try:
         import torch
         if torch.cuda.is_available():
-            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            handle = torch.cuda.current_stream().cuda_stream
+            return ctypes.c_void_p(handle if handle else CUDA_STREAM_LEGACY)
     except Exception:  # torch absent or without CUDA: the library makes its own stream
         pass
     return None

@@ -35,10 +35,9 @@ def small(**kw):
 
 def make_pair(oracle_mod, p, W, bits=256, row_lo=0, row_hi=None):
     g = teuk.Teuk(precision=W, **p)
-    dt = g.info()["dt"]
     par = p["parity"] or workloads.parity_of(p["m"], p["s"])
     o = oracle_mod.Oracle(M=p["M"], a=p["a"], s=p["s"], m=p["m"], rstar_min=p["rstar_min"],
-                          rstar_max=p["rstar_max"], n_r=p["n_r"], n_theta=p["n_theta"], dt=dt,
+                          rstar_max=p["rstar_max"], n_r=p["n_r"], n_theta=p["n_theta"], dt=p["dt"],
                           substeps=p["substeps"], theta_order=p["theta_order"], parity=par,
                           row_lo=row_lo, row_hi=row_hi, bits=bits)
     return g, o
@@ -157,11 +156,10 @@ def test_full_size_sampled_parity(oracle_mod, W, name, nsub):
     g.substep(nsub)
     g.sync()
     full = g.get_state()
-    dt = g.info()["dt"]
     for lo, hi in windows:
         wlo, whi = max(0, lo - nsub - 1), min(prob.n_r - 1, hi + nsub + 1)
         o = oracle_mod.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
-                              rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=dt,
+                              rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                               substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi,
                               bits=bits)
         o.pulse(prob.center, prob.width, ar, ai, prob.ell)
