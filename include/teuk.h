@@ -115,6 +115,27 @@ int teuk_info(teuk_t h, int* words, int* n_r, int* n_theta, int* substeps, doubl
 /* Number of step kernels launched by this handle so far (two per Lax-Wendroff iteration). */
 int64_t teuk_kernel_launches(teuk_t h);
 
+/* Lax-Wendroff iterations that allocate nothing, for callers that cannot let a library
+ * allocate device memory while they step (their memory belongs to a pool of their own, or
+ * they cannot afford cudaMalloc/cudaFree, which may synchronise the whole device). The paper
+ * has no counterpart: this is an interface variant of teuk_substep.
+ *  - h: an existing handle; only its constant tables, stream and device are used, its own
+ *    state is neither read nor written.
+ *  - u_in / u_out: caller-owned device buffers in the handle's layout
+ *    [4][w][n_r][P] doubles, P = n_theta rounded up to a multiple of 16 (128 bytes); they may
+ *    be the same buffer. The first iteration reads u_in, later ones run in place on u_out;
+ *    rows 0 and n_r-1 of u_out are set to zero.
+ *  - The half-step rows live in one fixed device array of 2^21 doubles (16 MiB) that every
+ *    GPU loading the library holds until exit; 4 * w * (n_r - 1) * P above 2^21 is rejected
+ *    with TEUK_ERR_INVALID_ARG. Every row of it that a call reads is written earlier in the
+ *    same call, so nothing needs clearing; calls that overlap on the GPU (other streams,
+ *    other handles) share the array and race.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture. The handle's device must be current.
+ *  - Calls no cudaMalloc, cudaFree or other allocating routine; work is queued on the
+ *    handle's stream. */
+int teuk_substep_noalloc(teuk_t h, const double* u_in, double* u_out, int64_t n_iterations);
+
 /* Per-kernel timing with CUDA events on the handle's stream: enable = 1 starts recording
  * the duration of every half-step and full-step launch; teuk_kernel_times() waits for the
  * stream and returns (and clears) the summed milliseconds and launch counts. */

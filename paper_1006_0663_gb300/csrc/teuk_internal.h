@@ -67,6 +67,9 @@ int pulse_w4(teuk_s* h, double center, double width, double ar, double ai, int e
 int substep_w1(teuk_s* h, bool record, int64_t slot);
 int substep_w2(teuk_s* h, bool record, int64_t slot);
 int substep_w4(teuk_s* h, bool record, int64_t slot);
+int substep_buffers_w1(teuk_s* h, const double* u_in, double* u_out, double* scratch);
+int substep_buffers_w2(teuk_s* h, const double* u_in, double* u_out, double* scratch);
+int substep_buffers_w4(teuk_s* h, const double* u_in, double* u_out, double* scratch);
 int mw_eval_w1(int op, int device, const double* a, const double* b, double* out, int64_t n);
 int mw_eval_w2(int op, int device, const double* a, const double* b, double* out, int64_t n);
 int mw_eval_w4(int op, int device, const double* a, const double* b, double* out, int64_t n);

@@ -216,6 +216,40 @@ int substep_impl(teuk_s* h, bool record, int64_t slot) {
   return TEUK_OK;
 }
 
+// One Lax-Wendroff iteration from u_in to u_out (may alias) with the half-step rows in a
+// caller-supplied scratch area; used by the no-allocation entry point (teuk_noalloc.cu).
+int substep_buffers_impl(teuk_s* h, const double* u_in, double* u_out, double* scratch) {
+  StepArgs sa{};
+  sa.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
+  sa.u_in = u_in;
+  sa.u_out = u_out;
+  sa.uh = scratch;
+  sa.cn = h->cn;
+  sa.ch = h->ch;
+  sa.wts = h->wts;
+  std::memcpy(sa.h4, h->h4_w, sizeof(sa.h4));
+  std::memcpy(sa.h2, h->h2_w, sizeof(sa.h2));
+  sa.radius = h->radius;
+  sa.record = 0;
+  sa.i_obs = -1;
+  sa.ring_slot = 0;
+  sa.ring = nullptr;
+  sa.status = h->status;
+  dim3 blk;
+  step_shape(h->n_th, blk);
+  const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
+  const int nh = h->n_r - 1, nf = h->n_r - 2;
+  if (smem > 48 * 1024) {
+    TEUK_CUDA(h, cudaFuncSetAttribute(half_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TEUK_CUDA(h, cudaFuncSetAttribute(full_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  half_kernel<W><<<(nh + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  full_kernel<W><<<(nf + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  h->launches += 2;
+  TEUK_CUDA(h, cudaGetLastError());
+  return TEUK_OK;
+}
+
 // ---- multi-word self test ---------------------------------------------------------------------
 template <class RR>
 __host__ __device__ RR apply_op(int op, RR x, RR y, RR acc, RR ln2) {
@@ -281,6 +315,9 @@ int TEUK_SUFFIX(pulse_w)(teuk_s* h, double center, double width, double ar, doub
   return pulse_impl(h, center, width, ar, ai, ell);
 }
 int TEUK_SUFFIX(substep_w)(teuk_s* h, bool record, int64_t slot) { return substep_impl(h, record, slot); }
+int TEUK_SUFFIX(substep_buffers_w)(teuk_s* h, const double* u_in, double* u_out, double* scratch) {
+  return substep_buffers_impl(h, u_in, u_out, scratch);
+}
 int TEUK_SUFFIX(mw_eval_w)(int op, int device, const double* a, const double* b, double* out, int64_t n) {
   return mw_eval_impl(op, device, a, b, out, n);
 }

@@ -24,7 +24,7 @@ SYMBOLS = [
     "teuk_substep", "teuk_sync", "teuk_observe", "teuk_set_observer", "teuk_read_waveform",
     "teuk_get_state", "teuk_set_state", "teuk_get_state_device", "teuk_get_coeffs",
     "teuk_get_tortoise", "teuk_info", "teuk_kernel_launches", "teuk_strerror", "teuk_last_error",
-    "teuk_mw_eval", "teuk_timing", "teuk_kernel_times", "teuk_fp64_peak",
+    "teuk_mw_eval", "teuk_timing", "teuk_kernel_times", "teuk_fp64_peak", "teuk_substep_noalloc",
 ]
 
 
@@ -85,6 +85,7 @@ def lib(build_if_missing: bool = True):
         L.teuk_timing.argtypes = [vp, i32]
         L.teuk_kernel_times.argtypes = [vp, dp, dp, P(i64), P(i64)]
         L.teuk_fp64_peak.argtypes = [dp]
+        L.teuk_substep_noalloc.argtypes = [vp, vp, vp, i64]
         _lib = L
     return _lib
 
