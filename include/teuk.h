@@ -115,6 +115,33 @@ int teuk_info(teuk_t h, int* words, int* n_r, int* n_theta, int* substeps, doubl
 /* Number of step kernels launched by this handle so far (two per Lax-Wendroff iteration). */
 int64_t teuk_kernel_launches(teuk_t h);
 
+/* Batched execution. Several problems (members) advance together in one cooperative launch
+ * per up to 200 outer steps: the paper's data-parallel decomposition of the grid over cores
+ * (Sec. 4) applied across independent problems of uneven size. In round q of an outer step
+ * every member with more than q Lax-Wendroff iterations per step does one iteration; work
+ * items of equal size (rows x theta columns) from all active members share the GPU, with a
+ * grid-wide barrier between the half-step and full-step phases. Results are bit-identical to
+ * stepping each member alone with teuk_step. Members must use the same precision and device,
+ * stay alive while the batch exists, and not be stepped by other calls meanwhile; the batch
+ * runs on the first member's stream. Observer rings of members receive one sample per outer
+ * step, as with teuk_step. */
+typedef struct teuk_batch_s* teuk_batch_t;
+int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members);
+int teuk_batch_step(teuk_batch_t b, int64_t n_outer_steps);
+/* Waits for the batch; returns TEUK_ERR_NONFINITE if any member produced Inf/NaN. */
+int teuk_batch_sync(teuk_batch_t b);
+/* Grid size of the cooperative launch, largest substep count, grid-point updates per outer
+ * step over all members, cooperative launches so far. Any pointer may be NULL. */
+int teuk_batch_info(teuk_batch_t b, int* grid_blocks, int* k_max, int64_t* points_per_outer_step,
+                    int64_t* launches);
+int teuk_batch_destroy(teuk_batch_t b);
+
+/* Autotuner: times a few Lax-Wendroff iterations for each candidate launch shape (rows of
+ * theta per thread block) on a copy of the current state, keeps the fastest for this handle,
+ * restores the state and returns the choice in *rows_per_block (may be NULL). Allocates and
+ * frees one state-sized device buffer; call it before timing-critical work. */
+int teuk_tune(teuk_t h, int* rows_per_block);
+
 /* Lax-Wendroff iterations that allocate nothing, for callers that cannot let a library
  * allocate device memory while they step (their memory belongs to a pool of their own, or
  * they cannot afford cudaMalloc/cudaFree, which may synchronise the whole device). The paper
@@ -150,7 +177,8 @@ const char* teuk_strerror(int code);
 const char* teuk_last_error(teuk_t h);
 
 /* Multi-word arithmetic self-test: applies op (0 add, 1 sub, 2 mul, 3 div, 4 sqrt, 5 exp,
- * 6 log, 7 dot-accumulate a*b + out) elementwise to n values of precision w, on the host
+ * 6 log, 7 dot-accumulate a*b + out, 8 out[t] + sum_{q<11} a[t+q] b[t+q] (indices mod n) through
+ * one accumulator) elementwise to n values of precision w, on the host
  * (device = 0) or the current CUDA device (device = 1). a, b, out: [w][n] host arrays. */
 int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out,
                  int64_t n);

@@ -28,14 +28,16 @@ def _nvcc() -> str:
 
 
 def _sources():
-    units = [("teuk_capi", "teuk_capi.cu", []), ("teuk_noalloc", "teuk_noalloc.cu", [])]
+    units = [("teuk_capi", "teuk_capi.cu", []), ("teuk_noalloc", "teuk_noalloc.cu", []),
+             ("teuk_batch", "teuk_batch.cu", [])]
     for w in (1, 2, 4):
         units.append((f"teuk_w{w}", "teuk_prec.cu", [f"-DTEUK_WORDS={w}"]))
     return units
 
 
 def _inputs_mtime() -> float:
-    files = [os.path.join(CSRC, f) for f in HEADERS + ["teuk_capi.cu", "teuk_prec.cu", "teuk_noalloc.cu"]]
+    files = [os.path.join(CSRC, f) for f in HEADERS + ["teuk_capi.cu", "teuk_prec.cu", "teuk_noalloc.cu",
+                                                          "teuk_batch.cu"]]
     files.append(os.path.join(ROOT, "include", "teuk.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)

@@ -88,19 +88,47 @@ MW_HD void two_prod(double a, double b, double& p, double& e) {
 // identical to two_sum for finite operands.
 MW_HD void two_sum_ord(double a, double b, double& s, double& e) {
 #if defined(__CUDA_ARCH__)
-  const long long ia = __double_as_longlong(a) & 0x7fffffffffffffffLL;
-  const long long ib = __double_as_longlong(b) & 0x7fffffffffffffffLL;
+  // The ordering is done with an explicit predicated select so that the compiler cannot
+  // move the select behind the additions (it would then form both error terms).
+  const unsigned long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
+  unsigned long long hb, lb;
+  asm("{\n\t.reg .pred p;\n\t"
+      "setp.gt.u64 p, %2, %3;\n\t"
+      "selp.b64 %0, %5, %4, p;\n\t"
+      "selp.b64 %1, %4, %5, p;\n\t}"
+      : "=l"(hb), "=l"(lb)
+      : "l"(bb & 0x7fffffffffffffffULL), "l"(ab & 0x7fffffffffffffffULL), "l"(ab), "l"(bb));
+  fast_two_sum(__longlong_as_double(hb), __longlong_as_double(lb), s, e);
 #else
   long long ia, ib;
   std::memcpy(&ia, &a, 8);
   std::memcpy(&ib, &b, 8);
   ia &= 0x7fffffffffffffffLL;
   ib &= 0x7fffffffffffffffLL;
-#endif
   const bool swap = ib > ia;
   const double hi = swap ? b : a;
   const double lo = swap ? a : b;
   fast_two_sum(hi, lo, s, e);
+#endif
+}
+
+// a - b as two_sum_ord(a, -b), with the sign of b flipped on the integer side so that the
+// negation costs no FP64 operation.
+MW_HD void two_diff_ord(double a, double b, double& s, double& e) {
+#if defined(__CUDA_ARCH__)
+  const unsigned long long ab = __double_as_longlong(a);
+  const unsigned long long nb = __double_as_longlong(b) ^ 0x8000000000000000ULL;
+  unsigned long long hb, lb;
+  asm("{\n\t.reg .pred p;\n\t"
+      "setp.gt.u64 p, %2, %3;\n\t"
+      "selp.b64 %0, %5, %4, p;\n\t"
+      "selp.b64 %1, %4, %5, p;\n\t}"
+      : "=l"(hb), "=l"(lb)
+      : "l"(nb & 0x7fffffffffffffffULL), "l"(ab & 0x7fffffffffffffffULL), "l"(ab), "l"(nb));
+  fast_two_sum(__longlong_as_double(hb), __longlong_as_double(lb), s, e);
+#else
+  two_sum_ord(a, -b, s, e);
+#endif
 }
 
 // ---------------------------------------------------------------------------------------
@@ -129,6 +157,19 @@ MW_HD dd dd_add_accurate(dd a, dd b) {
   double sh, sl, th, tl;
   two_sum_ord(a.h, b.h, sh, sl);
   two_sum_ord(a.l, b.l, th, tl);
+  const double c = add_(sl, th);
+  double vh, vl;
+  fast_two_sum(sh, c, vh, vl);
+  const double w = add_(tl, vl);
+  dd r;
+  fast_two_sum(vh, w, r.h, r.l);
+  return r;
+}
+// a - b by JMP17 Algorithm 6 with the subtractions folded into the ordered TwoSums.
+MW_HD dd dd_sub_accurate(dd a, dd b) {
+  double sh, sl, th, tl;
+  two_diff_ord(a.h, b.h, sh, sl);
+  two_diff_ord(a.l, b.l, th, tl);
   const double c = add_(sl, th);
   double vh, vl;
   fast_two_sum(sh, c, vh, vl);

@@ -1,5 +1,6 @@
 // C ABI of the teuk library (include/teuk.h): argument checking, device memory, the
 // per-outer-step launch sequence and host <-> device transfers.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -377,6 +378,53 @@ int teuk_get_tortoise(teuk_t h, int which, double* x_out) {
   return TEUK_OK;
 }
 
+int teuk_tune(teuk_t h, int* rows_per_block) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  const size_t n = (size_t)4 * h->W * h->n_r * h->pitch;
+  double* saved = nullptr;
+  unsigned int status = 0;
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  TEUK_CUDA(h, cudaMemcpy(&status, h->status, sizeof(status), cudaMemcpyDeviceToHost));
+  TEUK_CUDA(h, cudaMalloc(&saved, n * sizeof(double)));
+  cudaMemcpyAsync(saved, h->u, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  const bool timing = h->timing;
+  h->timing = false;
+  const int64_t launches = h->launches;
+  const int tx = std::min(256, ((h->n_th + 31) / 32) * 32);
+  int best = 0;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = TEUK_OK;
+  for (int ty = 1; ty <= 8 && tx * ty <= 256; ty *= 2) {
+    h->rows_per_block = ty;
+    if ((rc = dispatch_substep(h, false, 0)) != TEUK_OK) break;  // warm-up
+    cudaEventRecord(e0, h->stream);
+    for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rc != TEUK_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = ty;
+    }
+  }
+  cudaMemcpyAsync(h->u, saved, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(h->status, &status, sizeof(status), cudaMemcpyHostToDevice, h->stream);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(saved);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->timing = timing;
+  h->launches = launches;
+  h->rows_per_block = best;
+  if (rows_per_block) *rows_per_block = best;
+  return rc;
+}
+
 int teuk_timing(teuk_t h, int enable) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   drain_timing(h);
@@ -429,7 +477,7 @@ int teuk_fp64_peak(double* ops_per_second) {
 }
 
 int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out, int64_t n) {
-  if (!a || !b || !out || n < 0 || op < 0 || op > 7) return TEUK_ERR_INVALID_ARG;
+  if (!a || !b || !out || n < 0 || op < 0 || op > 8) return TEUK_ERR_INVALID_ARG;
   switch (words) {
     case 1: return teuk::mw_eval_w1(op, device, a, b, out, n);
     case 2: return teuk::mw_eval_w2(op, device, a, b, out, n);

@@ -15,6 +15,7 @@ struct teuk_s {
   int s = 0, m = 0;
   teuk_grid grid{};
   int W = 1;            // words per real
+  int rows_per_block = 0;  // step-kernel launch shape: rows of theta per block (0: default)
   int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;
   double dt_outer = 0;  // leading word of the outer step
   int device = 0;

@@ -6,6 +6,7 @@
 // so every warp access along theta is one coalesced 128-byte line per word plane.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "mw_func.cuh"
@@ -58,7 +59,7 @@ __host__ __device__ __forceinline__ double v_sub(double a, double b) { return a 
 __host__ __device__ __forceinline__ double v_half(double a) { return 0.5 * a; }
 __host__ __device__ __forceinline__ double v_neg(double a) { return -a; }
 __host__ __device__ __forceinline__ mw::dd v_add(mw::dd a, mw::dd b) { return mw::dd_add_accurate(a, b); }
-__host__ __device__ __forceinline__ mw::dd v_sub(mw::dd a, mw::dd b) { return mw::dd_add_accurate(a, mw::dd_neg(b)); }
+__host__ __device__ __forceinline__ mw::dd v_sub(mw::dd a, mw::dd b) { return mw::dd_sub_accurate(a, b); }
 __host__ __device__ __forceinline__ mw::dd v_half(mw::dd a) { return mw::dd_scale2(a, 0.5); }
 __host__ __device__ __forceinline__ mw::dd v_neg(mw::dd a) { return mw::dd_neg(a); }
 __host__ __device__ __forceinline__ mw::qd v_add(mw::qd a, mw::qd b) { return mw::qd_add(a, b); }
@@ -97,11 +98,54 @@ template <> struct Acc<mw::dd> {
     return r;
   }
 };
+// qd: the product c v of two quad-doubles is split by order of magnitude (c_i v_j is of
+// order i + j): order-0..2 products are formed exactly by TwoProd, order-3 products rounded,
+// higher orders dropped (as in HLB01's multiplication). Each order has its own running sum;
+// every TwoSum into level k sends its exact error to level k + 1, level 3 is summed plainly,
+// and one renormalisation at the end turns the four levels into a quad-double. The result
+// equals the quad-double dot product to about 2^-200 of sum |c_k v_k|, at ~70 FP64
+// operations per term instead of a quad-double multiply plus add (~168).
 template <> struct Acc<mw::qd> {
-  mw::qd s;
-  __host__ __device__ __forceinline__ explicit Acc(mw::qd x0) : s(x0) {}
-  __host__ __device__ __forceinline__ void mac(mw::qd c, mw::qd v) { s = mw::qd_add(s, mw::qd_mul(c, v)); }
-  __host__ __device__ __forceinline__ mw::qd get() const { return s; }
+  double l0, l1, l2, l3;
+  __host__ __device__ __forceinline__ explicit Acc(mw::qd x0) : l0(x0.x0), l1(x0.x1), l2(x0.x2), l3(x0.x3) {}
+  __host__ __device__ __forceinline__ void mac(mw::qd c, mw::qd v) {
+    using namespace mw;
+    double p00, e00, p01, e01, p10, e10, p02, e02, p11, e11, p20, e20, t;
+    two_prod(c.x0, v.x0, p00, e00);
+    two_prod(c.x0, v.x1, p01, e01);
+    two_prod(c.x1, v.x0, p10, e10);
+    two_prod(c.x0, v.x2, p02, e02);
+    two_prod(c.x1, v.x1, p11, e11);
+    two_prod(c.x2, v.x0, p20, e20);
+    // level 0
+    two_sum_ord(l0, p00, l0, t);
+    // level 1: t, e00, p01, p10
+    double q0, q1, q2, q3;
+    two_sum_ord(l1, t, l1, q0);
+    two_sum_ord(l1, e00, l1, q1);
+    two_sum_ord(l1, p01, l1, q2);
+    two_sum_ord(l1, p10, l1, q3);
+    // level 2: q0..q3, e01, e10, p02, p11, p20
+    double r0, r1, r2, r3, r4, r5, r6, r7, r8;
+    two_sum_ord(l2, q0, l2, r0);
+    two_sum_ord(l2, q1, l2, r1);
+    two_sum_ord(l2, q2, l2, r2);
+    two_sum_ord(l2, q3, l2, r3);
+    two_sum_ord(l2, e01, l2, r4);
+    two_sum_ord(l2, e10, l2, r5);
+    two_sum_ord(l2, p02, l2, r6);
+    two_sum_ord(l2, p11, l2, r7);
+    two_sum_ord(l2, p20, l2, r8);
+    // level 3: rounded
+    double s3 = add_(add_(add_(r0, r1), add_(r2, r3)), add_(add_(r4, r5), add_(r6, r7)));
+    s3 = add_(s3, add_(r8, add_(add_(e02, e11), e20)));
+    s3 = fma_(c.x0, v.x3, s3);
+    s3 = fma_(c.x1, v.x2, s3);
+    s3 = fma_(c.x2, v.x1, s3);
+    s3 = fma_(c.x3, v.x0, s3);
+    l3 = add_(l3, s3);
+  }
+  __host__ __device__ __forceinline__ mw::qd get() const { return mw::qd_renorm(l0, l1, l2, l3, 0.0); }
 };
 
 // ---- kernel argument blocks ---------------------------------------------------------------
@@ -373,6 +417,34 @@ __device__ __forceinline__ void put_ghosted(double* srow, int gstride, int n_th,
   if (j >= n_th - radius) st_r(srow + (2 * n_th - 1 - j) + radius, gstride, pv);  // column 2n-1-j
 }
 
+__device__ __forceinline__ bool nonfinite(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+}
+__device__ __forceinline__ double lead_of(double x) { return x; }
+__device__ __forceinline__ double lead_of(mw::dd x) { return x.h; }
+__device__ __forceinline__ double lead_of(mw::qd x) { return x.x0; }
+
+// ---- per-row bodies, shared by the single-problem kernels and the batched kernel ----------
+// A row is handled by TX threads along theta (thread tx takes columns tx, tx + TX, ...); sR
+// and sI are that row's ghosted shared-memory buffers for the real and imaginary parts.
+
+// Eq. lw1, first phase at half node h: s_Phi = Phi_{h+1} + Phi_h into the ghosted row.
+template <int W>
+__device__ __forceinline__ void half_row_prep(const StepArgs& a, int h, int tx, int TX, double* sR, double* sI) {
+  using R = typename RT<W>::T;
+  const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
+  const int gstride = n_th + 2 * rad;
+  const size_t ws = (size_t)n_r * pitch;
+  const double* u = a.u_in;
+  for (int j = tx; j < n_th; j += TX) {
+    const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
+    const R sPR = v_add(ld_s<R>(u + 0 * W * ws + i1, ws), ld_s<R>(u + 0 * W * ws + i0, ws));
+    const R sPI = v_add(ld_s<R>(u + 1 * W * ws + i1, ws), ld_s<R>(u + 1 * W * ws + i0, ws));
+    put_ghosted<R>(sR, gstride, n_th, rad, a.g.parity, j, sPR);
+    put_ghosted<R>(sI, gstride, n_th, rad, a.g.parity, j, sPI);
+  }
+}
+
 // Eq. lw1 at half nodes h = 0 .. n_r-2:
 //   u^{n+1/2}_{h} = (u_{h+1} + u_h)/2 - dt/2 [D (u_{h+1} - u_h)/dr - S(ubar, du)],
 // written with the folded tables and s = u_{h+1} + u_h, d = u_{h+1} - u_h:
@@ -380,31 +452,16 @@ __device__ __forceinline__ void put_ghosted(double* srow, int gstride, int n_th,
 //   Pi_h,R = H3 s_PiR + H4 s_PiI + H0 d_PiR + H1 d_PhiR + H2 d_PhiI + H5 L(s_Phi)_R + H6 s_PhiR - H7 s_PhiI,
 //   Pi_h,I = H3 s_PiI - H4 s_PiR + H0 d_PiI + H1 d_PhiI - H2 d_PhiR + H5 L(s_Phi)_I + H6 s_PhiI + H7 s_PhiR.
 template <int W>
-__global__ void __launch_bounds__(256) half_kernel(StepArgs a) {
+__device__ __forceinline__ void half_row_out(const StepArgs& a, int h, int tx, int TX, const double* sR,
+                                             const double* sI) {
   using R = typename RT<W>::T;
-  extern __shared__ double sm[];
   const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
-  const int gstride = n_th + 2 * rad;             // one ghosted word row
-  const int h = blockIdx.x * blockDim.y + threadIdx.y;
-  const bool ok = h < n_r - 1;
-  double* sR = sm + (size_t)threadIdx.y * 2 * W * gstride;
-  double* sI = sR + (size_t)W * gstride;
-  const size_t ws = (size_t)n_r * pitch;          // state word-plane stride
-  const size_t hs = (size_t)(n_r - 1) * pitch;    // half word-plane stride
+  const int gstride = n_th + 2 * rad;
+  const size_t ws = (size_t)n_r * pitch;
+  const size_t hs = (size_t)(n_r - 1) * pitch;
   const double* u = a.u_in;
-  if (ok) {
-    for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
-      const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
-      const R sPR = v_add(ld_s<R>(u + 0 * W * ws + i1, ws), ld_s<R>(u + 0 * W * ws + i0, ws));
-      const R sPI = v_add(ld_s<R>(u + 1 * W * ws + i1, ws), ld_s<R>(u + 1 * W * ws + i0, ws));
-      put_ghosted<R>(sR, gstride, n_th, rad, a.g.parity, j, sPR);
-      put_ghosted<R>(sI, gstride, n_th, rad, a.g.parity, j, sPI);
-    }
-  }
-  __syncthreads();
-  if (!ok) return;
   const R h4 = from_words<R>(a.h4);
-  for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+  for (int j = tx; j < n_th; j += TX) {
     const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
     const R uPR0 = ld_s<R>(u + 0 * W * ws + i0, ws), uPR1 = ld_s<R>(u + 0 * W * ws + i1, ws);
     const R uPI0 = ld_s<R>(u + 1 * W * ws + i0, ws), uPI1 = ld_s<R>(u + 1 * W * ws + i1, ws);
@@ -440,12 +497,22 @@ __global__ void __launch_bounds__(256) half_kernel(StepArgs a) {
   }
 }
 
-__device__ __forceinline__ bool nonfinite(double x) {
-  return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+// Eq. lw2, first phase at node i: s_Phi = Phi_{i+1/2} + Phi_{i-1/2} into the ghosted row.
+template <int W>
+__device__ __forceinline__ void full_row_prep(const StepArgs& a, int i, int tx, int TX, double* sR, double* sI) {
+  using R = typename RT<W>::T;
+  const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
+  const int gstride = n_th + 2 * rad;
+  const size_t hs = (size_t)(n_r - 1) * pitch;
+  const double* uh = a.uh;
+  for (int j = tx; j < n_th; j += TX) {
+    const size_t p = (size_t)i * pitch + j, m = p - pitch;  // half rows i+1/2 and i-1/2
+    const R sPR = v_add(ld_s<R>(uh + 0 * W * hs + p, hs), ld_s<R>(uh + 0 * W * hs + m, hs));
+    const R sPI = v_add(ld_s<R>(uh + 1 * W * hs + p, hs), ld_s<R>(uh + 1 * W * hs + m, hs));
+    put_ghosted<R>(sR, gstride, n_th, rad, a.g.parity, j, sPR);
+    put_ghosted<R>(sI, gstride, n_th, rad, a.g.parity, j, sPI);
+  }
 }
-__device__ __forceinline__ double lead_of(double x) { return x; }
-__device__ __forceinline__ double lead_of(mw::dd x) { return x.h; }
-__device__ __forceinline__ double lead_of(mw::qd x) { return x.x0; }
 
 // Eq. lw2 at nodes i = 1 .. n_r-2 (rows 0 and n_r-1 stay zero, Sec. 3.B):
 //   u^{n+1}_i = u^n_i - dt [D (u_{i+1/2} - u_{i-1/2})/dr - S(ubar, du)],
@@ -453,33 +520,20 @@ __device__ __forceinline__ double lead_of(mw::qd x) { return x.x0; }
 //   Phi'  = Phi - N0 d_Phi + (h/2) s_Pi,
 //   Pi'_R = Pi_R + N0 d_PiR + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L(s_Phi)_R + N6 s_PhiR - N7 s_PhiI,
 //   Pi'_I = Pi_I + N0 d_PiI + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L(s_Phi)_I + N6 s_PhiI + N7 s_PhiR.
+// Returns true if a non-finite value was produced. `slot` is the observer ring slot to fill
+// (negative: none).
 template <int W>
-__global__ void __launch_bounds__(256) full_kernel(StepArgs a) {
+__device__ __forceinline__ bool full_row_out(const StepArgs& a, int i, int tx, int TX, const double* sR,
+                                             const double* sI, long long slot) {
   using R = typename RT<W>::T;
-  extern __shared__ double sm[];
   const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
   const int gstride = n_th + 2 * rad;
-  const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
-  const bool ok = i < n_r - 1;
-  double* sR = sm + (size_t)threadIdx.y * 2 * W * gstride;
-  double* sI = sR + (size_t)W * gstride;
   const size_t ws = (size_t)n_r * pitch;
   const size_t hs = (size_t)(n_r - 1) * pitch;
   const double* uh = a.uh;
-  if (ok) {
-    for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
-      const size_t p = (size_t)i * pitch + j, m = p - pitch;  // half rows i+1/2 and i-1/2
-      const R sPR = v_add(ld_s<R>(uh + 0 * W * hs + p, hs), ld_s<R>(uh + 0 * W * hs + m, hs));
-      const R sPI = v_add(ld_s<R>(uh + 1 * W * hs + p, hs), ld_s<R>(uh + 1 * W * hs + m, hs));
-      put_ghosted<R>(sR, gstride, n_th, rad, a.g.parity, j, sPR);
-      put_ghosted<R>(sI, gstride, n_th, rad, a.g.parity, j, sPI);
-    }
-  }
-  __syncthreads();
-  if (!ok) return;
   const R h2 = from_words<R>(a.h2);
   bool bad = false;
-  for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+  for (int j = tx; j < n_th; j += TX) {
     const size_t p = (size_t)i * pitch + j, m = p - pitch;
     const R hPR1 = ld_s<R>(uh + 0 * W * hs + p, hs), hPR0 = ld_s<R>(uh + 0 * W * hs + m, hs);
     const R hPI1 = ld_s<R>(uh + 1 * W * hs + p, hs), hPI0 = ld_s<R>(uh + 1 * W * hs + m, hs);
@@ -516,13 +570,108 @@ __global__ void __launch_bounds__(256) full_kernel(StepArgs a) {
     st_r(a.u_out + 2 * W * ws + ci, ws, oQR);
     st_r(a.u_out + 3 * W * ws + ci, ws, oQI);
     bad |= nonfinite(lead_of(oPR)) | nonfinite(lead_of(oPI)) | nonfinite(lead_of(oQR)) | nonfinite(lead_of(oQI));
-    if (a.record && i == a.i_obs) {
-      double* slot = a.ring + (size_t)a.ring_slot * 2 * W * n_th;
-      st_r(slot + 0 * W * n_th + j, n_th, oPR);
-      st_r(slot + 1 * W * n_th + j, n_th, oPI);
+    if (slot >= 0 && i == a.i_obs) {
+      double* dst = a.ring + (size_t)slot * 2 * W * n_th;
+      st_r(dst + 0 * W * n_th + j, n_th, oPR);
+      st_r(dst + 1 * W * n_th + j, n_th, oPI);
     }
   }
-  if (bad) atomicOr(a.status, 1u);
+  return bad;
+}
+
+// ---- single-problem kernels: blockDim.y rows per block, blockDim.x threads along theta ------
+template <int W>
+__global__ void __launch_bounds__(256) half_kernel(StepArgs a) {
+  extern __shared__ double sm[];
+  const int gstride = a.g.n_th + 2 * a.radius;
+  const int h = blockIdx.x * blockDim.y + threadIdx.y;
+  const bool ok = h < a.g.n_r - 1;
+  double* sR = sm + (size_t)threadIdx.y * 2 * W * gstride;
+  double* sI = sR + (size_t)W * gstride;
+  if (ok) half_row_prep<W>(a, h, threadIdx.x, blockDim.x, sR, sI);
+  __syncthreads();
+  if (ok) half_row_out<W>(a, h, threadIdx.x, blockDim.x, sR, sI);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) full_kernel(StepArgs a) {
+  extern __shared__ double sm[];
+  const int gstride = a.g.n_th + 2 * a.radius;
+  const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
+  const bool ok = i < a.g.n_r - 1;
+  double* sR = sm + (size_t)threadIdx.y * 2 * W * gstride;
+  double* sI = sR + (size_t)W * gstride;
+  if (ok) full_row_prep<W>(a, i, threadIdx.x, blockDim.x, sR, sI);
+  __syncthreads();
+  if (!ok) return;
+  const long long slot = a.record ? a.ring_slot : -1;
+  if (full_row_out<W>(a, i, threadIdx.x, blockDim.x, sR, sI, slot)) atomicOr(a.status, 1u);
+}
+
+// ---- batched execution: many problems of uneven size in one cooperative launch ------------
+struct BatchMember {
+  StepArgs a;            // the member's buffers (state updated in place, scratch, tables)
+  int k;                 // Lax-Wendroff iterations per outer step
+  int tx;                // threads along theta per row
+  int rows;              // rows per work item (tx * rows <= blockDim.x)
+  int item_begin;        // first work item of this member
+  long long ring_base;   // samples already in the member's observer ring
+  long long ring_cap;    // ring capacity, 0 = no observer
+};
+
+struct BatchArgs {
+  const BatchMember* m;     // sorted by k, descending
+  const int* item_member;   // member of each work item
+  const int* active_items;  // [k_max]: number of items whose member has k > q (a prefix)
+  int k_max;
+  int n_outer;
+};
+
+// Outer steps of all members: in round q = 0 .. k_max-1 every member with k > q performs one
+// Lax-Wendroff iteration, as a half-step phase over all their work items, a grid-wide
+// barrier, a full-step phase, another barrier. Work items hold the same number of grid points
+// (rows x theta = blockDim.x), so the grid-stride loops stay balanced across uneven members.
+template <int W>
+__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs b) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double sm[];
+  for (int s = 0; s < b.n_outer; ++s) {
+    for (int q = 0; q < b.k_max; ++q) {
+      const int n_act = b.active_items[q];
+      for (int it = blockIdx.x; it < n_act; it += gridDim.x) {
+        const BatchMember& M = b.m[b.item_member[it]];
+        const int tx = threadIdx.x % M.tx, ty = threadIdx.x / M.tx;
+        const int h = (it - M.item_begin) * M.rows + ty;
+        const bool ok = ty < M.rows && h < M.a.g.n_r - 1;
+        const int gstride = M.a.g.n_th + 2 * M.a.radius;
+        double* sR = sm + (size_t)(ty < M.rows ? ty : 0) * 2 * W * gstride;
+        double* sI = sR + (size_t)W * gstride;
+        if (ok) half_row_prep<W>(M.a, h, tx, M.tx, sR, sI);
+        __syncthreads();
+        if (ok) half_row_out<W>(M.a, h, tx, M.tx, sR, sI);
+        __syncthreads();
+      }
+      grid.sync();
+      for (int it = blockIdx.x; it < n_act; it += gridDim.x) {
+        const BatchMember& M = b.m[b.item_member[it]];
+        const int tx = threadIdx.x % M.tx, ty = threadIdx.x / M.tx;
+        const int i = 1 + (it - M.item_begin) * M.rows + ty;
+        const bool ok = ty < M.rows && i < M.a.g.n_r - 1;
+        const int gstride = M.a.g.n_th + 2 * M.a.radius;
+        double* sR = sm + (size_t)(ty < M.rows ? ty : 0) * 2 * W * gstride;
+        double* sI = sR + (size_t)W * gstride;
+        if (ok) full_row_prep<W>(M.a, i, tx, M.tx, sR, sI);
+        __syncthreads();
+        if (ok) {
+          const long long slot = (q == M.k - 1 && M.ring_cap > 0) ? (M.ring_base + s) % M.ring_cap : -1;
+          if (full_row_out<W>(M.a, i, tx, M.tx, sR, sI, slot)) atomicOr(M.a.status, 1u);
+        }
+        __syncthreads();
+      }
+      grid.sync();
+    }
+  }
 }
 
 }  // namespace teuk

@@ -170,12 +170,14 @@ int pulse_impl(teuk_s* h, double center, double width, double ar, double ai, int
   return TEUK_OK;
 }
 
-// Launch shape of the step kernels: threads along theta (x), rows (y), ~256 threads.
-void step_shape(int n_th, dim3& blk) {
-  int tx = ((n_th + 31) / 32) * 32;
+// Launch shape of the step kernels: threads along theta (x, one warp multiple up to 256) and
+// rows per block (y). Default: about 128 threads per block, so that the last wave of blocks
+// still spreads over every SM; teuk_tune picks the fastest rows-per-block instead.
+void step_shape(const teuk_s* h, dim3& blk) {
+  int tx = ((h->n_th + 31) / 32) * 32;
   if (tx > 256) tx = 256;
-  int ty = 256 / tx;
-  if (ty < 1) ty = 1;
+  int ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
+  while (ty > 1 && tx * ty > 256) ty /= 2;
   blk = dim3(tx, ty);
 }
 
@@ -197,7 +199,7 @@ int substep_impl(teuk_s* h, bool record, int64_t slot) {
   sa.ring = h->ring;
   sa.status = h->status;
   dim3 blk;
-  step_shape(h->n_th, blk);
+  step_shape(h, blk);
   const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
   const int nh = h->n_r - 1, nf = h->n_r - 2;
   if (smem > 48 * 1024) {  // above the default dynamic limit (quad-double, n_theta > 700)
@@ -236,7 +238,7 @@ int substep_buffers_impl(teuk_s* h, const double* u_in, double* u_out, double* s
   sa.ring = nullptr;
   sa.status = h->status;
   dim3 blk;
-  step_shape(h->n_th, blk);
+  step_shape(h, blk);
   const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
   const int nh = h->n_r - 1, nf = h->n_r - 2;
   if (smem > 48 * 1024) {
@@ -269,18 +271,49 @@ __host__ __device__ RR apply_op(int op, RR x, RR y, RR acc, RR ln2) {
   }
 }
 
-__global__ void mw_eval_kernel(int op, const double* a, const double* b, double* out, int64_t n, R ln2) {
+// op 8: out[t] + sum_{q < 11} a[(t+q) % n] b[(t+q) % n] through one accumulator (the length
+// of the theta stencil), without intermediate renormalisation.
+__host__ __device__ R dot11(const double* a, const double* b, const double* out, int64_t n, int64_t t) {
+  double wo[4] = {0, 0, 0, 0};
+  for (int k = 0; k < W; ++k) wo[k] = out[k * n + t];
+  Acc<R> acc(from_words<R>(wo));
+  for (int q = 0; q < 11; ++q) {
+    const int64_t u = (t + q) % n;
+    double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0};
+    for (int k = 0; k < W; ++k) { wa[k] = a[k * n + u]; wb[k] = b[k * n + u]; }
+    acc.mac(from_words<R>(wa), from_words<R>(wb));
+  }
+  return acc.get();
+}
+
+__global__ void mw_eval_kernel(int op, const double* a, const double* b, double* out, double* res, int64_t n,
+                               R ln2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0};
+  if (op == 8) {
+    to_words(dot11(a, b, out, n, t), wo);
+    for (int k = 0; k < W; ++k) res[k * n + t] = wo[k];
+    return;
+  }
   for (int k = 0; k < W; ++k) { wa[k] = a[k * n + t]; wb[k] = b[k * n + t]; wo[k] = out[k * n + t]; }
   const R r = apply_op<R>(op, from_words<R>(wa), from_words<R>(wb), from_words<R>(wo), ln2);
   to_words(r, wo);
-  for (int k = 0; k < W; ++k) out[k * n + t] = wo[k];
+  for (int k = 0; k < W; ++k) res[k * n + t] = wo[k];
 }
 
 int mw_eval_impl(int op, int device, const double* a, const double* b, double* out, int64_t n) {
   const R ln2 = r_ln2<R>();
+  if (!device && op == 8) {
+    std::vector<double> res((size_t)W * n);
+    for (int64_t t = 0; t < n; ++t) {
+      double wo[4];
+      to_words(dot11(a, b, out, n, t), wo);
+      for (int k = 0; k < W; ++k) res[k * n + t] = wo[k];
+    }
+    std::memcpy(out, res.data(), res.size() * sizeof(double));
+    return TEUK_OK;
+  }
   if (!device) {
     for (int64_t t = 0; t < n; ++t) {
       double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0};
@@ -291,19 +324,21 @@ int mw_eval_impl(int op, int device, const double* a, const double* b, double* o
     }
     return TEUK_OK;
   }
-  double *da = nullptr, *db = nullptr, *dout = nullptr;
+  double *da = nullptr, *db = nullptr, *dout = nullptr, *dres = nullptr;
   const size_t bytes = (size_t)W * n * sizeof(double);
   TEUK_CUDA(nullptr, cudaMalloc(&da, bytes));
   TEUK_CUDA(nullptr, cudaMalloc(&db, bytes));
   TEUK_CUDA(nullptr, cudaMalloc(&dout, bytes));
+  TEUK_CUDA(nullptr, cudaMalloc(&dres, bytes));
   cudaMemcpy(da, a, bytes, cudaMemcpyHostToDevice);
   cudaMemcpy(db, b, bytes, cudaMemcpyHostToDevice);
   cudaMemcpy(dout, out, bytes, cudaMemcpyHostToDevice);
-  mw_eval_kernel<<<(unsigned)((n + 127) / 128), 128>>>(op, da, db, dout, n, ln2);
-  cudaError_t e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  mw_eval_kernel<<<(unsigned)((n + 127) / 128), 128>>>(op, da, db, dout, dres, n, ln2);
+  cudaError_t e = cudaMemcpy(out, dres, bytes, cudaMemcpyDeviceToHost);
   cudaFree(da);
   cudaFree(db);
   cudaFree(dout);
+  cudaFree(dres);
   return e == cudaSuccess ? TEUK_OK : TEUK_ERR_CUDA;
 }
 

@@ -25,6 +25,8 @@ SYMBOLS = [
     "teuk_get_state", "teuk_set_state", "teuk_get_state_device", "teuk_get_coeffs",
     "teuk_get_tortoise", "teuk_info", "teuk_kernel_launches", "teuk_strerror", "teuk_last_error",
     "teuk_mw_eval", "teuk_timing", "teuk_kernel_times", "teuk_fp64_peak", "teuk_substep_noalloc",
+    "teuk_tune", "teuk_batch_create", "teuk_batch_step", "teuk_batch_sync", "teuk_batch_info",
+    "teuk_batch_destroy",
 ]
 
 
@@ -86,6 +88,12 @@ def lib(build_if_missing: bool = True):
         L.teuk_kernel_times.argtypes = [vp, dp, dp, P(i64), P(i64)]
         L.teuk_fp64_peak.argtypes = [dp]
         L.teuk_substep_noalloc.argtypes = [vp, vp, vp, i64]
+        L.teuk_tune.argtypes = [vp, P(i32)]
+        L.teuk_batch_create.argtypes = [P(vp), P(vp), i32]
+        L.teuk_batch_step.argtypes = [vp, i64]
+        L.teuk_batch_sync.argtypes = [vp]
+        L.teuk_batch_info.argtypes = [vp, P(i32), P(i32), P(i64), P(i64)]
+        L.teuk_batch_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -232,6 +240,12 @@ class Teuk:
                                ctypes.byref(k), ctypes.byref(dt)), self._h)
         return dict(words=w.value, n_r=nr.value, n_theta=nt.value, substeps=k.value, dt=dt.value)
 
+    def tune(self) -> int:
+        """Pick the fastest step-kernel launch shape (rows per block); state is preserved."""
+        r = ctypes.c_int()
+        _check(lib().teuk_tune(self._h, ctypes.byref(r)), self._h)
+        return r.value
+
     def timing(self, enable=True):
         _check(lib().teuk_timing(self._h, 1 if enable else 0), self._h)
 
@@ -246,6 +260,45 @@ class Teuk:
     @property
     def kernel_launches(self) -> int:
         return int(lib().teuk_kernel_launches(self._h))
+
+
+class Batch:
+    """Several Teuk problems advanced together in one cooperative launch per 200 steps."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        h = ctypes.c_void_p()
+        _check(lib().teuk_batch_create(ctypes.byref(h), arr, len(self.members)))
+        self._h = h
+
+    def step(self, n_outer=1):
+        rc = lib().teuk_batch_step(self._h, int(n_outer))
+        if rc != OK:
+            raise TeukError(rc, lib().teuk_strerror(rc).decode())
+
+    def sync(self):
+        rc = lib().teuk_batch_sync(self._h)
+        if rc != OK:
+            raise TeukError(rc, lib().teuk_strerror(rc).decode())
+
+    def info(self):
+        g, k = ctypes.c_int(), ctypes.c_int()
+        pts, nl = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().teuk_batch_info(self._h, ctypes.byref(g), ctypes.byref(k), ctypes.byref(pts),
+                                     ctypes.byref(nl)))
+        return dict(grid=g.value, k_max=k.value, points_per_outer_step=pts.value, launches=nl.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().teuk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fp64_peak() -> float:

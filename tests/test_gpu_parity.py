@@ -232,3 +232,91 @@ def test_nonfinite_guard_reports_error():
     with pytest.raises(teuk.TeukError) as e:
         g.sync()
     assert e.value.code == teuk.ERR_NONFINITE
+
+
+@pytest.mark.parametrize("W", [1, 2])
+def test_autotuner_keeps_state_and_results(W):
+    """teuk_tune times launch shapes on a copy of the state: the state is unchanged and the
+    results of any launch shape are identical bit for bit (same arithmetic per point)."""
+    p = small(n_r=61, n_theta=40)
+    g1 = teuk.Teuk(precision=W, **p)
+    g2 = teuk.Teuk(precision=W, **p)
+    for g in (g1, g2):
+        g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+    before = g2.get_state()
+    rows = g2.tune()
+    assert rows in (1, 2, 4)
+    np.testing.assert_array_equal(g2.get_state(), before)
+    g1.step(2)
+    g2.step(2)
+    np.testing.assert_array_equal(g1.get_state(), g2.get_state())
+    assert g2.kernel_launches == 2 * 2 * p["substeps"]
+
+
+@pytest.mark.parametrize("W", [2, 4])
+def test_mw_dot11_device_matches_host(W):
+    rng = np.random.default_rng(9)
+    n = 4096
+    a = np.zeros((W, n)); b = np.zeros((W, n))
+    a[0] = rng.uniform(-2, 2, n) * 1e3
+    b[0] = rng.uniform(-1, 1, n)
+    for k in range(1, W):
+        a[k] = a[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -53
+        b[k] = b[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -53
+    c = np.zeros_like(a)
+    h = teuk.mw_eval(8, W, a, b, out=c, device=False)
+    d = teuk.mw_eval(8, W, a, b, out=c, device=True)
+    np.testing.assert_array_equal(h, d)
+
+
+BATCH_MEMBERS = [
+    dict(a=0.9, s=-2, m=2, n_r=41, n_theta=24, substeps=4),
+    dict(a=0.3, s=0, m=1, n_r=77, n_theta=64, substeps=2, rstar_max=90.0),
+    dict(a=0.7, s=-1, m=-3, n_r=33, n_theta=32, substeps=7),
+    dict(a=0.5, s=-2, m=0, n_r=129, n_theta=128, substeps=1, rstar_min=-60.0),
+    dict(a=0.99, s=0, m=0, n_r=50, n_theta=40, substeps=3, theta_order=2),
+]
+
+
+def _member(W, kw):
+    p = small(**kw)
+    g = teuk.Teuk(precision=W, **p)
+    ell = max(abs(p["m"]), abs(p["s"]))
+    g.set_initial_pulse(8.0, 4.0, 0.8, 0.6, ell)
+    g.set_observer(15.0, capacity=16)
+    return g
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+def test_batch_matches_individual_bitwise(W):
+    """Uneven members (sizes, theta resolutions, spins, substeps) advanced in one cooperative
+    launch give exactly the states and waveforms of advancing each member alone."""
+    alone = [_member(W, kw) for kw in BATCH_MEMBERS]
+    batched = [_member(W, kw) for kw in BATCH_MEMBERS]
+    n = 5
+    for g in alone:
+        g.step(n)
+        g.sync()
+    b = teuk.Batch(batched)
+    b.step(n)
+    b.sync()
+    info = b.info()
+    assert info["k_max"] == 7 and info["launches"] == 1
+    for ga, gb in zip(alone, batched):
+        np.testing.assert_array_equal(ga.get_state(), gb.get_state())
+        np.testing.assert_array_equal(ga.read_waveform(), gb.read_waveform())
+    b.close()
+
+
+def test_batch_chunks_of_200_steps():
+    alone = [_member(1, kw) for kw in BATCH_MEMBERS[:2]]
+    batched = [_member(1, kw) for kw in BATCH_MEMBERS[:2]]
+    for g in alone:
+        g.step(203)
+    b = teuk.Batch(batched)
+    b.step(203)
+    b.sync()
+    assert b.info()["launches"] == 2
+    for ga, gb in zip(alone, batched):
+        np.testing.assert_array_equal(ga.get_state(), gb.get_state())
+        np.testing.assert_array_equal(ga.read_waveform(), gb.read_waveform())

@@ -127,3 +127,34 @@ def test_no_device_is_an_error_not_a_fallback():
     with pytest.raises(teuk.TeukError) as e:
         teuk.Teuk(M=1.0, a=0.5, s=-2, m=2, rstar_min=-10, rstar_max=10, n_r=16, n_theta=16)
     assert e.value.code in (teuk.ERR_NO_DEVICE, teuk.ERR_CUDA)
+
+
+@pytest.mark.parametrize("words", [2, 4])
+def test_dot11_accumulator_with_cancellation_host(words):
+    """The kernels' 11-term dot products (the theta stencil): weights of both signs and
+    magnitude ~1e3 applied to smooth data, so that the sum cancels by ~1e3; the error stays
+    at the arithmetic's level relative to sum |c_k v_k|."""
+    mpm.mp.prec = 400
+    n = 64
+    rng = np.random.default_rng(5 + words)
+    w2 = [8, -125, 1000, -6000, 42000, -73766, 42000, -6000, 1000, -125, 8]
+    a = np.zeros((words, n)); b = np.zeros((words, n))
+    av, bv = [], []
+    for t in range(n):
+        x = mpm.mpf(w2[t % 11]) / 25200 * 400 * (1 + mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** -60)
+        y = mpm.cos(mpm.mpf(t) / 17) * (1 + mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** -70)
+        for vals, arr, v in ((av, a, x), (bv, b, y)):
+            rest = v
+            for k in range(words):
+                arr[k, t] = float(rest)
+                rest -= arr[k, t]
+            vals.append(sum(mpm.mpf(float(q)) for q in arr[:, t]))
+    c = np.zeros((words, n))
+    out = teuk.mw_eval(8, words, a, b, out=c, device=False)
+    worst = 0.0
+    for t in range(n):
+        terms = [av[(t + q) % n] * bv[(t + q) % n] for q in range(11)]
+        want = sum(terms)
+        got = _words_value(out, t)
+        worst = max(worst, float(abs(got - want) / sum(abs(x) for x in terms)))
+    assert worst < BOUND[words], worst
