@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 / qd side figures")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-member batched workload")
     return ap.parse_args()
 
 
@@ -130,6 +131,64 @@ def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=Tru
     out["waveform_samples"] = int(wf.shape[0])
     g.close()
     return out
+
+
+def run_batch1(prob, words, steps, torch, teuk):
+    """One problem through the cooperative batched kernel (all iterations of `steps` outer
+    steps in one launch): the launch-bound regime of small grids."""
+    g = teuk.Teuk.from_problem(prob, precision=words)
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    b = teuk.Batch([g])
+    b.step(1)
+    b.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.sync()
+    dt = time.perf_counter() - t0
+    b.close()
+    g.close()
+    return prob.n_r * prob.n_theta * prob.substeps * steps / dt, dt / steps * 1e3
+
+
+def run_c4(torch, teuk, workloads):
+    """The 64-member double-double batch: one cooperative launch per outer step against the
+    same members stepped one at a time (CUDA graphs on), equal arithmetic (bit-identical)."""
+    members = []
+    for i in range(workloads.BATCH_SIZE):
+        p = workloads.batch_member(i)
+        g = teuk.Teuk.from_problem(p)
+        ar, ai = p.amps
+        g.set_initial_pulse(p.center, p.width, ar, ai, p.ell)
+        g.set_observer(p.rstar_obs, capacity=8)
+        members.append(g)
+    pts = sum(g.n_r * g.n_theta * g.substeps for g in members)
+    for g in members:
+        g.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in members:
+        g.step(1)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    b = teuk.Batch(members)
+    b.step(1)
+    b.sync()
+    t0 = time.perf_counter()
+    b.step(1)
+    b.sync()
+    t_bat = time.perf_counter() - t0
+    info = b.info()
+    b.close()
+    for g in members:
+        g.close()
+    return {"workload": "c4: 64 double-double members, n_r U[512,4096], n_theta {32..256}, "
+                        "m in [-4,4], s in {0,-1,-2}, a U[0,0.99], substeps 1..454 (seeds 1000+i)",
+            "updates_per_outer_step": pts,
+            "batched_updates_per_s": pts / t_bat, "one_at_a_time_updates_per_s": pts / t_seq,
+            "speedup": t_seq / t_bat, "batched_ms_per_step": t_bat * 1e3,
+            "one_at_a_time_ms_per_step": t_seq * 1e3, "grid_blocks": info["grid"]}
 
 
 def run_e2e(prob, words, steps, torch, teuk):
@@ -293,12 +352,16 @@ def main():
         e2e = run_e2e(prob, W, max(3, args.steps // 2), torch, teuk)
         variants = {}
         if not args.no_variants:
-            for name, w in (("c1", 1), ("c5", 1), ("c3", 4), ("c5", 2)):
+            for name, w, nst in (("c1", 1, 20), ("c5", 1, 2), ("c3", 4, 2), ("c5", 2, 1)):
                 p = workloads.CONFIGS[name]
-                r = run_workload(p, w, 2, 1, torch, teuk, flush, with_timing=False)
+                r = run_workload(p, w, nst, 1, torch, teuk, flush, with_timing=False)
                 variants[f"{name}/{DTYPE[w].split(' ')[0]}"] = {
-                    "updates_per_s": p.n_r * p.n_theta * p.substeps * 2 / (r["ms_total"] * 1e-3),
-                    "ms_per_step": r["ms_total"] / 2}
+                    "updates_per_s": p.n_r * p.n_theta * p.substeps * nst / (r["ms_total"] * 1e-3),
+                    "ms_per_step": r["ms_total"] / nst, "launch": "CUDA graph per outer step"}
+            ups, msps = run_batch1(workloads.CONFIGS["c1"], 1, 20, torch, teuk)
+            variants["c1/f64 batched kernel"] = {"updates_per_s": ups, "ms_per_step": msps,
+                                                 "launch": "one cooperative launch, 20 steps"}
+        batched = None if args.no_batch else run_c4(torch, teuk, workloads)
         cpu = None if args.no_cpu else cpu_baseline(prob, W)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -314,6 +377,7 @@ def main():
             "gpu_launches": res["launches"],
             "clocks": clocks,
             "per_precision": variants,
+            "batched": batched,
             "tolerance_vs_256bit_oracle": TOL[W],
         }
         print(json.dumps(out))

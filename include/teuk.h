@@ -84,6 +84,12 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
 /* Advances n outer steps (n * substeps Lax-Wendroff iterations), asynchronously on the
  * handle's stream. The observer ring (if any) gets one sample per outer step. */
 int teuk_step(teuk_t h, int64_t n_outer_steps);
+/* CUDA graphs: teuk_step captures one outer step (its 2 * substeps kernel launches and the
+ * observer bookkeeping) as a CUDA graph on first use and replays it, which removes most of
+ * the launch overhead of small problems. On by default; not used while per-kernel timing is
+ * on or when the handle runs on the legacy default stream. enable = 0 launches kernels one
+ * by one. Results are identical either way. */
+int teuk_use_graphs(teuk_t h, int enable);
 /* Advances n single Lax-Wendroff iterations of dt/substeps (no observer samples). */
 int teuk_substep(teuk_t h, int64_t n_iterations);
 /* Waits for the handle's stream; returns TEUK_ERR_NONFINITE if any Inf/NaN was produced. */

@@ -48,6 +48,8 @@ teuk::StepArgs member_args(const teuk_s* h) {
   sa.record = 0;
   sa.i_obs = h->i_obs;
   sa.ring_slot = 0;
+  sa.ring_counter = nullptr;
+  sa.ring_cap = h->ring_cap;
   sa.ring = h->ring;
   sa.status = h->status;
   return sa;

@@ -31,6 +31,8 @@ int invalid(teuk_s* h, const char* msg) {
   return TEUK_ERR_INVALID_ARG;
 }
 
+void drop_graph(teuk_s* h);
+
 void free_all(teuk_s* h) {
   double** bufs[] = {&h->u, &h->uh, &h->cn_raw, &h->ch_raw, &h->cn, &h->ch, &h->wts, &h->sin_th,
                      &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring};
@@ -40,6 +42,9 @@ void free_all(teuk_s* h) {
   }
   if (h->status) cudaFree(h->status);
   h->status = nullptr;
+  if (h->d_ring_counter) cudaFree(h->d_ring_counter);
+  h->d_ring_counter = nullptr;
+  drop_graph(h);
 }
 
 // Copies a [C][W][rows][n_th] host array to / from the pitched device layout.
@@ -75,6 +80,48 @@ __global__ void fp64_peak_kernel(double* out, double a, double b, int iters) {
     x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+// One more sample in the observer ring (launched after the last iteration of a captured
+// outer step; the kernels read the slot from this counter).
+__global__ void advance_counter_kernel(long long* counter) { *counter += 1; }
+
+void drop_graph(teuk_s* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+}
+
+bool graphs_possible(const teuk_s* h) {
+  const cudaStream_t legacy = (cudaStream_t)0x1;
+  return h->use_graphs && !h->timing && h->stream != nullptr && h->stream != legacy;
+}
+
+// Captures one outer step: k iterations, the last one recording the observer row at slot
+// *d_ring_counter % cap, then the counter increment.
+int build_graph(teuk_s* h, bool record) {
+  drop_graph(h);
+  const int64_t launches = h->launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return teuk::cuda_fail(h, e, "cudaStreamBeginCapture");
+  int rc = TEUK_OK;
+  for (int q = 0; q < h->k && rc == TEUK_OK; ++q) rc = dispatch_substep(h, record && q == h->k - 1, -1);
+  if (rc == TEUK_OK && record) advance_counter_kernel<<<1, 1, 0, h->stream>>>(h->d_ring_counter);
+  e = cudaStreamEndCapture(h->stream, &graph);
+  h->launches = launches;
+  if (rc != TEUK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return teuk::cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->graph_exec = nullptr;
+    return teuk::cuda_fail(h, e, "cudaGraphInstantiate");
+  }
+  h->graph_record = record;
+  return TEUK_OK;
 }
 
 void drain_timing(teuk_s* h) {
@@ -198,6 +245,8 @@ int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   }
   if (cudaMalloc(&h->status, sizeof(unsigned int)) != cudaSuccess) return fail(TEUK_ERR_OOM);
   cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream);
+  if (cudaMalloc(&h->d_ring_counter, sizeof(long long)) != cudaSuccess) return fail(TEUK_ERR_OOM);
+  cudaMemsetAsync(h->d_ring_counter, 0, sizeof(long long), h->stream);
   rc = dispatch_setup(h);
   if (rc != TEUK_OK) return fail(rc);
   *out = h;
@@ -270,8 +319,32 @@ int teuk_substep(teuk_t h, int64_t n) {
   return TEUK_OK;
 }
 
+int teuk_use_graphs(teuk_t h, int enable) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  h->use_graphs = enable != 0;
+  if (!h->use_graphs) drop_graph(h);
+  return TEUK_OK;
+}
+
 int teuk_step(teuk_t h, int64_t n) {
   if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
+  if (n > 0 && graphs_possible(h)) {
+    const bool record = h->ring != nullptr;
+    if (!h->graph_exec || h->graph_record != record) {
+      int rc = build_graph(h, record);
+      if (rc != TEUK_OK) return rc;
+    }
+    if (record) {
+      const long long recorded = h->n_recorded;
+      TEUK_CUDA(h, cudaMemcpyAsync(h->d_ring_counter, &recorded, sizeof(recorded), cudaMemcpyHostToDevice,
+                                   h->stream));
+    }
+    for (int64_t t = 0; t < n; ++t) TEUK_CUDA(h, cudaGraphLaunch(h->graph_exec, h->stream));
+    h->substeps_done += n * h->k;
+    h->launches += n * 2 * h->k;
+    if (record) h->n_recorded += n;
+    return TEUK_OK;
+  }
   for (int64_t t = 0; t < n; ++t) {
     for (int q = 0; q < h->k; ++q) {
       const bool last = q == h->k - 1;
@@ -321,6 +394,7 @@ int teuk_set_observer(teuk_t h, double rstar_obs, int64_t capacity) {
   h->ring_cap = capacity;
   h->i_obs = observer_row(h, rstar_obs);
   h->n_recorded = 0;
+  drop_graph(h);
   return TEUK_OK;
 }
 
@@ -421,6 +495,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   h->timing = timing;
   h->launches = launches;
   h->rows_per_block = best;
+  drop_graph(h);
   if (rows_per_block) *rows_per_block = best;
   return rc;
 }

@@ -36,6 +36,11 @@ struct teuk_s {
   double* rs_node = nullptr; // [W][n_r]
   double* prof = nullptr;    // [W][n_th]
   unsigned int* status = nullptr;
+  // CUDA graph of one outer step (k iterations), replayed by teuk_step
+  bool use_graphs = true;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_record = false;   // whether the captured step records an observer sample
+  long long* d_ring_counter = nullptr;  // samples recorded so far (device copy)
   // observer ring
   int i_obs = -1;
   int64_t ring_cap = 0;
@@ -65,6 +70,7 @@ int setup_w4(teuk_s* h);
 int pulse_w1(teuk_s* h, double center, double width, double ar, double ai, int ell);
 int pulse_w2(teuk_s* h, double center, double width, double ar, double ai, int ell);
 int pulse_w4(teuk_s* h, double center, double width, double ar, double ai, int ell);
+int advance_counter(teuk_s* h);
 int substep_w1(teuk_s* h, bool record, int64_t slot);
 int substep_w2(teuk_s* h, bool record, int64_t slot);
 int substep_w4(teuk_s* h, bool record, int64_t slot);

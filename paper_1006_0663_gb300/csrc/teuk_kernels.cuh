@@ -382,7 +382,9 @@ struct StepArgs {
   int radius;              // 5 (10th order) or 1 (2nd order)
   int record;              // write Phi(i_obs, .) to the ring after this substep
   int i_obs;
-  long long ring_slot;
+  long long ring_slot;     // slot to write, or -1: take it from *ring_counter % ring_cap
+  const long long* ring_counter;  // samples recorded so far (device), used when ring_slot < 0
+  long long ring_cap;
   double* ring;            // [cap][2][W][n_th]
   unsigned int* status;    // bit 0: non-finite value produced
 };
@@ -604,7 +606,8 @@ __global__ void __launch_bounds__(256) full_kernel(StepArgs a) {
   if (ok) full_row_prep<W>(a, i, threadIdx.x, blockDim.x, sR, sI);
   __syncthreads();
   if (!ok) return;
-  const long long slot = a.record ? a.ring_slot : -1;
+  long long slot = -1;
+  if (a.record) slot = a.ring_slot >= 0 ? a.ring_slot : (*a.ring_counter) % a.ring_cap;
   if (full_row_out<W>(a, i, threadIdx.x, blockDim.x, sR, sI, slot)) atomicOr(a.status, 1u);
 }
 

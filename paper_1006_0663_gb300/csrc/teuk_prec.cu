@@ -196,6 +196,8 @@ int substep_impl(teuk_s* h, bool record, int64_t slot) {
   sa.record = record ? 1 : 0;
   sa.i_obs = h->i_obs;
   sa.ring_slot = slot;
+  sa.ring_counter = h->d_ring_counter;
+  sa.ring_cap = h->ring_cap;
   sa.ring = h->ring;
   sa.status = h->status;
   dim3 blk;
@@ -235,6 +237,8 @@ int substep_buffers_impl(teuk_s* h, const double* u_in, double* u_out, double* s
   sa.record = 0;
   sa.i_obs = -1;
   sa.ring_slot = 0;
+  sa.ring_counter = nullptr;
+  sa.ring_cap = 0;
   sa.ring = nullptr;
   sa.status = h->status;
   dim3 blk;

@@ -26,7 +26,7 @@ SYMBOLS = [
     "teuk_get_tortoise", "teuk_info", "teuk_kernel_launches", "teuk_strerror", "teuk_last_error",
     "teuk_mw_eval", "teuk_timing", "teuk_kernel_times", "teuk_fp64_peak", "teuk_substep_noalloc",
     "teuk_tune", "teuk_batch_create", "teuk_batch_step", "teuk_batch_sync", "teuk_batch_info",
-    "teuk_batch_destroy",
+    "teuk_batch_destroy", "teuk_use_graphs",
 ]
 
 
@@ -94,6 +94,7 @@ def lib(build_if_missing: bool = True):
         L.teuk_batch_sync.argtypes = [vp]
         L.teuk_batch_info.argtypes = [vp, P(i32), P(i32), P(i64), P(i64)]
         L.teuk_batch_destroy.argtypes = [vp]
+        L.teuk_use_graphs.argtypes = [vp, i32]
         _lib = L
     return _lib
 
@@ -239,6 +240,9 @@ class Teuk:
         _check(lib().teuk_info(self._h, ctypes.byref(w), ctypes.byref(nr), ctypes.byref(nt),
                                ctypes.byref(k), ctypes.byref(dt)), self._h)
         return dict(words=w.value, n_r=nr.value, n_theta=nt.value, substeps=k.value, dt=dt.value)
+
+    def use_graphs(self, enable=True):
+        _check(lib().teuk_use_graphs(self._h, 1 if enable else 0), self._h)
 
     def tune(self) -> int:
         """Pick the fastest step-kernel launch shape (rows per block); state is preserved."""
