@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 / qd side figures")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-member batched workload")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["c1", "c2", "c3", "c5"],
+                    help="workload of the main line (default c2, the benchmark configuration)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="words per real (0: the workload's own precision)")
+    ap.add_argument("--digits", action="store_true",
+                    help="print the cost-per-digit table (errors vs the oracle and each other)")
     return ap.parse_args()
 
 
@@ -284,10 +290,100 @@ def describe(prob):
             f"{prob.seed}), waveform at r*={prob.rstar_obs} every step")
 
 
+def word_diff(a, b):
+    """(sum of a's words) - (sum of b's words), summed from the smallest words up."""
+    import numpy as np
+    diff = np.zeros(a.shape[:1] + a.shape[2:])
+    for k in reversed(range(max(a.shape[1], b.shape[1]))):
+        x = a[:, k] if k < a.shape[1] else 0.0
+        y = b[:, k] if k < b.shape[1] else 0.0
+        diff = diff + (x - y)
+    return diff
+
+
+def digits_table():
+    """Errors of FP64 / double-double / quad-double runs and their cost.
+
+    1. c1 at its full length (1000 outer steps = 46000 iterations) in all three arithmetics
+       on the GPU; quad-double is the reference for the FP64 and dd errors.
+    2. The reference itself: a prefix of c1 (3 outer steps) against the 256-bit oracle.
+    3. Throughput of each arithmetic on the c2 grid (CUDA events)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1006_0663_gb300 import teuk, workloads
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    c1, c2 = workloads.CONFIGS["c1"], workloads.CONFIGS["c2"]
+    ar, ai = c1.amps
+    out = {"reference_check": {}, "c1_full_run": {}, "throughput_c2_grid": {}}
+    # prefix vs the 256-bit oracle
+    o = oracle.Oracle(M=c1.M, a=c1.a, s=c1.s, m=c1.m, rstar_min=c1.rstar_min, rstar_max=c1.rstar_max,
+                      n_r=c1.n_r, n_theta=c1.n_theta, dt=0.0, substeps=c1.substeps, bits=256)
+    o.pulse(c1.center, c1.width, ar, ai, c1.ell)
+    o.step(3 * c1.substeps)
+    for W in (1, 2, 4):
+        g = teuk.Teuk.from_problem(c1, precision=W)
+        g.set_initial_pulse(c1.center, c1.width, ar, ai, c1.ell)
+        g.step(3)
+        g.sync()
+        err, _ = o.max_rel_err(g.get_state())
+        out["reference_check"][DTYPE[W]] = {"steps": 3, "max_rel_err_vs_256bit": err}
+        g.close()
+    # full-length c1 in all arithmetics
+    states, times = {}, {}
+    for W in (4, 2, 1):
+        g = teuk.Teuk.from_problem(c1, precision=W)
+        g.set_initial_pulse(c1.center, c1.width, ar, ai, c1.ell)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(c1.steps)
+        g.sync()
+        times[W] = time.perf_counter() - t0
+        states[W] = g.get_state()
+        g.close()
+    ref = states[4]
+    scale = np.abs(ref[:, 0]).max()
+    for W in (1, 2):
+        err = float(np.abs(word_diff(states[W], ref)).max() / scale)
+        out["c1_full_run"][DTYPE[W]] = {"steps": c1.steps, "max_rel_err_vs_qd": err,
+                                        "digits": -np.log10(err) if err > 0 else None,
+                                        "seconds": times[W]}
+    out["c1_full_run"][DTYPE[4]] = {"steps": c1.steps, "seconds": times[4],
+                                    "max_abs_field": float(scale)}
+    # throughput on the c2 grid
+    for W, nst in ((1, 3), (2, 2), (4, 1)):
+        p = c2
+        g = teuk.Teuk.from_problem(p, precision=W)
+        g.set_initial_pulse(p.center, p.width, ar, ai, p.ell)
+        g.tune()
+        g.step(1)
+        g.sync()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        g.step(nst)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1)
+        ups = p.n_r * p.n_theta * p.substeps * nst / (ms * 1e-3)
+        out["throughput_c2_grid"][DTYPE[W]] = {"updates_per_s": ups, "ns_per_update": 1e9 / ups}
+        g.close()
+    for W in (1, 2):
+        d = out["c1_full_run"][DTYPE[W]]["digits"]
+        ns = out["throughput_c2_grid"][DTYPE[W]]["ns_per_update"]
+        out["c1_full_run"][DTYPE[W]]["ns_per_update_per_digit"] = ns / d if d else None
+    print(json.dumps({"digits_table": out}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.digits:
+        return digits_table()
     import torch
     import torch.distributed as dist
 
@@ -299,8 +395,8 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prob = workloads.CONFIGS[WORKLOAD]
-    W = prob.words
+    prob = workloads.CONFIGS[args.workload]
+    W = args.precision or prob.words
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)  # the library handles are created on this stream
@@ -325,6 +421,7 @@ def main():
 
     out = None
     if rank == 0:
+        describe_w = describe(prob) if W == prob.words else describe(prob).replace(DTYPE[prob.words], DTYPE[W])
         ms_h, ms_f, n_h, n_f = res["kernel_times"]
         pts_h = (prob.n_r - 1) * prob.n_theta
         pts_f = (prob.n_r - 2) * prob.n_theta
@@ -333,7 +430,13 @@ def main():
         dom = "half" if ms_h >= ms_f else "full"
         ops = (OPS_HALF[W] * pts_h if dom == "half" else OPS_FULL[W] * pts_f)
         avg = avg_h if dom == "half" else avg_f
-        peak = teuk.fp64_peak()
+        # FP64 pipe peak: 2 operations per SM per cycle (ncu
+        # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per cycle for
+        # 152 SMs) x SMs x the SM clock sampled during the timed region.
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        peak = 2.0 * sms * mhz * 1e6
+        probe = teuk.fp64_peak()
         achieved = ops / (avg * 1e-3)
         traffic_note = None
         roofline = {
@@ -342,7 +445,9 @@ def main():
             "kernel": f"{dom}_kernel<{W}>", "avg_launch_ms": avg,
             "rows_per_block": res["rows_per_block"],
             "ops_per_point": OPS_HALF[W] if dom == "half" else OPS_FULL[W],
-            "peak_source": "measured in this run: FP64 FMA chain on every SM (teuk_fp64_peak)",
+            "peak_source": f"2 FP64 ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (SM clock sampled "
+                           "during the timed region)",
+            "fma_chain_probe_tops": probe / 1e12,
             "op_unit": "FP64 pipe operations (add, mul, fma count one each)",
             "hbm_achieved_gbs": (BYTES_HALF[W] * pts_h if dom == "half" else BYTES_FULL[W] * pts_f)
             / (avg * 1e-3) / 1e9,
@@ -350,6 +455,8 @@ def main():
             / max(res["ms_total"], 1e-9),
         }
         e2e = run_e2e(prob, W, max(3, args.steps // 2), torch, teuk)
+        if W != prob.words or args.workload != WORKLOAD:
+            args.no_variants = args.no_batch = True
         variants = {}
         if not args.no_variants:
             for name, w, nst in (("c1", 1, 20), ("c5", 1, 2), ("c3", 4, 2), ("c5", 2, 1)):
@@ -367,7 +474,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[W], "data": "synthetic",
-            "config": {"workload": describe(prob),
+            "config": {"workload": describe_w,
                        "l2": "256 MiB buffer written between timed steps (outside the timed "
                              "interval); the 100 MB working set is L2-resident within a step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

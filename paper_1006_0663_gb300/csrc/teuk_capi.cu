@@ -464,27 +464,34 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   const bool timing = h->timing;
   h->timing = false;
   const int64_t launches = h->launches;
-  const int tx = std::min(256, ((h->n_th + 31) / 32) * 32);
-  int best = 0;
+  const int tx_full = std::min(256, ((h->n_th + 31) / 32) * 32);
+  int best = 0, best_tx = 0;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int rc = TEUK_OK;
-  for (int ty = 1; ty <= 8 && tx * ty <= 256; ty *= 2) {
-    h->rows_per_block = ty;
-    if ((rc = dispatch_substep(h, false, 0)) != TEUK_OK) break;  // warm-up
-    cudaEventRecord(e0, h->stream);
-    for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
-    cudaEventRecord(e1, h->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (rc != TEUK_OK) break;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = ty;
+  // candidates: threads along theta (32 .. the row width, powers of two times 32, or the
+  // row width itself) x rows per block, at most 256 threads
+  for (int tx = 32; tx <= tx_full && rc == TEUK_OK; tx = (tx * 2 > tx_full && tx < tx_full) ? tx_full : tx * 2) {
+    for (int ty = 1; ty <= 8 && tx * ty <= 256 && rc == TEUK_OK; ty *= 2) {
+      h->threads_theta = tx;
+      h->rows_per_block = ty;
+      if ((rc = dispatch_substep(h, false, 0)) != TEUK_OK) break;  // warm-up
+      cudaEventRecord(e0, h->stream);
+      for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc != TEUK_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ty;
+        best_tx = tx;
+      }
     }
+    if (tx == tx_full) break;
   }
   cudaMemcpyAsync(h->u, saved, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(h->status, &status, sizeof(status), cudaMemcpyHostToDevice, h->stream);
@@ -495,6 +502,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   h->timing = timing;
   h->launches = launches;
   h->rows_per_block = best;
+  h->threads_theta = best_tx;
   drop_graph(h);
   if (rows_per_block) *rows_per_block = best;
   return rc;

@@ -392,21 +392,25 @@ struct StepArgs {
 // Centred theta operator at column j on a ghosted shared-memory row (index j + radius is
 // column j): sum_q w[q][j] f[j + q], combined second-derivative and cot(th) first-derivative
 // weights (Sec. 3.D, 11-point 10th-order stencil; 3-point for 2nd order).
-template <class R, int W>
+template <class R, int W, int RAD>
 __device__ __forceinline__ R theta_op(const double* srow, int gstride, const double* __restrict__ wts,
-                                      int n_th, int radius, int j) {
-  const int nq = 2 * radius + 1;
+                                      int n_th, int j) {
+  // fully unrolled (compile-time radius): a loop here costs extra FP64 moves per term
   const size_t wws = (size_t)n_th;
-  R c0 = ld_r<R>(wts + (size_t)0 * W * wws + j, wws);
-  R v0 = ld_s<R>(srow + j, gstride);
   Acc<R> acc(mw::r_from<R>(0.0));
-  acc.mac(c0, v0);
-  for (int q = 1; q < nq; ++q) {
+#pragma unroll
+  for (int q = 0; q < 2 * RAD + 1; ++q) {
     const R cq = ld_r<R>(wts + (size_t)q * W * wws + j, wws);
     const R vq = ld_s<R>(srow + j + q, gstride);
     acc.mac(cq, vq);
   }
   return acc.get();
+}
+template <class R, int W>
+__device__ __forceinline__ R theta_op(const double* srow, int gstride, const double* __restrict__ wts,
+                                      int n_th, int radius, int j) {
+  return radius == 5 ? theta_op<R, W, 5>(srow, gstride, wts, n_th, j)
+                     : theta_op<R, W, 1>(srow, gstride, wts, n_th, j);
 }
 
 // Writes value v of ghosted row column j, and its parity images across the poles.

@@ -176,6 +176,7 @@ int pulse_impl(teuk_s* h, double center, double width, double ar, double ai, int
 void step_shape(const teuk_s* h, dim3& blk) {
   int tx = ((h->n_th + 31) / 32) * 32;
   if (tx > 256) tx = 256;
+  if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
   int ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
   while (ty > 1 && tx * ty > 256) ty /= 2;
   blk = dim3(tx, ty);
