@@ -31,8 +31,8 @@ WORKLOAD = "c2"
 # FP64 pipe operations (add, mul and fma count one each) per grid point for one launch of
 # each kernel, from the operation list of the scheme in each arithmetic ("Work
 # per point"). half = Eq. lw1 kernel, full = Eq. lw2 kernel.
-OPS_HALF = {1: 52, 2: 512, 4: 7632}
-OPS_FULL = {1: 50, 2: 508, 4: 7620}
+OPS_HALF = {1: 52, 2: 512, 4: 3744}
+OPS_FULL = {1: 50, 2: 508, 4: 3736}
 # Algorithmic DRAM bytes per grid point per launch: state rows read once, half rows written
 # once (half kernel) / read once and state written once (full kernel), 8 folded coefficients.
 BYTES_HALF = {w: (4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
@@ -137,6 +137,33 @@ def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=Tru
     out["waveform_samples"] = int(wf.shape[0])
     g.close()
     return out
+
+
+def stated_error(prob, words, teuk, nsub=12):
+    """Error of this workload's GPU state against the 256-bit oracle (FP64 oracle for FP64)
+    after nsub Lax-Wendroff iterations, on a window of rows around the pulse, where the window
+    interior is exact (domain of dependence)."""
+    import oracle
+    oracle.build()
+    g = teuk.Teuk.from_problem(prob, precision=words)
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    g.substep(nsub)
+    g.sync()
+    full = g.get_state()
+    g.close()
+    ic = int(round((prob.center - prob.rstar_min) / prob.dr))
+    lo, hi = ic - 12, ic + 12
+    wlo, whi = max(0, lo - nsub - 1), min(prob.n_r - 1, hi + nsub + 1)
+    bits = 53 if words == 1 else 256
+    o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
+                      rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
+                      substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=bits)
+    o.pulse(prob.center, prob.width, ar, ai, prob.ell)
+    o.step(nsub)
+    err, _ = o.max_rel_err(full[:, :, wlo:whi + 1].copy(), lo - wlo, hi - wlo)
+    return {"max_rel_err": err, "oracle_bits": bits, "iterations": nsub,
+            "rows": f"{lo}..{hi} of {prob.n_r}", "tolerance": TOL[words]}
 
 
 def run_batch1(prob, words, steps, torch, teuk):
@@ -282,6 +309,19 @@ def reference_arm(args):
     return 0
 
 
+def aggregate_ranks(t_local_ms, updates_per_rank, world, dist, torch, device):
+    """Whole-job throughput of independent replicas: every rank advances its own copy of the
+    workload; the job time is the slowest rank's, value = all ranks' updates / that time."""
+    if world > 1:
+        t = torch.tensor([t_local_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    else:
+        t_max = t_local_ms
+    return t_max, world * updates_per_rank / (t_max * 1e-3)
+
+
 def describe(prob):
     return (f"{prob.name}: {DTYPE[prob.words]}, M={prob.M}, a={prob.a}, s={prob.s}, m={prob.m}, "
             f"r* in [{prob.rstar_min}, {prob.rstar_max}] x {prob.n_r} nodes, theta x {prob.n_theta} "
@@ -408,16 +448,8 @@ def main():
     res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush)
     clocks = stop_clock_sampler(*sampler, device_index=local)
     torch.cuda.synchronize()
-    t_local = res["ms_total"]
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        dist.barrier()
-    else:
-        t_max = t_local
     updates_per_rank = res["points"] * res["substeps"] * args.steps
-    value = world * updates_per_rank / (t_max * 1e-3)
+    t_max, value = aggregate_ranks(res["ms_total"], updates_per_rank, world, dist, torch, "cuda")
 
     out = None
     if rank == 0:
@@ -470,6 +502,7 @@ def main():
                                                  "launch": "one cooperative launch, 20 steps"}
         batched = None if args.no_batch else run_c4(torch, teuk, workloads)
         cpu = None if args.no_cpu else cpu_baseline(prob, W)
+        parity = None if args.no_cpu else stated_error(prob, W, teuk)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -486,6 +519,7 @@ def main():
             "per_precision": variants,
             "batched": batched,
             "tolerance_vs_256bit_oracle": TOL[W],
+            "error_vs_oracle": parity,
         }
         print(json.dumps(out))
     if world > 1:

@@ -82,6 +82,7 @@ def lib():
         L.oracle_max_rel_err.argtypes = [vp, dp, i32, i32, i32, dp, dp]
         L.oracle_theta_op.argtypes = [i32, i32, i32, i32, dp, i32, dp, i32]
         L.oracle_spin_profile.argtypes = [i32, i32, i32, i32, i32, dp, i32]
+        L.oracle_set_row.argtypes = [vp, i32, dp, i32]
         L.oracle_set_threads.argtypes = [i32]
         L.oracle_max_threads.restype = i32
         _lib = L
@@ -165,6 +166,13 @@ class Oracle:
         if lib().oracle_get_row(self._h, int(row), _dp(out), words) != 0:
             raise IndexError(row)
         return out
+
+    def set_row(self, row: int, values: np.ndarray):
+        """Overwrite one window row from values [4, words, n_theta]."""
+        values = np.ascontiguousarray(values, dtype=np.float64)
+        assert values.shape[0] == 4 and values.shape[2] == self.nth
+        if lib().oracle_set_row(self._h, int(row), _dp(values), values.shape[1]) != 0:
+            raise IndexError(row)
 
     def coeffs(self, which: int, words: int = 1) -> np.ndarray:
         rows = self.nrow - 1 if which else self.nrow

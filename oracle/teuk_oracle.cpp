@@ -737,3 +737,21 @@ int oracle_spin_profile(int bits, int s, int m, int ell, int nth, double* out, i
 }
 
 }  // extern "C"
+
+extern "C" {
+
+// Overwrites one theta row of the state (window-relative row index) from in [4][words][nth]:
+// used to place halo rows received from a neighbouring slab.
+int oracle_set_row(void* hv, int row, const double* in, int words) {
+  Handle* h = (Handle*)hv;
+  return dispatch(h, [&](auto& S) {
+    using T = typename std::decay<decltype(S.dts)>::type;
+    if (row < 0 || row >= S.nrow) return -1;
+    for (int c = 0; c < 4; ++c)
+      for (int j = 0; j < S.nth; ++j)
+        S.u[c][(size_t)row * S.nth + j] = from_words<T>(in + ((int64_t)c * words) * S.nth + j, words, S.nth);
+    return 0;
+  });
+}
+
+}  // extern "C"

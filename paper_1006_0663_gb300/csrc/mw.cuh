@@ -286,7 +286,20 @@ MW_HD qd qd_add(qd a, qd b) {
   t0 = add_(add_(t0, t1), t3);
   return qd_renorm(s0, s1, s2, s3, t0);
 }
-MW_HD qd qd_sub(qd a, qd b) { return qd_add(a, qd_neg(b)); }
+// a - b: qd_add with the four leading subtractions done as ordered TwoDiffs (the sign of b is
+// flipped on the integer side, no FP64 negations).
+MW_HD qd qd_sub(qd a, qd b) {
+  double s0, s1, s2, s3, t0, t1, t2, t3;
+  two_diff_ord(a.x0, b.x0, s0, t0);
+  two_diff_ord(a.x1, b.x1, s1, t1);
+  two_diff_ord(a.x2, b.x2, s2, t2);
+  two_diff_ord(a.x3, b.x3, s3, t3);
+  two_sum_ord(s1, t0, s1, t0);
+  three_sum(s2, t0, t1);
+  three_sum2(s3, t0, t2);
+  t0 = add_(add_(t0, t1), t3);
+  return qd_renorm(s0, s1, s2, s3, t0);
+}
 MW_HD qd qd_add_d(qd a, double b) { return qd_add(a, qd_from(b)); }
 
 // HLB01 quad-double multiplication: exact products of order 0..2 by TwoProd, order-3

@@ -473,25 +473,30 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   int rc = TEUK_OK;
   // candidates: threads along theta (32 .. the row width, powers of two times 32, or the
   // row width itself) x rows per block, at most 256 threads
-  for (int tx = 32; tx <= tx_full && rc == TEUK_OK; tx = (tx * 2 > tx_full && tx < tx_full) ? tx_full : tx * 2) {
-    for (int ty = 1; ty <= 8 && tx * ty <= 256 && rc == TEUK_OK; ty *= 2) {
-      h->threads_theta = tx;
-      h->rows_per_block = ty;
-      if ((rc = dispatch_substep(h, false, 0)) != TEUK_OK) break;  // warm-up
-      cudaEventRecord(e0, h->stream);
-      for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
-      cudaEventRecord(e1, h->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rc != TEUK_OK) break;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = ty;
-        best_tx = tx;
+  int best_v = 0;
+  for (int v = 0; v < 3 && rc == TEUK_OK; ++v) {
+    for (int tx = 32; tx <= tx_full && rc == TEUK_OK; tx = (tx * 2 > tx_full && tx < tx_full) ? tx_full : tx * 2) {
+      for (int ty = 1; ty <= 8 && tx * ty <= 256 && rc == TEUK_OK; ty *= 2) {
+        h->kernel_variant = v;
+        h->threads_theta = tx;
+        h->rows_per_block = ty;
+        if ((rc = dispatch_substep(h, false, 0)) != TEUK_OK) break;  // warm-up
+        cudaEventRecord(e0, h->stream);
+        for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc != TEUK_OK) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = ty;
+          best_tx = tx;
+          best_v = v;
+        }
       }
+      if (tx == tx_full) break;
     }
-    if (tx == tx_full) break;
   }
   cudaMemcpyAsync(h->u, saved, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(h->status, &status, sizeof(status), cudaMemcpyHostToDevice, h->stream);
@@ -503,6 +508,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   h->launches = launches;
   h->rows_per_block = best;
   h->threads_theta = best_tx;
+  h->kernel_variant = best_v;
   drop_graph(h);
   if (rows_per_block) *rows_per_block = best;
   return rc;

@@ -17,6 +17,7 @@ struct teuk_s {
   int W = 1;            // words per real
   int rows_per_block = 0;  // step-kernel launch shape: rows of theta per block (0: default)
   int threads_theta = 0;   // threads along theta per row (0: n_theta rounded up to 32, <= 256)
+  int kernel_variant = 0;  // register budget of the step kernels: 0 (<= 255), 1 (<= 128), 2 (<= 85)
   int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;
   double dt_outer = 0;  // leading word of the outer step
   int device = 0;

@@ -63,7 +63,7 @@ __host__ __device__ __forceinline__ mw::dd v_sub(mw::dd a, mw::dd b) { return mw
 __host__ __device__ __forceinline__ mw::dd v_half(mw::dd a) { return mw::dd_scale2(a, 0.5); }
 __host__ __device__ __forceinline__ mw::dd v_neg(mw::dd a) { return mw::dd_neg(a); }
 __host__ __device__ __forceinline__ mw::qd v_add(mw::qd a, mw::qd b) { return mw::qd_add(a, b); }
-__host__ __device__ __forceinline__ mw::qd v_sub(mw::qd a, mw::qd b) { return mw::qd_add(a, mw::qd_neg(b)); }
+__host__ __device__ __forceinline__ mw::qd v_sub(mw::qd a, mw::qd b) { return mw::qd_sub(a, b); }
 __host__ __device__ __forceinline__ mw::qd v_half(mw::qd a) { return mw::qd_scale2(a, 0.5); }
 __host__ __device__ __forceinline__ mw::qd v_neg(mw::qd a) { return mw::qd_neg(a); }
 
@@ -586,8 +586,10 @@ __device__ __forceinline__ bool full_row_out(const StepArgs& a, int i, int tx, i
 }
 
 // ---- single-problem kernels: blockDim.y rows per block, blockDim.x threads along theta ------
-template <int W>
-__global__ void __launch_bounds__(256) half_kernel(StepArgs a) {
+// V selects the register budget (launch bounds: at least V + 1 blocks of 256 threads per SM,
+// i.e. <= 255, 128 or 85 registers); the autotuner picks the fastest variant per problem.
+template <int W, int V = 0>
+__global__ void __launch_bounds__(256, V + 1) half_kernel(StepArgs a) {
   extern __shared__ double sm[];
   const int gstride = a.g.n_th + 2 * a.radius;
   const int h = blockIdx.x * blockDim.y + threadIdx.y;
@@ -599,8 +601,8 @@ __global__ void __launch_bounds__(256) half_kernel(StepArgs a) {
   if (ok) half_row_out<W>(a, h, threadIdx.x, blockDim.x, sR, sI);
 }
 
-template <int W>
-__global__ void __launch_bounds__(256) full_kernel(StepArgs a) {
+template <int W, int V = 0>
+__global__ void __launch_bounds__(256, V + 1) full_kernel(StepArgs a) {
   extern __shared__ double sm[];
   const int gstride = a.g.n_th + 2 * a.radius;
   const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;

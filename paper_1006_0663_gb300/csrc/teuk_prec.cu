@@ -182,6 +182,34 @@ void step_shape(const teuk_s* h, dim3& blk) {
   blk = dim3(tx, ty);
 }
 
+// Launches the half and full kernels of the handle's register-budget variant.
+template <int V>
+int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
+  const int nh = h->n_r - 1, nf = h->n_r - 2;
+  if (smem > 48 * 1024) {  // above the default dynamic limit (quad-double, n_theta > 700)
+    TEUK_CUDA(h, cudaFuncSetAttribute(half_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TEUK_CUDA(h, cudaFuncSetAttribute(full_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  cudaEvent_t ev = nullptr;
+  time_begin(h, &ev);
+  half_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  time_end(h, 0, ev);
+  time_begin(h, &ev);
+  full_kernel<W, V><<<(nf + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  time_end(h, 1, ev);
+  h->launches += 2;
+  TEUK_CUDA(h, cudaGetLastError());
+  return TEUK_OK;
+}
+
+int launch_pair(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
+  switch (h->kernel_variant) {
+    case 1: return launch_pair_v<1>(h, sa, blk, smem);
+    case 2: return launch_pair_v<2>(h, sa, blk, smem);
+    default: return launch_pair_v<0>(h, sa, blk, smem);
+  }
+}
+
 int substep_impl(teuk_s* h, bool record, int64_t slot) {
   StepArgs sa{};
   sa.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
@@ -204,21 +232,7 @@ int substep_impl(teuk_s* h, bool record, int64_t slot) {
   dim3 blk;
   step_shape(h, blk);
   const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
-  const int nh = h->n_r - 1, nf = h->n_r - 2;
-  if (smem > 48 * 1024) {  // above the default dynamic limit (quad-double, n_theta > 700)
-    TEUK_CUDA(h, cudaFuncSetAttribute(half_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TEUK_CUDA(h, cudaFuncSetAttribute(full_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
-  cudaEvent_t ev = nullptr;
-  time_begin(h, &ev);
-  half_kernel<W><<<(nh + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
-  time_end(h, 0, ev);
-  time_begin(h, &ev);
-  full_kernel<W><<<(nf + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
-  time_end(h, 1, ev);
-  h->launches += 2;
-  TEUK_CUDA(h, cudaGetLastError());
-  return TEUK_OK;
+  return launch_pair(h, sa, blk, smem);
 }
 
 // One Lax-Wendroff iteration from u_in to u_out (may alias) with the half-step rows in a
@@ -245,16 +259,11 @@ int substep_buffers_impl(teuk_s* h, const double* u_in, double* u_out, double* s
   dim3 blk;
   step_shape(h, blk);
   const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
-  const int nh = h->n_r - 1, nf = h->n_r - 2;
-  if (smem > 48 * 1024) {
-    TEUK_CUDA(h, cudaFuncSetAttribute(half_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TEUK_CUDA(h, cudaFuncSetAttribute(full_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
-  half_kernel<W><<<(nh + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
-  full_kernel<W><<<(nf + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
-  h->launches += 2;
-  TEUK_CUDA(h, cudaGetLastError());
-  return TEUK_OK;
+  const bool timing = h->timing;
+  h->timing = false;  // no events on this path
+  const int rc = launch_pair(h, sa, blk, smem);
+  h->timing = timing;
+  return rc;
 }
 
 // ---- multi-word self test ---------------------------------------------------------------------
