@@ -147,6 +147,14 @@ int teuk_batch_destroy(teuk_batch_t b);
  * restores the state and returns the choice in *rows_per_block (may be NULL). Allocates and
  * frees one state-sized device buffer; call it before timing-critical work. */
 int teuk_tune(teuk_t h, int* rows_per_block);
+/* The step kernels' launch shape in use: threads along theta per row, rows per block, and the
+ * kernel variant: 0, 1, 2 = whole rows per block with <= 255, 128, 85 registers per thread;
+ * 3, 4, 5 = one warp per (row, 32 theta columns) with the same three register budgets. */
+int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant);
+/* Sets the launch shape explicitly (same meaning as above; threads_theta a multiple of 32,
+ * threads_theta * rows_per_block <= 256; both ignored for variants 3..5). Results do not
+ * depend on the shape. */
+int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant);
 
 /* Lax-Wendroff iterations that allocate nothing, for callers that cannot let a library
  * allocate device memory while they step (their memory belongs to a pool of their own, or

@@ -473,30 +473,35 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   int rc = TEUK_OK;
   // candidates: threads along theta (32 .. the row width, powers of two times 32, or the
   // row width itself) x rows per block, at most 256 threads
-  int best_v = 0;
+  int best_v = 0, best_f = 0;
+  auto trial = [&](int f, int v, int tx, int ty) {
+    h->kernel_family = f;
+    h->kernel_variant = v;
+    h->threads_theta = tx;
+    h->rows_per_block = ty;
+    if ((rc = dispatch_substep(h, false, 0)) != TEUK_OK) return;  // warm-up
+    cudaEventRecord(e0, h->stream);
+    for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == TEUK_OK && ms < best_ms) {
+      best_ms = ms;
+      best = ty;
+      best_tx = tx;
+      best_v = v;
+      best_f = f;
+    }
+  };
   for (int v = 0; v < 3 && rc == TEUK_OK; ++v) {
+    // rows-per-block kernels: threads along theta x rows per block, at most 256 threads
     for (int tx = 32; tx <= tx_full && rc == TEUK_OK; tx = (tx * 2 > tx_full && tx < tx_full) ? tx_full : tx * 2) {
-      for (int ty = 1; ty <= 8 && tx * ty <= 256 && rc == TEUK_OK; ty *= 2) {
-        h->kernel_variant = v;
-        h->threads_theta = tx;
-        h->rows_per_block = ty;
-        if ((rc = dispatch_substep(h, false, 0)) != TEUK_OK) break;  // warm-up
-        cudaEventRecord(e0, h->stream);
-        for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
-        cudaEventRecord(e1, h->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rc != TEUK_OK) break;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = ty;
-          best_tx = tx;
-          best_v = v;
-        }
-      }
+      for (int ty = 1; ty <= 8 && tx * ty <= 256 && rc == TEUK_OK; ty *= 2) trial(0, v, tx, ty);
       if (tx == tx_full) break;
     }
+    // one warp per (row, 32 columns)
+    if (rc == TEUK_OK) trial(1, v, 0, 0);
   }
   cudaMemcpyAsync(h->u, saved, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(h->status, &status, sizeof(status), cudaMemcpyHostToDevice, h->stream);
@@ -509,9 +514,46 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   h->rows_per_block = best;
   h->threads_theta = best_tx;
   h->kernel_variant = best_v;
+  h->kernel_family = best_f;
   drop_graph(h);
   if (rows_per_block) *rows_per_block = best;
   return rc;
+}
+
+int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (h->kernel_family == 1) {  // one warp per 32 columns: reported as 32 threads x 1 row, variant + 3
+    if (threads_theta) *threads_theta = 32;
+    if (rows_per_block) *rows_per_block = 1;
+    if (variant) *variant = 3 + h->kernel_variant;
+    return TEUK_OK;
+  }
+  int tx = std::min(256, ((h->n_th + 31) / 32) * 32);
+  if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
+  int ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
+  while (ty > 1 && tx * ty > 256) ty /= 2;
+  if (threads_theta) *threads_theta = tx;
+  if (rows_per_block) *rows_per_block = ty;
+  if (variant) *variant = h->kernel_variant;
+  return TEUK_OK;
+}
+
+int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant) {
+  if (!h || variant < 0 || variant > 5) return TEUK_ERR_INVALID_ARG;
+  if (variant < 3) {
+    if (threads_theta < 32 || threads_theta % 32 != 0 || rows_per_block < 1 ||
+        threads_theta * rows_per_block > 256)
+      return invalid(h, "launch shape: threads_theta a multiple of 32, threads_theta * rows <= 256");
+    h->kernel_family = 0;
+    h->kernel_variant = variant;
+    h->threads_theta = threads_theta;
+    h->rows_per_block = rows_per_block;
+  } else {
+    h->kernel_family = 1;
+    h->kernel_variant = variant - 3;
+  }
+  drop_graph(h);
+  return TEUK_OK;
 }
 
 int teuk_timing(teuk_t h, int enable) {

@@ -18,6 +18,7 @@ struct teuk_s {
   int rows_per_block = 0;  // step-kernel launch shape: rows of theta per block (0: default)
   int threads_theta = 0;   // threads along theta per row (0: n_theta rounded up to 32, <= 256)
   int kernel_variant = 0;  // register budget of the step kernels: 0 (<= 255), 1 (<= 128), 2 (<= 85)
+  int kernel_family = 0;   // 0: rows per block (half_kernel/full_kernel), 1: one warp per 32 columns
   int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;
   double dt_outer = 0;  // leading word of the outer step
   int device = 0;

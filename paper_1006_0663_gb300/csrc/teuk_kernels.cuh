@@ -392,6 +392,7 @@ struct StepArgs {
 // Centred theta operator at column j on a ghosted shared-memory row (index j + radius is
 // column j): sum_q w[q][j] f[j + q], combined second-derivative and cot(th) first-derivative
 // weights (Sec. 3.D, 11-point 10th-order stencil; 3-point for 2nd order).
+// srow points at the shared-memory entry of column j - RAD of a ghosted row (word stride gstride).
 template <class R, int W, int RAD>
 __device__ __forceinline__ R theta_op(const double* srow, int gstride, const double* __restrict__ wts,
                                       int n_th, int j) {
@@ -401,7 +402,7 @@ __device__ __forceinline__ R theta_op(const double* srow, int gstride, const dou
 #pragma unroll
   for (int q = 0; q < 2 * RAD + 1; ++q) {
     const R cq = ld_r<R>(wts + (size_t)q * W * wws + j, wws);
-    const R vq = ld_s<R>(srow + j + q, gstride);
+    const R vq = ld_s<R>(srow + q, gstride);
     acc.mac(cq, vq);
   }
   return acc.get();
@@ -457,50 +458,55 @@ __device__ __forceinline__ void half_row_prep(const StepArgs& a, int h, int tx, 
 //   Phi_h  = s_Phi/2 - H0 d_Phi + (h/4) s_Pi,
 //   Pi_h,R = H3 s_PiR + H4 s_PiI + H0 d_PiR + H1 d_PhiR + H2 d_PhiI + H5 L(s_Phi)_R + H6 s_PhiR - H7 s_PhiI,
 //   Pi_h,I = H3 s_PiI - H4 s_PiR + H0 d_PiI + H1 d_PhiI - H2 d_PhiR + H5 L(s_Phi)_I + H6 s_PhiI + H7 s_PhiR.
+// One point (h, j); sRj / sIj point at the ghosted s_Phi entries of column j - radius.
 template <int W>
-__device__ __forceinline__ void half_row_out(const StepArgs& a, int h, int tx, int TX, const double* sR,
-                                             const double* sI) {
+__device__ __forceinline__ void half_point(const StepArgs& a, int h, int j, const double* sRj, const double* sIj,
+                                           int gstride) {
   using R = typename RT<W>::T;
   const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
-  const int gstride = n_th + 2 * rad;
   const size_t ws = (size_t)n_r * pitch;
   const size_t hs = (size_t)(n_r - 1) * pitch;
   const double* u = a.u_in;
   const R h4 = from_words<R>(a.h4);
-  for (int j = tx; j < n_th; j += TX) {
-    const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
-    const R uPR0 = ld_s<R>(u + 0 * W * ws + i0, ws), uPR1 = ld_s<R>(u + 0 * W * ws + i1, ws);
-    const R uPI0 = ld_s<R>(u + 1 * W * ws + i0, ws), uPI1 = ld_s<R>(u + 1 * W * ws + i1, ws);
-    const R uQR0 = ld_s<R>(u + 2 * W * ws + i0, ws), uQR1 = ld_s<R>(u + 2 * W * ws + i1, ws);
-    const R uQI0 = ld_s<R>(u + 3 * W * ws + i0, ws), uQI1 = ld_s<R>(u + 3 * W * ws + i1, ws);
-    const R sPR = ld_s<R>(sR + j + rad, gstride), sPI = ld_s<R>(sI + j + rad, gstride);
-    const R dPR = v_sub(uPR1, uPR0), dPI = v_sub(uPI1, uPI0);
-    const R sQR = v_add(uQR1, uQR0), sQI = v_add(uQI1, uQI0);
-    const R dQR = v_sub(uQR1, uQR0), dQI = v_sub(uQI1, uQI0);
-    const R LR = theta_op<R, W>(sR, gstride, a.wts, n_th, rad, j);
-    const R LI = theta_op<R, W>(sI, gstride, a.wts, n_th, rad, j);
-    const size_t ci = (size_t)h * pitch + j;
-    const R H0 = ld_r<R>(a.ch + 0 * W * hs + ci, hs), H1 = ld_r<R>(a.ch + 1 * W * hs + ci, hs);
-    const R H2 = ld_r<R>(a.ch + 2 * W * hs + ci, hs), H3 = ld_r<R>(a.ch + 3 * W * hs + ci, hs);
-    const R H4 = ld_r<R>(a.ch + 4 * W * hs + ci, hs), H5 = ld_r<R>(a.ch + 5 * W * hs + ci, hs);
-    const R H6 = ld_r<R>(a.ch + 6 * W * hs + ci, hs), H7 = ld_r<R>(a.ch + 7 * W * hs + ci, hs);
-    Acc<R> pr(v_half(sPR));
-    pr.mac(v_neg(H0), dPR);
-    pr.mac(h4, sQR);
-    Acc<R> pi(v_half(sPI));
-    pi.mac(v_neg(H0), dPI);
-    pi.mac(h4, sQI);
-    Acc<R> qr(mw::r_from<R>(0.0));
-    qr.mac(H3, sQR); qr.mac(H4, sQI); qr.mac(H0, dQR); qr.mac(H1, dPR); qr.mac(H2, dPI);
-    qr.mac(H5, LR); qr.mac(H6, sPR); qr.mac(v_neg(H7), sPI);
-    Acc<R> qi(mw::r_from<R>(0.0));
-    qi.mac(H3, sQI); qi.mac(v_neg(H4), sQR); qi.mac(H0, dQI); qi.mac(H1, dPI); qi.mac(v_neg(H2), dPR);
-    qi.mac(H5, LI); qi.mac(H6, sPI); qi.mac(H7, sPR);
-    st_r(a.uh + 0 * W * hs + ci, hs, pr.get());
-    st_r(a.uh + 1 * W * hs + ci, hs, pi.get());
-    st_r(a.uh + 2 * W * hs + ci, hs, qr.get());
-    st_r(a.uh + 3 * W * hs + ci, hs, qi.get());
-  }
+  const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
+  const R uPR0 = ld_s<R>(u + 0 * W * ws + i0, ws), uPR1 = ld_s<R>(u + 0 * W * ws + i1, ws);
+  const R uPI0 = ld_s<R>(u + 1 * W * ws + i0, ws), uPI1 = ld_s<R>(u + 1 * W * ws + i1, ws);
+  const R uQR0 = ld_s<R>(u + 2 * W * ws + i0, ws), uQR1 = ld_s<R>(u + 2 * W * ws + i1, ws);
+  const R uQI0 = ld_s<R>(u + 3 * W * ws + i0, ws), uQI1 = ld_s<R>(u + 3 * W * ws + i1, ws);
+  const R sPR = ld_s<R>(sRj + rad, gstride), sPI = ld_s<R>(sIj + rad, gstride);
+  const R dPR = v_sub(uPR1, uPR0), dPI = v_sub(uPI1, uPI0);
+  const R sQR = v_add(uQR1, uQR0), sQI = v_add(uQI1, uQI0);
+  const R dQR = v_sub(uQR1, uQR0), dQI = v_sub(uQI1, uQI0);
+  const R LR = theta_op<R, W>(sRj, gstride, a.wts, n_th, rad, j);
+  const R LI = theta_op<R, W>(sIj, gstride, a.wts, n_th, rad, j);
+  const size_t ci = (size_t)h * pitch + j;
+  const R H0 = ld_r<R>(a.ch + 0 * W * hs + ci, hs), H1 = ld_r<R>(a.ch + 1 * W * hs + ci, hs);
+  const R H2 = ld_r<R>(a.ch + 2 * W * hs + ci, hs), H3 = ld_r<R>(a.ch + 3 * W * hs + ci, hs);
+  const R H4 = ld_r<R>(a.ch + 4 * W * hs + ci, hs), H5 = ld_r<R>(a.ch + 5 * W * hs + ci, hs);
+  const R H6 = ld_r<R>(a.ch + 6 * W * hs + ci, hs), H7 = ld_r<R>(a.ch + 7 * W * hs + ci, hs);
+  Acc<R> pr(v_half(sPR));
+  pr.mac(v_neg(H0), dPR);
+  pr.mac(h4, sQR);
+  Acc<R> pi(v_half(sPI));
+  pi.mac(v_neg(H0), dPI);
+  pi.mac(h4, sQI);
+  Acc<R> qr(mw::r_from<R>(0.0));
+  qr.mac(H3, sQR); qr.mac(H4, sQI); qr.mac(H0, dQR); qr.mac(H1, dPR); qr.mac(H2, dPI);
+  qr.mac(H5, LR); qr.mac(H6, sPR); qr.mac(v_neg(H7), sPI);
+  Acc<R> qi(mw::r_from<R>(0.0));
+  qi.mac(H3, sQI); qi.mac(v_neg(H4), sQR); qi.mac(H0, dQI); qi.mac(H1, dPI); qi.mac(v_neg(H2), dPR);
+  qi.mac(H5, LI); qi.mac(H6, sPI); qi.mac(H7, sPR);
+  st_r(a.uh + 0 * W * hs + ci, hs, pr.get());
+  st_r(a.uh + 1 * W * hs + ci, hs, pi.get());
+  st_r(a.uh + 2 * W * hs + ci, hs, qr.get());
+  st_r(a.uh + 3 * W * hs + ci, hs, qi.get());
+}
+
+template <int W>
+__device__ __forceinline__ void half_row_out(const StepArgs& a, int h, int tx, int TX, const double* sR,
+                                             const double* sI) {
+  const int gstride = a.g.n_th + 2 * a.radius;
+  for (int j = tx; j < a.g.n_th; j += TX) half_point<W>(a, h, j, sR + j, sI + j, gstride);
 }
 
 // Eq. lw2, first phase at node i: s_Phi = Phi_{i+1/2} + Phi_{i-1/2} into the ghosted row.
@@ -526,63 +532,133 @@ __device__ __forceinline__ void full_row_prep(const StepArgs& a, int i, int tx, 
 //   Phi'  = Phi - N0 d_Phi + (h/2) s_Pi,
 //   Pi'_R = Pi_R + N0 d_PiR + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L(s_Phi)_R + N6 s_PhiR - N7 s_PhiI,
 //   Pi'_I = Pi_I + N0 d_PiI + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L(s_Phi)_I + N6 s_PhiI + N7 s_PhiR.
-// Returns true if a non-finite value was produced. `slot` is the observer ring slot to fill
-// (negative: none).
+// One point (i, j); returns true if a non-finite value was produced. `slot` is the observer
+// ring slot to fill (negative: none).
 template <int W>
-__device__ __forceinline__ bool full_row_out(const StepArgs& a, int i, int tx, int TX, const double* sR,
-                                             const double* sI, long long slot) {
+__device__ __forceinline__ bool full_point(const StepArgs& a, int i, int j, const double* sRj, const double* sIj,
+                                           int gstride, long long slot) {
   using R = typename RT<W>::T;
   const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
-  const int gstride = n_th + 2 * rad;
   const size_t ws = (size_t)n_r * pitch;
   const size_t hs = (size_t)(n_r - 1) * pitch;
   const double* uh = a.uh;
   const R h2 = from_words<R>(a.h2);
-  bool bad = false;
-  for (int j = tx; j < n_th; j += TX) {
-    const size_t p = (size_t)i * pitch + j, m = p - pitch;
-    const R hPR1 = ld_s<R>(uh + 0 * W * hs + p, hs), hPR0 = ld_s<R>(uh + 0 * W * hs + m, hs);
-    const R hPI1 = ld_s<R>(uh + 1 * W * hs + p, hs), hPI0 = ld_s<R>(uh + 1 * W * hs + m, hs);
-    const R hQR1 = ld_s<R>(uh + 2 * W * hs + p, hs), hQR0 = ld_s<R>(uh + 2 * W * hs + m, hs);
-    const R hQI1 = ld_s<R>(uh + 3 * W * hs + p, hs), hQI0 = ld_s<R>(uh + 3 * W * hs + m, hs);
-    const R sPR = ld_s<R>(sR + j + rad, gstride), sPI = ld_s<R>(sI + j + rad, gstride);
-    const R dPR = v_sub(hPR1, hPR0), dPI = v_sub(hPI1, hPI0);
-    const R sQR = v_add(hQR1, hQR0), sQI = v_add(hQI1, hQI0);
-    const R dQR = v_sub(hQR1, hQR0), dQI = v_sub(hQI1, hQI0);
-    const R LR = theta_op<R, W>(sR, gstride, a.wts, n_th, rad, j);
-    const R LI = theta_op<R, W>(sI, gstride, a.wts, n_th, rad, j);
-    const size_t ci = (size_t)i * pitch + j;
-    const R N0 = ld_r<R>(a.cn + 0 * W * ws + ci, ws), N1 = ld_r<R>(a.cn + 1 * W * ws + ci, ws);
-    const R N2 = ld_r<R>(a.cn + 2 * W * ws + ci, ws), N3 = ld_r<R>(a.cn + 3 * W * ws + ci, ws);
-    const R N4 = ld_r<R>(a.cn + 4 * W * ws + ci, ws), N5 = ld_r<R>(a.cn + 5 * W * ws + ci, ws);
-    const R N6 = ld_r<R>(a.cn + 6 * W * ws + ci, ws), N7 = ld_r<R>(a.cn + 7 * W * ws + ci, ws);
-    const R PR = ld_s<R>(a.u_in + 0 * W * ws + ci, ws), PI = ld_s<R>(a.u_in + 1 * W * ws + ci, ws);
-    const R QR = ld_s<R>(a.u_in + 2 * W * ws + ci, ws), QI = ld_s<R>(a.u_in + 3 * W * ws + ci, ws);
-    Acc<R> pr(PR);
-    pr.mac(v_neg(N0), dPR);
-    pr.mac(h2, sQR);
-    Acc<R> pi(PI);
-    pi.mac(v_neg(N0), dPI);
-    pi.mac(h2, sQI);
-    Acc<R> qr(QR);
-    qr.mac(N0, dQR); qr.mac(N1, dPR); qr.mac(N2, dPI); qr.mac(N3, sQR); qr.mac(N4, sQI);
-    qr.mac(N5, LR); qr.mac(N6, sPR); qr.mac(v_neg(N7), sPI);
-    Acc<R> qi(QI);
-    qi.mac(N0, dQI); qi.mac(N1, dPI); qi.mac(v_neg(N2), dPR); qi.mac(N3, sQI); qi.mac(v_neg(N4), sQR);
-    qi.mac(N5, LI); qi.mac(N6, sPI); qi.mac(N7, sPR);
-    const R oPR = pr.get(), oPI = pi.get(), oQR = qr.get(), oQI = qi.get();
-    st_r(a.u_out + 0 * W * ws + ci, ws, oPR);
-    st_r(a.u_out + 1 * W * ws + ci, ws, oPI);
-    st_r(a.u_out + 2 * W * ws + ci, ws, oQR);
-    st_r(a.u_out + 3 * W * ws + ci, ws, oQI);
-    bad |= nonfinite(lead_of(oPR)) | nonfinite(lead_of(oPI)) | nonfinite(lead_of(oQR)) | nonfinite(lead_of(oQI));
-    if (slot >= 0 && i == a.i_obs) {
-      double* dst = a.ring + (size_t)slot * 2 * W * n_th;
-      st_r(dst + 0 * W * n_th + j, n_th, oPR);
-      st_r(dst + 1 * W * n_th + j, n_th, oPI);
-    }
+  const size_t p = (size_t)i * pitch + j, m = p - pitch;
+  const R hPR1 = ld_s<R>(uh + 0 * W * hs + p, hs), hPR0 = ld_s<R>(uh + 0 * W * hs + m, hs);
+  const R hPI1 = ld_s<R>(uh + 1 * W * hs + p, hs), hPI0 = ld_s<R>(uh + 1 * W * hs + m, hs);
+  const R hQR1 = ld_s<R>(uh + 2 * W * hs + p, hs), hQR0 = ld_s<R>(uh + 2 * W * hs + m, hs);
+  const R hQI1 = ld_s<R>(uh + 3 * W * hs + p, hs), hQI0 = ld_s<R>(uh + 3 * W * hs + m, hs);
+  const R sPR = ld_s<R>(sRj + rad, gstride), sPI = ld_s<R>(sIj + rad, gstride);
+  const R dPR = v_sub(hPR1, hPR0), dPI = v_sub(hPI1, hPI0);
+  const R sQR = v_add(hQR1, hQR0), sQI = v_add(hQI1, hQI0);
+  const R dQR = v_sub(hQR1, hQR0), dQI = v_sub(hQI1, hQI0);
+  const R LR = theta_op<R, W>(sRj, gstride, a.wts, n_th, rad, j);
+  const R LI = theta_op<R, W>(sIj, gstride, a.wts, n_th, rad, j);
+  const size_t ci = (size_t)i * pitch + j;
+  const R N0 = ld_r<R>(a.cn + 0 * W * ws + ci, ws), N1 = ld_r<R>(a.cn + 1 * W * ws + ci, ws);
+  const R N2 = ld_r<R>(a.cn + 2 * W * ws + ci, ws), N3 = ld_r<R>(a.cn + 3 * W * ws + ci, ws);
+  const R N4 = ld_r<R>(a.cn + 4 * W * ws + ci, ws), N5 = ld_r<R>(a.cn + 5 * W * ws + ci, ws);
+  const R N6 = ld_r<R>(a.cn + 6 * W * ws + ci, ws), N7 = ld_r<R>(a.cn + 7 * W * ws + ci, ws);
+  const R PR = ld_s<R>(a.u_in + 0 * W * ws + ci, ws), PI = ld_s<R>(a.u_in + 1 * W * ws + ci, ws);
+  const R QR = ld_s<R>(a.u_in + 2 * W * ws + ci, ws), QI = ld_s<R>(a.u_in + 3 * W * ws + ci, ws);
+  Acc<R> pr(PR);
+  pr.mac(v_neg(N0), dPR);
+  pr.mac(h2, sQR);
+  Acc<R> pi(PI);
+  pi.mac(v_neg(N0), dPI);
+  pi.mac(h2, sQI);
+  Acc<R> qr(QR);
+  qr.mac(N0, dQR); qr.mac(N1, dPR); qr.mac(N2, dPI); qr.mac(N3, sQR); qr.mac(N4, sQI);
+  qr.mac(N5, LR); qr.mac(N6, sPR); qr.mac(v_neg(N7), sPI);
+  Acc<R> qi(QI);
+  qi.mac(N0, dQI); qi.mac(N1, dPI); qi.mac(v_neg(N2), dPR); qi.mac(N3, sQI); qi.mac(v_neg(N4), sQR);
+  qi.mac(N5, LI); qi.mac(N6, sPI); qi.mac(N7, sPR);
+  const R oPR = pr.get(), oPI = pi.get(), oQR = qr.get(), oQI = qi.get();
+  st_r(a.u_out + 0 * W * ws + ci, ws, oPR);
+  st_r(a.u_out + 1 * W * ws + ci, ws, oPI);
+  st_r(a.u_out + 2 * W * ws + ci, ws, oQR);
+  st_r(a.u_out + 3 * W * ws + ci, ws, oQI);
+  if (slot >= 0 && i == a.i_obs) {
+    double* dst = a.ring + (size_t)slot * 2 * W * n_th;
+    st_r(dst + 0 * W * n_th + j, n_th, oPR);
+    st_r(dst + 1 * W * n_th + j, n_th, oPI);
   }
+  return nonfinite(lead_of(oPR)) | nonfinite(lead_of(oPI)) | nonfinite(lead_of(oQR)) | nonfinite(lead_of(oQI));
+}
+
+template <int W>
+__device__ __forceinline__ bool full_row_out(const StepArgs& a, int i, int tx, int TX, const double* sR,
+                                             const double* sI, long long slot) {
+  const int gstride = a.g.n_th + 2 * a.radius;
+  bool bad = false;
+  for (int j = tx; j < a.g.n_th; j += TX) bad |= full_point<W>(a, i, j, sR + j, sI + j, gstride, slot);
   return bad;
+}
+
+// ---- warp-segment kernels: one warp per (row, 32 theta columns) --------------------------
+// Each warp computes the averaged Phi of its 32 columns plus `radius` columns on each side
+// (the halo is recomputed, with the parity reflection at the poles), synchronises only
+// itself, then produces its 32 points. Thousands of independent warps keep every SM's FP64
+// pipe busy to the end of the launch. V selects the register budget (<= 255, 128, 85).
+template <int W>
+__device__ __forceinline__ void seg_prep(const StepArgs& a, const double* src, size_t plane, int row0, int j0,
+                                         int lane, double* sR, double* sI) {
+  using R = typename RT<W>::T;
+  const int n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
+  const int gs = 32 + 2 * rad;
+  const int cmax = min(j0 + 31, n_th - 1) + rad;  // last column any lane needs
+  for (int idx = lane; idx < gs; idx += 32) {
+    const int c = j0 - rad + idx;
+    if (c > cmax) continue;
+    int cc = c;
+    bool ghost = false;
+    if (c < 0) { cc = -1 - c; ghost = true; }
+    else if (c >= n_th) { cc = 2 * n_th - 1 - c; ghost = true; }
+    const size_t k0 = (size_t)row0 * pitch + cc, k1 = k0 + pitch;
+    R sPR = v_add(ld_s<R>(src + 0 * W * plane + k1, plane), ld_s<R>(src + 0 * W * plane + k0, plane));
+    R sPI = v_add(ld_s<R>(src + 1 * W * plane + k1, plane), ld_s<R>(src + 1 * W * plane + k0, plane));
+    if (ghost && a.g.parity < 0) {
+      sPR = v_neg(sPR);
+      sPI = v_neg(sPI);
+    }
+    st_r(sR + idx, gs, sPR);
+    st_r(sI + idx, gs, sPI);
+  }
+}
+
+template <int W, int V = 0>
+__global__ void __launch_bounds__(128, 2 * (V + 1)) half_seg_kernel(StepArgs a, int nseg) {
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int h = unit / nseg, j0 = (unit % nseg) * 32;
+  if (h >= a.g.n_r - 1) return;  // whole warps only: no block-wide barrier below
+  const int gs = 32 + 2 * a.radius;
+  double* sR = sm + (size_t)warp * 2 * W * gs;
+  double* sI = sR + (size_t)W * gs;
+  seg_prep<W>(a, a.u_in, (size_t)a.g.n_r * a.g.pitch, h, j0, lane, sR, sI);
+  __syncwarp();
+  const int j = j0 + lane;
+  if (j < a.g.n_th) half_point<W>(a, h, j, sR + lane, sI + lane, gs);
+}
+
+template <int W, int V = 0>
+__global__ void __launch_bounds__(128, 2 * (V + 1)) full_seg_kernel(StepArgs a, int nseg) {
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int i = 1 + unit / nseg, j0 = (unit % nseg) * 32;
+  if (i >= a.g.n_r - 1) return;
+  const int gs = 32 + 2 * a.radius;
+  double* sR = sm + (size_t)warp * 2 * W * gs;
+  double* sI = sR + (size_t)W * gs;
+  seg_prep<W>(a, a.uh, (size_t)(a.g.n_r - 1) * a.g.pitch, i - 1, j0, lane, sR, sI);
+  __syncwarp();
+  const int j = j0 + lane;
+  long long slot = -1;
+  if (a.record) slot = a.ring_slot >= 0 ? a.ring_slot : (*a.ring_counter) % a.ring_cap;
+  const bool bad = j < a.g.n_th && full_point<W>(a, i, j, sR + lane, sI + lane, gs, slot);
+  if (bad) atomicOr(a.status, 1u);
 }
 
 // ---- single-problem kernels: blockDim.y rows per block, blockDim.x threads along theta ------

@@ -186,6 +186,21 @@ void step_shape(const teuk_s* h, dim3& blk) {
 template <int V>
 int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
   const int nh = h->n_r - 1, nf = h->n_r - 2;
+  if (h->kernel_family == 1) {
+    const int nseg = (h->n_th + 31) / 32;
+    const size_t seg_smem = (size_t)4 * 2 * W * (32 + 2 * h->radius) * sizeof(double);
+    const int64_t units_h = (int64_t)nh * nseg, units_f = (int64_t)nf * nseg;
+    cudaEvent_t ev = nullptr;
+    time_begin(h, &ev);
+    half_seg_kernel<W, V><<<(unsigned)((units_h + 3) / 4), 128, seg_smem, h->stream>>>(sa, nseg);
+    time_end(h, 0, ev);
+    time_begin(h, &ev);
+    full_seg_kernel<W, V><<<(unsigned)((units_f + 3) / 4), 128, seg_smem, h->stream>>>(sa, nseg);
+    time_end(h, 1, ev);
+    h->launches += 2;
+    TEUK_CUDA(h, cudaGetLastError());
+    return TEUK_OK;
+  }
   if (smem > 48 * 1024) {  // above the default dynamic limit (quad-double, n_theta > 700)
     TEUK_CUDA(h, cudaFuncSetAttribute(half_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TEUK_CUDA(h, cudaFuncSetAttribute(full_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -26,7 +26,8 @@ SYMBOLS = [
     "teuk_get_tortoise", "teuk_info", "teuk_kernel_launches", "teuk_strerror", "teuk_last_error",
     "teuk_mw_eval", "teuk_timing", "teuk_kernel_times", "teuk_fp64_peak", "teuk_substep_noalloc",
     "teuk_tune", "teuk_batch_create", "teuk_batch_step", "teuk_batch_sync", "teuk_batch_info",
-    "teuk_batch_destroy", "teuk_use_graphs",
+    "teuk_batch_destroy", "teuk_use_graphs", "teuk_launch_shape",
+    "teuk_set_launch_shape",
 ]
 
 
@@ -95,6 +96,8 @@ def lib(build_if_missing: bool = True):
         L.teuk_batch_info.argtypes = [vp, P(i32), P(i32), P(i64), P(i64)]
         L.teuk_batch_destroy.argtypes = [vp]
         L.teuk_use_graphs.argtypes = [vp, i32]
+        L.teuk_launch_shape.argtypes = [vp, P(i32), P(i32), P(i32)]
+        L.teuk_set_launch_shape.argtypes = [vp, i32, i32, i32]
         _lib = L
     return _lib
 
@@ -240,6 +243,16 @@ class Teuk:
         _check(lib().teuk_info(self._h, ctypes.byref(w), ctypes.byref(nr), ctypes.byref(nt),
                                ctypes.byref(k), ctypes.byref(dt)), self._h)
         return dict(words=w.value, n_r=nr.value, n_theta=nt.value, substeps=k.value, dt=dt.value)
+
+    def launch_shape(self):
+        tx, ty, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().teuk_launch_shape(self._h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(v)),
+               self._h)
+        return dict(threads_theta=tx.value, rows_per_block=ty.value, variant=v.value)
+
+    def set_launch_shape(self, threads_theta=128, rows_per_block=1, variant=0):
+        _check(lib().teuk_set_launch_shape(self._h, int(threads_theta), int(rows_per_block),
+                                           int(variant)), self._h)
 
     def use_graphs(self, enable=True):
         _check(lib().teuk_use_graphs(self._h, 1 if enable else 0), self._h)

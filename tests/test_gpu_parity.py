@@ -351,3 +351,24 @@ def test_graph_replay_matches_direct_launches(W):
         g1.sync()
         np.testing.assert_array_equal(g1.get_state(), g2.get_state())
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+@pytest.mark.parametrize("n_theta,parity_m", [(24, 2), (70, 1), (128, 2)])
+def test_launch_shapes_bitwise_identical(W, n_theta, parity_m):
+    """Every launch shape (rows per block, threads per row with several columns per thread,
+    register budgets, one warp per 32 columns with recomputed halos) gives the same bits."""
+    p = small(n_r=37, n_theta=n_theta, m=parity_m)
+    shapes = [(32, 1, 0), (64, 2, 1), (32, 8, 2), (0, 0, 3), (0, 0, 4), (0, 0, 5)]
+    ref = None
+    for tx, ty, v in shapes:
+        g = teuk.Teuk(precision=W, **p)
+        g.set_launch_shape(tx or 32, ty or 1, v)
+        g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+        g.step(2)
+        st = g.get_state()
+        if ref is None:
+            ref = st
+        else:
+            np.testing.assert_array_equal(st, ref, err_msg=f"shape {(tx, ty, v)}")
+        g.close()
