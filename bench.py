@@ -38,6 +38,14 @@ OPS_FULL = {1: 50, 2: 508, 4: 3736}
 BYTES_HALF = {w: (4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
 BYTES_FULL = {w: (4 + 4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
 DTYPE = {1: "f64", 2: "f64x2 (double-double)", 4: "f64x4 (quad-double)"}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the kernel as it stands: (workload, words, kernel) -> (bytes, profile summary).
+TRAFFIC = {("c2", 2, "half"): (50.41e6 + 0.27e6, "profiles/step_kernels_dd_c2.md"),
+           ("c2", 2, "full"): (67.15e6 + 0.55e6, "profiles/step_kernels_dd_c2.md"),
+           ("c5", 1, "half"): (864.57e6 + 260.51e6, "profiles/step_kernels_f64_c5.md"),
+           ("c5", 1, "full"): (1130.53e6 + 247.88e6, "profiles/step_kernels_f64_c5.md"),
+           ("c3", 4, "half"): (25.59e6 + 0.005e6, "profiles/step_kernels_qd_c3.md"),
+           ("c3", 4, "full"): (34.07e6 + 0.035e6, "profiles/step_kernels_qd_c3.md")}
 TOL = {1: 1e-12, 2: 1e-26, 4: 1e-55}
 
 
@@ -54,6 +62,9 @@ def parse():
                     help="workload of the main line (default c2, the benchmark configuration)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 4],
                     help="words per real (0: the workload's own precision)")
+    ap.add_argument("--shape", default="",
+                    help="pin the step kernels' launch shape 'threads_theta,rows,variant' "
+                         "instead of autotuning (profiling)")
     ap.add_argument("--digits", action="store_true",
                     help="print the cost-per-digit table (errors vs the oracle and each other)")
     return ap.parse_args()
@@ -104,13 +115,17 @@ def stop_clock_sampler(p, f, path, device_index):
 
 
 # ---------------------------------------------------------------------------------------------
-def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=True):
+def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=True, shape=""):
     """Device-resident timing of `steps` outer steps; returns a dict of measurements."""
     g = teuk.Teuk.from_problem(prob, precision=words)
     ar, ai = prob.amps
     g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
     g.set_observer(prob.rstar_obs, capacity=steps + warmup + 1)
-    g.tune()  # launch-shape autotuner, untimed set-up
+    if shape:
+        tx, ty, v = (int(x) for x in shape.split(","))
+        g.set_launch_shape(tx, ty, v)
+    else:
+        g.tune()  # launch-shape autotuner, untimed set-up
     rows_per_block = g.launch_shape()
     for _ in range(warmup):
         g.step(1)
@@ -446,7 +461,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     sampler = start_clock_sampler()
-    res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush)
+    res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush, shape=args.shape)
     clocks = stop_clock_sampler(*sampler, device_index=local)
     torch.cuda.synchronize()
     updates_per_rank = res["points"] * res["substeps"] * args.steps
@@ -472,9 +487,11 @@ def main():
         probe = teuk.fp64_peak()
         achieved = ops / (avg * 1e-3)
         traffic_note = None
+        tr = TRAFFIC.get((args.workload, W, dom))
         roofline = {
             "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": tr[0] if tr else None,
+            "traffic_source": tr[1] if tr else None,
             "kernel": f"{dom}_kernel<{W}>", "avg_launch_ms": avg,
             "launch_shape": res["rows_per_block"],
             "ops_per_point": OPS_HALF[W] if dom == "half" else OPS_FULL[W],
