@@ -506,7 +506,14 @@ template <int W>
 __device__ __forceinline__ void half_row_out(const StepArgs& a, int h, int tx, int TX, const double* sR,
                                              const double* sI) {
   const int gstride = a.g.n_th + 2 * a.radius;
-  for (int j = tx; j < a.g.n_th; j += TX) half_point<W>(a, h, j, sR + j, sI + j, gstride);
+  // two columns per iteration when a thread owns several: independent dependency chains that
+  // the scheduler interleaves (latency of chained FP64 operations)
+  int j = tx;
+  for (; j + TX < a.g.n_th; j += 2 * TX) {
+    half_point<W>(a, h, j, sR + j, sI + j, gstride);
+    half_point<W>(a, h, j + TX, sR + j + TX, sI + j + TX, gstride);
+  }
+  if (j < a.g.n_th) half_point<W>(a, h, j, sR + j, sI + j, gstride);
 }
 
 // Eq. lw2, first phase at node i: s_Phi = Phi_{i+1/2} + Phi_{i-1/2} into the ghosted row.
@@ -591,7 +598,12 @@ __device__ __forceinline__ bool full_row_out(const StepArgs& a, int i, int tx, i
                                              const double* sI, long long slot) {
   const int gstride = a.g.n_th + 2 * a.radius;
   bool bad = false;
-  for (int j = tx; j < a.g.n_th; j += TX) bad |= full_point<W>(a, i, j, sR + j, sI + j, gstride, slot);
+  int j = tx;
+  for (; j + TX < a.g.n_th; j += 2 * TX) {
+    bad |= full_point<W>(a, i, j, sR + j, sI + j, gstride, slot);
+    bad |= full_point<W>(a, i, j + TX, sR + j + TX, sI + j + TX, gstride, slot);
+  }
+  if (j < a.g.n_th) bad |= full_point<W>(a, i, j, sR + j, sI + j, gstride, slot);
   return bad;
 }
 
