@@ -77,7 +77,7 @@ int teuk_set_initial(teuk_t h, const double* phi_pi);
 /* Gaussian pulse Phi = A exp(-((r* - center)/width)^2) sY_{ell m}(theta) with A = amp_re +
  * i amp_im, zero initial time derivative (Pi = b Phi_{r*}), evaluated on the device in the
  * target precision; sY is the spin-weighted harmonic without its normalisation constant.
- * ell >= max(|m|, |s|). */
+ * max(|m|, |s|) <= ell <= 40. */
 int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re, double amp_im,
                            int ell);
 
@@ -102,6 +102,20 @@ int teuk_set_observer(teuk_t h, double rstar_obs, int64_t capacity);
 /* Copies the recorded samples, oldest first: out[n][2][w][n_theta], n = min(recorded,
  * capacity) returned in *n_samples. out may be NULL to query n only. */
 int teuk_read_waveform(teuk_t h, double* out, int64_t* n_samples);
+
+/* Multipoles of the recorded waveform (Sec. 3.C: the late-time decay of each multipole l of the
+ * field at the observer, Fig. 1): for every recorded sample t (oldest first) and
+ * l = ell_min .. ell_max,
+ *   c_l(t) = 2 pi int_0^pi Phi(t, r*_obs, theta) sY_lm(theta) sin(theta) dtheta,
+ * sY_lm the normalised spin-weighted spherical harmonic of the handle's s and m (Goldberg et
+ * al. 1967 sum with the (-1)^m sign, phi = 0). Quadrature: Fejer's first rule in x = cos(theta)
+ * on the cell centres, exact when Phi sY_lm is a polynomial in x of degree < n_theta. Weights,
+ * harmonics and sums are in the handle's precision, on the device.
+ * Needs max(|m|, |s|) <= ell_min <= ell_max <= min(40, n_theta - 1) and an observer
+ * (TEUK_ERR_STATE_MISMATCH otherwise). out: host [n][ell_max - ell_min + 1][2 (re, im)][w]
+ * doubles, or NULL to query n only; *n_samples = n = min(recorded, capacity). Synchronises
+ * the handle's stream. */
+int teuk_read_multipoles(teuk_t h, int ell_min, int ell_max, double* out, int64_t* n_samples);
 
 /* Whole state as host word planes [4][w][n_r][n_theta], and the substep counter. */
 int teuk_get_state(teuk_t h, double* planes, int64_t* substeps_done);

@@ -83,6 +83,9 @@ def lib():
         L.oracle_theta_op.argtypes = [i32, i32, i32, i32, dp, i32, dp, i32]
         L.oracle_spin_profile.argtypes = [i32, i32, i32, i32, i32, dp, i32]
         L.oracle_set_row.argtypes = [vp, i32, dp, i32]
+        L.oracle_fejer_weights.argtypes = [i32, i32, dp, i32]
+        L.oracle_swsh.argtypes = [i32, i32, i32, i32, i32, dp, dp, i32]
+        L.oracle_project.argtypes = [i32, i32, i32, i32, i32, i32, dp, i32, i64, dp, i32]
         L.oracle_set_threads.argtypes = [i32]
         L.oracle_max_threads.restype = i32
         _lib = L
@@ -253,6 +256,35 @@ def spin_profile(s, m, ell, n_theta, *, bits=256, out_words=5) -> np.ndarray:
     if lib().oracle_spin_profile(int(bits), int(s), int(m), int(ell), int(n_theta), _dp(out),
                                  out_words):
         raise ValueError("oracle_spin_profile")
+    return out
+
+
+def fejer_weights(n_theta, *, bits=256, out_words=5) -> np.ndarray:
+    """Fejer's first-rule weights on the cell-centred theta grid: [out_words, n_theta]."""
+    out = np.empty((out_words, n_theta))
+    if lib().oracle_fejer_weights(int(bits), int(n_theta), _dp(out), out_words):
+        raise ValueError("oracle_fejer_weights")
+    return out
+
+
+def swsh(s, m, ell, theta, *, bits=256, out_words=5) -> np.ndarray:
+    """Normalised spin-weighted spherical harmonic sY_lm(theta, phi = 0): [out_words, n]."""
+    th = np.ascontiguousarray(np.atleast_1d(theta), dtype=np.float64)
+    out = np.empty((out_words, th.size))
+    if lib().oracle_swsh(int(bits), int(s), int(m), int(ell), th.size, _dp(th), _dp(out), out_words):
+        raise ValueError("oracle_swsh")
+    return out
+
+
+def project(s, m, ell_min, ell_max, samples, *, bits=256, out_words=5) -> np.ndarray:
+    """Multipoles c_l(t) = 2 pi int Phi sY_lm sin(theta) dtheta of recorded samples given as
+    word expansions [n][2][words][n_theta]: [n][ell_max - ell_min + 1][2][out_words]."""
+    x = np.ascontiguousarray(samples, dtype=np.float64)
+    n, two, words, nth = x.shape
+    out = np.empty((n, ell_max - ell_min + 1, 2, out_words))
+    if lib().oracle_project(int(bits), int(s), int(m), int(nth), int(ell_min), int(ell_max), _dp(x),
+                            int(words), int(n), _dp(out), out_words):
+        raise ValueError("oracle_project")
     return out
 
 

@@ -738,6 +738,125 @@ int oracle_spin_profile(int bits, int s, int m, int ell, int nth, double* out, i
 
 }  // extern "C"
 
+namespace {
+
+// ------------------------------------------------------------------------------------
+// Multipoles of the observed field (Sec. 3.C, Fig. 1): the tail of each multipole l is
+// read from c_l(t) = 2 pi int_0^pi Phi(t, theta) sY_lm(theta) sin(theta) dtheta.
+// ------------------------------------------------------------------------------------
+
+// Fejer's first quadrature rule on [-1, 1] with the N nodes x_j = cos(theta_j),
+// theta_j = (j + 1/2) pi / N (the solver's cell centres):
+//   w_j = (2/N) [1 - 2 sum_{k=1}^{floor(N/2)} cos(2 k theta_j) / (4 k^2 - 1)].
+template <class T>
+T fejer_weight(int N, int j) {
+  const T th = (T(double(j)) + T(0.5)) * pi_<T>() / T(double(N));
+  T sum = T(0.0);
+  for (int k = 1; k <= N / 2; ++k) sum = sum + cos_(T(2.0 * k) * th) / T(4.0 * k * k - 1.0);
+  return T(2.0) / T(double(N)) * (T(1.0) - T(2.0) * sum);
+}
+
+// n! as an exact product in T (exact in double up to 18!, in 256-bit MPFR far beyond).
+template <class T>
+T factorial(int n) {
+  T r = T(1.0);
+  for (int t = 2; t <= n; ++t) r = r * T(double(t));
+  return r;
+}
+
+// Binomial coefficient C(n, k) as a ratio of factorials in T (0 outside 0 <= k <= n).
+template <class T>
+T binomial(int n, int k) {
+  if (n < 0 || k < 0 || k > n) return T(0.0);
+  return factorial<T>(n) / (factorial<T>(k) * factorial<T>(n - k));
+}
+
+// Normalised spin-weighted spherical harmonic at phi = 0 (Goldberg et al. 1967):
+//   sY_lm = (-1)^m sqrt((2l+1)/(4 pi) (l+m)!(l-m)!/((l+s)!(l-s)!))
+//           sum_r C(l-s, r) C(l+s, r+s-m) (-1)^(l-r-s) sin(th/2)^(2l-2r-s+m) cos(th/2)^(2r+s-m).
+template <class T>
+T swsh(int s, int m, int l, const T& theta) {
+  const T sh = sin_(theta * T(0.5)), ch = cos_(theta * T(0.5));
+  T sum = T(0.0);
+  for (int r = 0; r <= l - s; ++r) {
+    const T c = binomial<T>(l - s, r) * binomial<T>(l + s, r + s - m);
+    T term = ((l - r - s) % 2 == 0) ? c : -c;
+    for (int e = 0; e < 2 * l - 2 * r - s + m; ++e) term = term * sh;
+    for (int e = 0; e < 2 * r + s - m; ++e) term = term * ch;
+    sum = sum + term;
+  }
+  const T norm = sqrt_(T(double(2 * l + 1)) / (T(4.0) * pi_<T>()) * factorial<T>(l + m) * factorial<T>(l - m) /
+                       (factorial<T>(l + s) * factorial<T>(l - s)));
+  return (m % 2 == 0 ? norm : -norm) * sum;
+}
+
+// c[t][l][part] = 2 pi sum_j w_j sY_lm(theta_j) Phi[t][part][j] for samples given as word
+// expansions [n][2][words][nth]; out [n][n_ell][2][out_words].
+template <class T>
+void project(int s, int m, int nth, int ell_min, int ell_max, const double* samples, int words, int64_t n,
+             double* out, int out_words) {
+  const int n_ell = ell_max - ell_min + 1;
+  const T pi = pi_<T>();
+  std::vector<T> tab((size_t)n_ell * nth);
+  for (int l = ell_min; l <= ell_max; ++l)
+    for (int j = 0; j < nth; ++j) {
+      const T th = (T(double(j)) + T(0.5)) * pi / T(double(nth));
+      tab[(size_t)(l - ell_min) * nth + j] = T(2.0) * pi * fejer_weight<T>(nth, j) * swsh<T>(s, m, l, th);
+    }
+#pragma omp parallel for schedule(dynamic)
+  for (int64_t t = 0; t < n; ++t)
+    for (int l = 0; l < n_ell; ++l)
+      for (int part = 0; part < 2; ++part) {
+        const double* f = samples + ((size_t)t * 2 + part) * words * nth;
+        T acc = T(0.0);
+        for (int j = 0; j < nth; ++j) acc = acc + tab[(size_t)l * nth + j] * from_words<T>(f + j, words, nth);
+        to_words(acc, out + (((size_t)t * n_ell + l) * 2 + part) * out_words, out_words, 1);
+      }
+}
+
+}  // namespace
+
+extern "C" {
+
+// Fejer weights of the nth-cell grid: out [out_words][nth].
+int oracle_fejer_weights(int bits, int nth, double* out, int out_words) {
+  if (nth < 1) return -1;
+  if (bits <= 53) {
+    for (int j = 0; j < nth; ++j) to_words(fejer_weight<double>(nth, j), out + j, out_words, nth);
+    return 0;
+  }
+  g_bits = bits;
+  for (int j = 0; j < nth; ++j) to_words(fejer_weight<mp>(nth, j), out + j, out_words, nth);
+  return 0;
+}
+
+// Normalised sY_lm at the given angles: out [out_words][n].
+int oracle_swsh(int bits, int s, int m, int ell, int n, const double* theta, double* out, int out_words) {
+  if (ell < std::abs(s) || ell < std::abs(m)) return -1;
+  if (bits <= 53) {
+    for (int j = 0; j < n; ++j) to_words(swsh<double>(s, m, ell, theta[j]), out + j, out_words, n);
+    return 0;
+  }
+  g_bits = bits;
+  for (int j = 0; j < n; ++j) to_words(swsh<mp>(s, m, ell, mp(theta[j])), out + j, out_words, n);
+  return 0;
+}
+
+// Multipoles of recorded samples (see project above).
+int oracle_project(int bits, int s, int m, int nth, int ell_min, int ell_max, const double* samples, int words,
+                   int64_t n, double* out, int out_words) {
+  if (ell_min < std::abs(s) || ell_min < std::abs(m) || ell_max < ell_min || nth < 1) return -1;
+  if (bits <= 53) {
+    project<double>(s, m, nth, ell_min, ell_max, samples, words, n, out, out_words);
+    return 0;
+  }
+  g_bits = bits;
+  project<mp>(s, m, nth, ell_min, ell_max, samples, words, n, out, out_words);
+  return 0;
+}
+
+}  // extern "C"
+
 extern "C" {
 
 // Overwrites one theta row of the state (window-relative row index) from in [4][words][nth]:

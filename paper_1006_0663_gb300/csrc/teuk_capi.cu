@@ -296,8 +296,8 @@ int teuk_set_initial(teuk_t h, const double* phi_pi) {
 
 int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re, double amp_im, int ell) {
   if (!h) return TEUK_ERR_INVALID_ARG;
-  if (ell < std::abs(h->m) || ell < std::abs(h->s) || !(width > 0) || !std::isfinite(center))
-    return invalid(h, "pulse: need ell >= max(|m|, |s|), width > 0");
+  if (ell < std::abs(h->m) || ell < std::abs(h->s) || ell > 40 || !(width > 0) || !std::isfinite(center))
+    return invalid(h, "pulse: need max(|m|, |s|) <= ell <= 40, width > 0");
   int rc;
   switch (h->W) {
     case 1: rc = teuk::pulse_w1(h, center, width, amp_re, amp_im, ell); break;
@@ -413,6 +413,24 @@ int teuk_read_waveform(teuk_t h, double* out, int64_t* n_samples) {
   }
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   return TEUK_OK;
+}
+
+int teuk_read_multipoles(teuk_t h, int ell_min, int ell_max, double* out, int64_t* n_samples) {
+  if (!h || !n_samples) return TEUK_ERR_INVALID_ARG;
+  const int lo = std::max(std::abs(h->m), std::abs(h->s));
+  if (ell_min < lo || ell_max < ell_min || ell_max > 40 || ell_max >= h->n_th)
+    return invalid(h, "multipoles: need max(|m|, |s|) <= ell_min <= ell_max <= min(40, n_theta - 1)");
+  if (!h->ring) return TEUK_ERR_STATE_MISMATCH;
+  const int64_t n = h->n_recorded < h->ring_cap ? h->n_recorded : h->ring_cap;
+  *n_samples = n;
+  if (!out || n == 0) return TEUK_OK;
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int64_t first = h->n_recorded - n;  // oldest sample kept
+  switch (h->W) {
+    case 1: return teuk::project_w1(h, ell_min, ell_max, out, n, first);
+    case 2: return teuk::project_w2(h, ell_min, ell_max, out, n, first);
+    default: return teuk::project_w4(h, ell_min, ell_max, out, n, first);
+  }
 }
 
 int teuk_get_state(teuk_t h, double* planes, int64_t* substeps_done) {

@@ -80,6 +80,9 @@ int substep_w4(teuk_s* h, bool record, int64_t slot);
 int substep_buffers_w1(teuk_s* h, const double* u_in, double* u_out, double* scratch);
 int substep_buffers_w2(teuk_s* h, const double* u_in, double* u_out, double* scratch);
 int substep_buffers_w4(teuk_s* h, const double* u_in, double* u_out, double* scratch);
+int project_w1(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);
+int project_w2(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);
+int project_w4(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);
 int mw_eval_w1(int op, int device, const double* a, const double* b, double* out, int64_t n);
 int mw_eval_w2(int op, int device, const double* a, const double* b, double* out, int64_t n);
 int mw_eval_w4(int op, int device, const double* a, const double* b, double* out, int64_t n);

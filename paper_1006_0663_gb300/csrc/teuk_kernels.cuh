@@ -369,6 +369,36 @@ __global__ void pulse_kernel(PulseArgs a) {
   st_r(a.u + 3 * W * ws + idx, ws, r_mul(b, r_mul_d(GpY, a.amp_im)));
 }
 
+// ---- multipole projection of the recorded waveform (Sec. 3.C, Fig. 1) ----------------------
+struct ProjectArgs {
+  int n_th, n_ell;
+  long long n, first, cap;  // samples, absolute index of the oldest one, ring capacity
+  const double* ring;       // [cap][2][W][n_th]: Phi(i_obs, theta_j) per outer step
+  const double* table;      // [n_ell][W][n_th]: quadrature weight x 2 pi x sY_lm(theta_j)
+  double* out;              // [n][n_ell][2][W]
+};
+
+// c_l(t) = sum_j T_l(theta_j) Phi(t, theta_j): one dot product in the target precision per
+// (sample, l, real/imaginary part), so that multipoles tens of orders of magnitude below the
+// leading one keep their digits.
+template <int W>
+__global__ void project_kernel(ProjectArgs a) {
+  using R = typename RT<W>::T;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.n * a.n_ell * 2) return;
+  const int part = (int)(idx % 2);
+  const int l = (int)((idx / 2) % a.n_ell);
+  const long long t = idx / (2 * a.n_ell);
+  const size_t n_th = (size_t)a.n_th;
+  const double* src = a.ring + (size_t)((a.first + t) % a.cap) * 2 * W * n_th + (size_t)part * W * n_th;
+  const double* tab = a.table + (size_t)l * W * n_th;
+  Acc<R> acc(mw::r_from<R>(0.0));
+  for (int j = 0; j < a.n_th; ++j) acc.mac(ld_r<R>(tab + j, n_th), ld_s<R>(src + j, n_th));
+  double w[4];
+  to_words(acc.get(), w);
+  for (int k = 0; k < W; ++k) a.out[(size_t)idx * W + k] = w[k];
+}
+
 // ---- the Lax-Wendroff substep ----------------------------------------------------------------
 struct StepArgs {
   Geom g;
@@ -458,6 +488,8 @@ __device__ __forceinline__ void half_row_prep(const StepArgs& a, int h, int tx, 
 //   Phi_h  = s_Phi/2 - H0 d_Phi + (h/4) s_Pi,
 //   Pi_h,R = H3 s_PiR + H4 s_PiI + H0 d_PiR + H1 d_PhiR + H2 d_PhiI + H5 L(s_Phi)_R + H6 s_PhiR - H7 s_PhiI,
 //   Pi_h,I = H3 s_PiI - H4 s_PiR + H0 d_PiI + H1 d_PhiI - H2 d_PhiR + H5 L(s_Phi)_I + H6 s_PhiI + H7 s_PhiR.
+// d_Pi is used once, so H0 d_Pi enters the dot product as the two terms H0 Pi_{h+1} and
+// -H0 Pi_h (in double-double one Dot2 term costs 9 FP64 operations, an accurate subtraction 14).
 // One point (h, j); sRj / sIj point at the ghosted s_Phi entries of column j - radius.
 template <int W>
 __device__ __forceinline__ void half_point(const StepArgs& a, int h, int j, const double* sRj, const double* sIj,
@@ -476,7 +508,6 @@ __device__ __forceinline__ void half_point(const StepArgs& a, int h, int j, cons
   const R sPR = ld_s<R>(sRj + rad, gstride), sPI = ld_s<R>(sIj + rad, gstride);
   const R dPR = v_sub(uPR1, uPR0), dPI = v_sub(uPI1, uPI0);
   const R sQR = v_add(uQR1, uQR0), sQI = v_add(uQI1, uQI0);
-  const R dQR = v_sub(uQR1, uQR0), dQI = v_sub(uQI1, uQI0);
   const R LR = theta_op<R, W>(sRj, gstride, a.wts, n_th, rad, j);
   const R LI = theta_op<R, W>(sIj, gstride, a.wts, n_th, rad, j);
   const size_t ci = (size_t)h * pitch + j;
@@ -491,10 +522,11 @@ __device__ __forceinline__ void half_point(const StepArgs& a, int h, int j, cons
   pi.mac(v_neg(H0), dPI);
   pi.mac(h4, sQI);
   Acc<R> qr(mw::r_from<R>(0.0));
-  qr.mac(H3, sQR); qr.mac(H4, sQI); qr.mac(H0, dQR); qr.mac(H1, dPR); qr.mac(H2, dPI);
+  qr.mac(H3, sQR); qr.mac(H4, sQI); qr.mac(H0, uQR1); qr.mac(v_neg(H0), uQR0); qr.mac(H1, dPR); qr.mac(H2, dPI);
   qr.mac(H5, LR); qr.mac(H6, sPR); qr.mac(v_neg(H7), sPI);
   Acc<R> qi(mw::r_from<R>(0.0));
-  qi.mac(H3, sQI); qi.mac(v_neg(H4), sQR); qi.mac(H0, dQI); qi.mac(H1, dPI); qi.mac(v_neg(H2), dPR);
+  qi.mac(H3, sQI); qi.mac(v_neg(H4), sQR); qi.mac(H0, uQI1); qi.mac(v_neg(H0), uQI0); qi.mac(H1, dPI);
+  qi.mac(v_neg(H2), dPR);
   qi.mac(H5, LI); qi.mac(H6, sPI); qi.mac(H7, sPR);
   st_r(a.uh + 0 * W * hs + ci, hs, pr.get());
   st_r(a.uh + 1 * W * hs + ci, hs, pi.get());
@@ -539,6 +571,7 @@ __device__ __forceinline__ void full_row_prep(const StepArgs& a, int i, int tx, 
 //   Phi'  = Phi - N0 d_Phi + (h/2) s_Pi,
 //   Pi'_R = Pi_R + N0 d_PiR + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L(s_Phi)_R + N6 s_PhiR - N7 s_PhiI,
 //   Pi'_I = Pi_I + N0 d_PiI + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L(s_Phi)_I + N6 s_PhiI + N7 s_PhiR.
+// As in the half step, N0 d_Pi enters as the two terms N0 Pi_{i+1/2} and -N0 Pi_{i-1/2}.
 // One point (i, j); returns true if a non-finite value was produced. `slot` is the observer
 // ring slot to fill (negative: none).
 template <int W>
@@ -558,7 +591,6 @@ __device__ __forceinline__ bool full_point(const StepArgs& a, int i, int j, cons
   const R sPR = ld_s<R>(sRj + rad, gstride), sPI = ld_s<R>(sIj + rad, gstride);
   const R dPR = v_sub(hPR1, hPR0), dPI = v_sub(hPI1, hPI0);
   const R sQR = v_add(hQR1, hQR0), sQI = v_add(hQI1, hQI0);
-  const R dQR = v_sub(hQR1, hQR0), dQI = v_sub(hQI1, hQI0);
   const R LR = theta_op<R, W>(sRj, gstride, a.wts, n_th, rad, j);
   const R LI = theta_op<R, W>(sIj, gstride, a.wts, n_th, rad, j);
   const size_t ci = (size_t)i * pitch + j;
@@ -575,10 +607,11 @@ __device__ __forceinline__ bool full_point(const StepArgs& a, int i, int j, cons
   pi.mac(v_neg(N0), dPI);
   pi.mac(h2, sQI);
   Acc<R> qr(QR);
-  qr.mac(N0, dQR); qr.mac(N1, dPR); qr.mac(N2, dPI); qr.mac(N3, sQR); qr.mac(N4, sQI);
-  qr.mac(N5, LR); qr.mac(N6, sPR); qr.mac(v_neg(N7), sPI);
+  qr.mac(N0, hQR1); qr.mac(v_neg(N0), hQR0); qr.mac(N1, dPR); qr.mac(N2, dPI); qr.mac(N3, sQR);
+  qr.mac(N4, sQI); qr.mac(N5, LR); qr.mac(N6, sPR); qr.mac(v_neg(N7), sPI);
   Acc<R> qi(QI);
-  qi.mac(N0, dQI); qi.mac(N1, dPI); qi.mac(v_neg(N2), dPR); qi.mac(N3, sQI); qi.mac(v_neg(N4), sQR);
+  qi.mac(N0, hQI1); qi.mac(v_neg(N0), hQI0); qi.mac(N1, dPI); qi.mac(v_neg(N2), dPR); qi.mac(N3, sQI);
+  qi.mac(v_neg(N4), sQR);
   qi.mac(N5, LI); qi.mac(N6, sPI); qi.mac(N7, sPR);
   const R oPR = pr.get(), oPI = pi.get(), oQR = qr.get(), oQI = qi.get();
   st_r(a.u_out + 0 * W * ws + ci, ws, oPR);

@@ -130,27 +130,38 @@ double binom(int n, int k) {
   return std::round(r);
 }
 
+// Goldberg et al. (1967) sum of sY_lm(theta), without its normalisation and e^{i m phi}:
+//   sum_r (-1)^(l-r-s) C(l-s, r) C(l+s, r+s-m) sin(th/2)^(2l-2r-s+m) cos(th/2)^(2r+s-m).
+// The binomial coefficients are exact doubles for l <= 40; their product is formed in R.
+R goldberg_sum(int ell, int s, int m, R sh, R ch) {
+  R sum = r_from<R>(0.0);
+  for (int r = 0; r <= ell - s; ++r) {
+    const double b1 = binom(ell - s, r), b2 = binom(ell + s, r + s - m);
+    if (b1 == 0.0 || b2 == 0.0) continue;
+    R term = r_mul(r_from<R>(b1), r_from<R>(b2));
+    if ((ell - r - s) % 2 != 0) term = r_neg(term);
+    for (int e = 0; e < 2 * ell - 2 * r - s + m; ++e) term = r_mul(term, sh);
+    for (int e = 0; e < 2 * r + s - m; ++e) term = r_mul(term, ch);
+    sum = r_add(sum, term);
+  }
+  return sum;
+}
+
+// sin(theta_j / 2), cos(theta_j / 2) at the cell centre theta_j = (j + 1/2) pi / n_theta.
+void half_angle(const R& pi, int n_th, int j, R& sh, R& ch) {
+  const R dth = r_div(pi, r_from<R>(double(n_th)));
+  const R half_th = r_scale2(r_mul_d(dth, double(j) + 0.5), 0.5);
+  r_sincos(half_th, pi, sh, ch);
+}
+
 int pulse_impl(teuk_s* h, double center, double width, double ar, double ai, int ell) {
   const int n_th = h->n_th, s = h->s, m = h->m;
   const R pi = r_pi<R>();
-  const R dth = r_div(pi, r_from<R>(double(n_th)));
-  // sY_{ell m}(theta) without its normalisation (Goldberg et al. 1967 sum):
-  //   sum_r (-1)^(l-r-s) C(l-s, r) C(l+s, r+s-m) sin(th/2)^(2l-2r-s+m) cos(th/2)^(2r+s-m)
   std::vector<double> prof((size_t)W * n_th);
   for (int j = 0; j < n_th; ++j) {
-    const R half_th = r_scale2(r_mul_d(dth, double(j) + 0.5), 0.5);
     R sh, ch;
-    r_sincos(half_th, pi, sh, ch);
-    R sum = r_from<R>(0.0);
-    for (int r = 0; r <= ell - s; ++r) {
-      const double c = binom(ell - s, r) * binom(ell + s, r + s - m);
-      if (c == 0.0) continue;
-      R term = r_from<R>(((ell - r - s) % 2 == 0) ? c : -c);
-      for (int e = 0; e < 2 * ell - 2 * r - s + m; ++e) term = r_mul(term, sh);
-      for (int e = 0; e < 2 * r + s - m; ++e) term = r_mul(term, ch);
-      sum = r_add(sum, term);
-    }
-    store_plane(prof, n_th, j, sum);
+    half_angle(pi, n_th, j, sh, ch);
+    store_plane(prof, n_th, j, goldberg_sum(ell, s, m, sh, ch));
   }
   TEUK_CUDA(h, cudaMemcpyAsync(h->prof, prof.data(), prof.size() * 8, cudaMemcpyHostToDevice, h->stream));
   PulseArgs pa{};
@@ -167,6 +178,98 @@ int pulse_impl(teuk_s* h, double center, double width, double ar, double ai, int
   pulse_kernel<W><<<dim3((n_th + 63) / 64, h->n_r), 64, 0, h->stream>>>(pa);
   TEUK_CUDA(h, cudaGetLastError());
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+// Multipole projection of the recorded waveform (Sec. 3.C: the tail of each multipole l of
+// the field seen by an observer, Fig. 1). For l = ell_min .. ell_max:
+//   c_l(t) = 2 pi int_0^pi Phi(t, theta) sY_lm(theta) sin(theta) dtheta
+// with the normalised harmonic sY_lm = (-1)^m sqrt((2l+1)/(4 pi) (l+m)!(l-m)!/((l+s)!(l-s)!))
+// x goldberg_sum. With x = cos(theta) the integral is int_{-1}^{1} Phi sY dx, and the cell
+// centres x_j = cos((j + 1/2) pi / N) are the nodes of Fejer's first rule, weights
+//   w_j = (2/N) [1 - 2 sum_{k=1}^{floor(N/2)} cos(2 k theta_j) / (4 k^2 - 1)],
+// exact for polynomials of degree < N (the integrand of a regular field is a polynomial in x
+// times its smooth amplitude). The cosines are cos(pi q / (2N)) with the integer
+// q = 2k(2j+1) reduced exactly to the first quadrant.
+int project_impl(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first) {
+  const int n_th = h->n_th, s = h->s, m = h->m, n_ell = ell_max - ell_min + 1;
+  const R pi = r_pi<R>();
+  // quarter-wave table cos(pi q / (2N)), q = 0 .. N
+  std::vector<R> qc(n_th + 1);
+  const R step = r_scale2(r_div(pi, r_from<R>(double(n_th))), 0.5);
+  for (int q = 0; q <= n_th; ++q) {
+    R sq, cq;
+    r_sincos(r_mul_d(step, double(q)), pi, sq, cq);
+    qc[q] = cq;
+  }
+  qc[0] = r_from<R>(1.0);
+  qc[n_th] = r_from<R>(0.0);
+  auto cos_q = [&](long long q) -> R {
+    q %= 4LL * n_th;
+    if (q > 2LL * n_th) q = 4LL * n_th - q;        // cos(2 pi - x) = cos(x)
+    if (q > n_th) return r_neg(qc[2 * n_th - q]);  // cos(pi - x) = -cos(x)
+    return qc[q];
+  };
+  std::vector<R> inv_k(n_th / 2 + 1);
+  for (int k = 1; k <= n_th / 2; ++k) inv_k[k] = r_div(r_from<R>(1.0), r_from<R>(4.0 * k * k - 1.0));
+  std::vector<R> wq(n_th);
+  for (int j = 0; j < n_th; ++j) {
+    R sum = r_from<R>(0.0);
+    for (int k = 1; k <= n_th / 2; ++k) sum = r_add(sum, r_mul(cos_q(2LL * k * (2 * j + 1)), inv_k[k]));
+    // 2 pi w_j = (4 pi / N) (1 - 2 sum)
+    wq[j] = r_mul(r_div(r_scale2(pi, 4.0), r_from<R>(double(n_th))), r_sub(r_from<R>(1.0), r_scale2(sum, 2.0)));
+  }
+  std::vector<double> table((size_t)n_ell * W * n_th);
+  for (int l = ell_min; l <= ell_max; ++l) {
+    // (l+m)!(l-m)! / ((l+s)!(l-s)!) as a product of exact integer ratios
+    R ratio = r_from<R>(1.0);
+    for (int t = 2; t <= l + m; ++t) ratio = r_mul_d(ratio, double(t));
+    for (int t = 2; t <= l - m; ++t) ratio = r_mul_d(ratio, double(t));
+    for (int t = 2; t <= l + s; ++t) ratio = r_div_d(ratio, double(t));
+    for (int t = 2; t <= l - s; ++t) ratio = r_div_d(ratio, double(t));
+    R norm = r_sqrt(r_div(r_mul_d(ratio, double(2 * l + 1)), r_scale2(pi, 4.0)));
+    if (m % 2 != 0) norm = r_neg(norm);
+    std::vector<double> row((size_t)W * n_th);
+    for (int j = 0; j < n_th; ++j) {
+      R sh, ch;
+      half_angle(pi, n_th, j, sh, ch);
+      store_plane(row, n_th, j, r_mul(wq[j], r_mul(norm, goldberg_sum(l, s, m, sh, ch))));
+    }
+    std::memcpy(table.data() + (size_t)(l - ell_min) * W * n_th, row.data(), row.size() * sizeof(double));
+  }
+  double* d_table = nullptr;
+  double* d_out = nullptr;
+  const size_t n_out = (size_t)n * n_ell * 2 * W;
+  auto release = [&]() {
+    if (d_table) cudaFree(d_table);
+    if (d_out) cudaFree(d_out);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&d_table, table.size() * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_out, n_out * sizeof(double))) != cudaSuccess) {
+    release();
+    return cuda_fail(h, e, "cudaMalloc (projection)");
+  }
+  ProjectArgs pa{};
+  pa.n_th = n_th;
+  pa.n_ell = n_ell;
+  pa.n = n;
+  pa.first = first;
+  pa.cap = h->ring_cap;
+  pa.ring = h->ring;
+  pa.table = d_table;
+  pa.out = d_out;
+  const long long threads = (long long)n * n_ell * 2;
+  if ((e = cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream)) == cudaSuccess) {
+    project_kernel<W><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(pa);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  release();
+  if (e != cudaSuccess) return cuda_fail(h, e, "projection");
   return TEUK_OK;
 }
 
@@ -379,6 +482,9 @@ int TEUK_SUFFIX(pulse_w)(teuk_s* h, double center, double width, double ar, doub
   return pulse_impl(h, center, width, ar, ai, ell);
 }
 int TEUK_SUFFIX(substep_w)(teuk_s* h, bool record, int64_t slot) { return substep_impl(h, record, slot); }
+int TEUK_SUFFIX(project_w)(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first) {
+  return project_impl(h, ell_min, ell_max, out, n, first);
+}
 int TEUK_SUFFIX(substep_buffers_w)(teuk_s* h, const double* u_in, double* u_out, double* scratch) {
   return substep_buffers_impl(h, u_in, u_out, scratch);
 }

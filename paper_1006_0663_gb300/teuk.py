@@ -27,7 +27,7 @@ SYMBOLS = [
     "teuk_mw_eval", "teuk_timing", "teuk_kernel_times", "teuk_fp64_peak", "teuk_substep_noalloc",
     "teuk_tune", "teuk_batch_create", "teuk_batch_step", "teuk_batch_sync", "teuk_batch_info",
     "teuk_batch_destroy", "teuk_use_graphs", "teuk_launch_shape",
-    "teuk_set_launch_shape",
+    "teuk_set_launch_shape", "teuk_read_multipoles",
 ]
 
 
@@ -72,6 +72,7 @@ def lib(build_if_missing: bool = True):
         L.teuk_observe.argtypes = [vp, d, dp, dp]
         L.teuk_set_observer.argtypes = [vp, d, i64]
         L.teuk_read_waveform.argtypes = [vp, dp, P(i64)]
+        L.teuk_read_multipoles.argtypes = [vp, i32, i32, dp, P(i64)]
         L.teuk_get_state.argtypes = [vp, dp, P(i64)]
         L.teuk_set_state.argtypes = [vp, dp, i64]
         L.teuk_get_state_device.argtypes = [vp, vp]
@@ -209,6 +210,17 @@ class Teuk:
         out = np.empty((n.value, 2, self.words, self.n_theta))
         if n.value:
             _check(lib().teuk_read_waveform(self._h, _dp(out), ctypes.byref(n)), self._h)
+        return out
+
+    def read_multipoles(self, ell_min, ell_max):
+        """Multipoles c_l(t) of the recorded waveform, computed on the device in the handle's
+        precision: array [n_samples][ell_max - ell_min + 1][2 (re, im)][words]."""
+        n = ctypes.c_int64()
+        _check(lib().teuk_read_multipoles(self._h, int(ell_min), int(ell_max), None, ctypes.byref(n)), self._h)
+        out = np.empty((n.value, ell_max - ell_min + 1, 2, self.words))
+        if n.value:
+            _check(lib().teuk_read_multipoles(self._h, int(ell_min), int(ell_max), _dp(out), ctypes.byref(n)),
+                   self._h)
         return out
 
     def get_state(self):

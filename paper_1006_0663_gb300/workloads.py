@@ -14,7 +14,9 @@ below are the benchmark configurations the library is measured on:
   40000 steps;
 * ``c4``: 64 double-double instances of uneven size, 5000 steps each;
 * ``c5``: FP64 and double-double, a = 0.9, s = -2, m = 2, r* in [-200, 1800] x 16384,
-  theta x 512, 2000 steps.
+  theta x 512, 2000 steps;
+* ``tails``: quad-double, a = 0.9, s = 0, m = 0, l' = 0 pulse, r* in [-760, 840] x 3201,
+  theta x 48, 12000 steps (t = 1500 M), observer at r* = 50 (the Kerr-tails study).
 
 Every instance has dt = 0.25 dr* as its outer (sampling) step, integrated with
 ``substeps`` Lax-Wendroff iterations of dt/substeps; ``substeps`` is fixed per workload
@@ -122,7 +124,15 @@ C2 = Problem("c2", 1.0, 0.9, -2, 2, -100.0, 400.0, 2048, 128, 40000, 88, 2, 2, 2
 C3 = Problem("c3", 1.0, 0.99, 0, 0, -100.0, 400.0, 1024, 64, 40000, 20, 4, 0, 3)
 C5 = Problem("c5", 1.0, 0.9, -2, 2, -200.0, 1800.0, 16384, 512, 2000, 81, 1, 2, 5, rstar_obs=1000.0)
 
-CONFIGS = {p.name: p for p in (C1, C2, C3, C5)}
+# Kerr-tails study (Sec. 3.C, Fig. 1): a scalar field (s = 0, m = 0) started as a pure l' = 0
+# Gaussian pulse on a = 0.9, observed at r* = 50 for t = 1500 M. The r* boundaries are far
+# enough that what they reflect (from 15 pulse widths ahead of the pulse centre on) reaches
+# the observer only after t = 1500 M, so the late-time field there is the boundary-free tail.
+# Quad-double: the multipoles l = 0..8 of the late field are tens of orders of magnitude apart.
+TAILS = Problem("tails", 1.0, 0.9, 0, 0, -760.0, 840.0, 3201, 48, 12000, 9, 4, 0, 7, center=25.0,
+                width=4.0, rstar_obs=50.0)
+
+CONFIGS = {p.name: p for p in (C1, C2, C3, C5, TAILS)}
 
 BATCH_SIZE = 64
 BATCH_STEPS = 5000

@@ -137,7 +137,8 @@ def test_evolution_parity(oracle_mod, W, case):
     assert err < TOL[W], err
 
 
-@pytest.mark.parametrize("W,name,nsub", [(2, "c2", 12), (4, "c3", 8), (1, "c5", 40), (1, "c1", 60)])
+@pytest.mark.parametrize("W,name,nsub", [(2, "c2", 12), (4, "c3", 8), (1, "c5", 40), (1, "c1", 60),
+                                        (4, "tails", 8)])
 def test_full_size_sampled_parity(oracle_mod, W, name, nsub):
     """Workload at its full size in the benchmark's launch configuration; the oracle
     computes a window of rows, exact in its interior after nsub iterations (one row per
@@ -372,3 +373,65 @@ def test_launch_shapes_bitwise_identical(W, n_theta, parity_m):
         else:
             np.testing.assert_array_equal(st, ref, err_msg=f"shape {(tx, ty, v)}")
         g.close()
+
+
+MULTIPOLE_CASES = [
+    dict(a=0.9, s=0, m=0, n_theta=24, ell0=0),                  # scalar, l = 0 data (Fig. 1 set-up)
+    dict(a=0.7, s=-2, m=2, n_theta=33, ell0=2),                 # ragged theta, even parity
+    dict(a=0.6, s=-1, m=2, n_theta=20, n_r=45, ell0=2),         # odd parity (m + s odd)
+]
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+@pytest.mark.parametrize("case", range(len(MULTIPOLE_CASES)))
+def test_multipole_parity(oracle_mod, W, case):
+    """Device multipoles c_l(t) of the recorded waveform against the oracle's projection of its
+    own evolution (same problem, 256-bit), l = l_min .. l_min + 7."""
+    c = dict(MULTIPOLE_CASES[case])
+    ell0 = c.pop("ell0")
+    p = small(**c)
+    g, o = make_pair(oracle_mod, p, W)
+    g.set_initial_pulse(12.0, 4.0, 0.8, 0.55, ell0)
+    o.pulse(12.0, 4.0, 0.8, 0.55, ell0)
+    robs = 20.0
+    outer = 5
+    g.set_observer(robs, capacity=outer)
+    _, used = g.observe(robs)
+    dr = (p["rstar_max"] - p["rstar_min"]) / (p["n_r"] - 1)
+    i_obs = int(round((used - p["rstar_min"]) / dr))
+    lo = max(abs(p["m"]), abs(p["s"]))
+    hi = lo + 7
+    samples = []
+    for _ in range(outer):
+        g.step(1)
+        o.step(p["substeps"])
+        samples.append(o.get_row(i_obs, words=5)[:2])  # Phi_R, Phi_I: [2][5][n_theta]
+    g.sync()
+    cg = g.read_multipoles(lo, hi)                       # [n][n_ell][2][W]
+    co = oracle_mod.project(p["s"], p["m"], lo, hi, np.array(samples), bits=256, out_words=5)
+    assert cg.shape == (outer, hi - lo + 1, 2, W)
+    scale = max(np.abs(np.array(samples)[:, :, 0]).max(), 1e-300)
+    diff = np.zeros(cg.shape[:3])
+    for k in reversed(range(5)):
+        diff = diff + ((cg[..., k] if k < W else 0.0) - co[..., k])
+    err = np.abs(diff).max() / scale
+    assert np.abs(co[:, 0, :, 0]).max() > 1e-3 * scale
+    assert err < TOL[W], err
+
+
+def test_multipoles_of_waveform_ring_wraparound():
+    """With more outer steps than ring slots, the multipoles follow the kept samples (oldest
+    first), identical to projecting the same samples recorded in a larger ring."""
+    p = small(s=0, m=0, a=0.9, n_theta=24)
+    g1 = teuk.Teuk(precision=2, **p)
+    g2 = teuk.Teuk(precision=2, **p)
+    for g, cap in ((g1, 3), (g2, 16)):
+        g.set_initial_pulse(12.0, 4.0, 0.8, 0.55, 0)
+        g.set_observer(20.0, capacity=cap)
+        g.step(7)
+    m1 = g1.read_multipoles(0, 6)
+    m2 = g2.read_multipoles(0, 6)
+    assert m1.shape[0] == 3 and m2.shape[0] == 7
+    np.testing.assert_array_equal(m1, m2[4:])
+    with pytest.raises(teuk.TeukError):
+        g1.read_multipoles(0, 24)   # l_max >= n_theta

@@ -41,6 +41,8 @@ def test_strerror_and_invalid_arguments():
     assert L.teuk_create(ctypes.byref(h), 1.0, 0.5, -2, 2, ctypes.byref(g), 3, None) == teuk.ERR_INVALID_ARG
     g = teuk.TeukGrid(-10.0, 10.0, 64, 16, 0.0, 1, 4, 0, 0)  # theta order 4 unsupported
     assert L.teuk_create(ctypes.byref(h), 1.0, 0.5, -2, 2, ctypes.byref(g), 1, None) == teuk.ERR_INVALID_ARG
+    n = ctypes.c_int64()
+    assert L.teuk_read_multipoles(None, 0, 4, None, ctypes.byref(n)) == teuk.ERR_INVALID_ARG
 
 
 def _rand_words(rng, words, n, spread=True):
