@@ -1,0 +1,37 @@
+"""Writes tests/golden/substeps.json: the Lax-Wendroff iterations per outer step k of every
+workload, from the oracle's stability analysis (oracle/stability.py) and nothing else.
+
+The paper gives no time-step rule (Sec. 3.B states only that the scheme is stable). The
+reading adopted: k is the smallest integer for which the excess amplification of the worst
+local mode of the discrete operator, over the whole run, stays below 10x.
+
+    python tests/golden/make_substeps.py
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle.stability import analyse  # noqa: E402
+from paper_1006_0663_gb300 import workloads  # noqa: E402
+
+
+def main():
+    out = {"reading": "smallest k with (worst excess amplification)^(steps k) <= 10; "
+                      "oracle/stability.py", "configs": {}, "batch": []}
+    for name, p in workloads.CONFIGS.items():
+        k, lam = analyse(p)
+        out["configs"][name] = {"substeps": k, "max_abs_lambda": lam}
+        print(name, k, lam, flush=True)
+    for i in range(workloads.BATCH_SIZE):
+        k, lam = analyse(workloads.batch_member(i, substeps=1))
+        out["batch"].append(k)
+        print(f"c4[{i}]", k, flush=True)
+    with open(os.path.join(HERE, "substeps.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()
