@@ -40,13 +40,22 @@ BYTES_HALF = {w: (4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
 BYTES_FULL = {w: (4 + 4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
 DTYPE = {1: "f64", 2: "f64x2 (double-double)", 4: "f64x4 (quad-double)"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the kernel as it stands: (workload, words, kernel) -> (bytes, profile summary).
-TRAFFIC = {("c2", 2, "half"): (50.41e6 + 0.27e6, "profiles/step_kernels_dd_c2.md"),
-           ("c2", 2, "full"): (67.15e6 + 0.55e6, "profiles/step_kernels_dd_c2.md"),
-           ("c5", 1, "half"): (864.57e6 + 260.51e6, "profiles/step_kernels_f64_c5.md"),
-           ("c5", 1, "full"): (1130.53e6 + 247.88e6, "profiles/step_kernels_f64_c5.md"),
-           ("c3", 4, "half"): (25.59e6 + 0.005e6, "profiles/step_kernels_qd_c3.md"),
-           ("c3", 4, "full"): (34.07e6 + 0.035e6, "profiles/step_kernels_qd_c3.md")}
+# the kernel as it stands: (workload, kernel function) -> (bytes, launch shape captured, summary).
+TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profiles/step_kernels_dd_c2.txt"),
+           ("c2", "full_kernel<2, 1>"): (67.192e6 + 0.623e6, "128 x 1", "profiles/step_kernels_dd_c2.txt"),
+           ("c5", "half_kernel<1, 0>"): (830.65e6 + 248.21e6, "64 x 1", "profiles/step_kernels_f64_c5.txt"),
+           ("c5", "full_kernel<1, 0>"): (1085.83e6 + 247.52e6, "64 x 1", "profiles/step_kernels_f64_c5.txt"),
+           ("c3", "half_kernel<4, 0>"): (25.95e6, "32 x 1", "profiles/step_kernels_qd_c3.txt"),
+           ("c3", "full_kernel<4, 0>"): (34.35e6, "32 x 1", "profiles/step_kernels_qd_c3.txt")}
+
+
+def kernel_name(dom, W, shape):
+    """The step kernel a launch shape selects (teuk_launch_shape variants 0..8)."""
+    v = shape["variant"]
+    fam = "" if v < 3 else ("seg_" if v < 6 else "bal_")
+    return f"{dom}_{fam}kernel<{W}, {v % 3}>"
+
+
 TOL = {1: 1e-12, 2: 1e-26, 4: 1e-55}
 
 
@@ -269,6 +278,39 @@ def run_e2e(prob, words, steps, torch, teuk):
                 d2h_bytes_per_step=int(obs.nbytes))
 
 
+def run_design_a(prob, words, iters, torch, teuk):
+    """The data flow of the paper's first CUDA design (Sec. 4) on this machine's CPU-GPU link:
+    the host keeps the state and every Lax-Wendroff iteration copies it to the device and
+    back (page-locked host memory, one cudaMemcpy2DAsync each way, the host waits), with all
+    arithmetic on the device. Against the same iterations with the state resident in HBM."""
+    g = teuk.Teuk.from_problem(prob, precision=words)
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    g.tune()
+    state = g.get_state()
+    pinned = torch.empty(state.shape, dtype=torch.float64, pin_memory=True)
+    host = pinned.numpy()
+    host[...] = state
+    g.substep_host_state(host, 2)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.substep_host_state(host, iters)
+    t_a = time.perf_counter() - t0
+    g.set_state(host)
+    g.substep(2)
+    g.sync()
+    t0 = time.perf_counter()
+    g.substep(iters)
+    g.sync()
+    t_r = time.perf_counter() - t0
+    g.close()
+    upd = prob.n_r * prob.n_theta * iters
+    link = 2 * state.nbytes
+    return {"updates_per_s": upd / t_a, "resident_updates_per_s": upd / t_r, "slowdown": t_a / t_r,
+            "iterations": iters, "link_bytes_per_iteration": link,
+            "link_gbps_effective": link * iters / (t_a - t_r) / 1e9 if t_a > t_r else None}
+
+
 def cpu_baseline(prob, words, seconds_target=15.0):
     """The oracle (256-bit MPFR for dd/qd workloads, FP64 for FP64) on all host cores, on a
     window of rows of the same workload for a bounded number of iterations."""
@@ -487,13 +529,13 @@ def main():
         peak = 2.0 * sms * mhz * 1e6
         probe = teuk.fp64_peak()
         achieved = ops / (avg * 1e-3)
-        traffic_note = None
-        tr = TRAFFIC.get((args.workload, W, dom))
+        kname = kernel_name(dom, W, res["rows_per_block"])
+        tr = TRAFFIC.get((args.workload, kname))
         roofline = {
             "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": tr[0] if tr else None,
-            "traffic_source": tr[1] if tr else None,
-            "kernel": f"{dom}_kernel<{W}>", "avg_launch_ms": avg,
+            "traffic_source": f"{tr[2]} (launch shape {tr[1]})" if tr else None,
+            "kernel": kname, "avg_launch_ms": avg,
             "launch_shape": res["rows_per_block"],
             "ops_per_point": OPS_HALF[W] if dom == "half" else OPS_FULL[W],
             "peak_source": f"2 FP64 ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (SM clock sampled "
@@ -519,6 +561,12 @@ def main():
             ups, msps = run_batch1(workloads.CONFIGS["c1"], 1, 20, torch, teuk)
             variants["c1/f64 batched kernel"] = {"updates_per_s": ups, "ms_per_step": msps,
                                                  "launch": "one cooperative launch, 20 steps"}
+            p2 = prob.with_(theta_order=2)
+            r = run_workload(p2, W, 2, 1, torch, teuk, flush, with_timing=False)
+            variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} 2nd-order theta"] = {
+                "updates_per_s": p2.points * p2.substeps * 2 / (r["ms_total"] * 1e-3),
+                "ms_per_step": r["ms_total"] / 2, "launch": "CUDA graph per outer step"}
+            variants["design_a_host_state"] = run_design_a(prob, W, 2 * prob.substeps, torch, teuk)
         batched = None if args.no_batch else run_c4(torch, teuk, workloads)
         cpu = None if args.no_cpu else cpu_baseline(prob, W)
         parity = None if args.no_cpu else stated_error(prob, W, teuk)

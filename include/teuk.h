@@ -81,6 +81,19 @@ int teuk_set_initial(teuk_t h, const double* phi_pi);
 int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re, double amp_im,
                            int ell);
 
+/* r* dissipation. NOT part of the paper's method (sigma = 0, the default, is the paper's
+ * scheme). With several Lax-Wendroff iterations per dt = 0.25 dr*, the scheme's own damping
+ * of short r* wavelengths is too weak for long runs: modes of near-zero numerical group
+ * velocity grow where the lower-order terms of the system (c Phi_{r*}, V/Sigma^2 Phi) make a
+ * frozen wave grow. With sigma > 0, every outer step (whenever the iteration count is a
+ * multiple of substeps) begins with
+ *   u_i <- u_i - eps (u_{i-2} - 4 u_{i-1} + 6 u_i - 4 u_{i+1} + u_{i+2}),  eps = sigma dt / (16 dr*),
+ * for all four components at rows 2 .. n_r - 3 (fourth-order Kreiss-Oliger dissipation over
+ * one outer step; an O(dr*^3) change for smooth fields). 0 <= sigma <= 4. Allocates one
+ * state-sized device buffer. Handles with sigma > 0 cannot join a batch or use
+ * teuk_substep_noalloc. */
+int teuk_set_dissipation(teuk_t h, double sigma);
+
 /* Advances n outer steps (n * substeps Lax-Wendroff iterations), asynchronously on the
  * handle's stream. The observer ring (if any) gets one sample per outer step. */
 int teuk_step(teuk_t h, int64_t n_outer_steps);
@@ -102,6 +115,15 @@ int teuk_set_observer(teuk_t h, double rstar_obs, int64_t capacity);
 /* Copies the recorded samples, oldest first: out[n][2][w][n_theta], n = min(recorded,
  * capacity) returned in *n_samples. out may be NULL to query n only. */
 int teuk_read_waveform(teuk_t h, double* out, int64_t* n_samples);
+
+/* The data flow of the paper's first CUDA design (Sec. 4): the time loop runs on the host and
+ * every iteration the state travels from main memory to the GPU and back, which over PCIe
+ * gave no overall gain. Here all arithmetic stays on the device: each of the n iterations
+ * copies host_planes [4][w][n_r][n_theta] (host memory, page-locked for full link speed) to
+ * the device, runs one Lax-Wendroff iteration (Eqs. lw1, lw2), copies the state back and
+ * waits for it. Rows 0 and n_r-1 are used as given (keep them zero, Sec. 3.B). The caller
+ * owns host_planes; the device state of the handle is overwritten. */
+int teuk_substep_host_state(teuk_t h, double* host_planes, int64_t n);
 
 /* Multipoles of the recorded waveform (Sec. 3.C: the late-time decay of each multipole l of the
  * field at the observer, Fig. 1): for every recorded sample t (oldest first) and
@@ -156,18 +178,22 @@ int teuk_batch_info(teuk_batch_t b, int* grid_blocks, int* k_max, int64_t* point
                     int64_t* launches);
 int teuk_batch_destroy(teuk_batch_t b);
 
-/* Autotuner: times a few Lax-Wendroff iterations for each candidate launch shape (rows of
- * theta per thread block) on a copy of the current state, keeps the fastest for this handle,
- * restores the state and returns the choice in *rows_per_block (may be NULL). Allocates and
- * frees one state-sized device buffer; call it before timing-critical work. */
+/* Autotuner: times a few Lax-Wendroff iterations for each candidate launch shape (threads
+ * along theta x rows of theta per thread block, one warp per 32 columns, register budgets)
+ * on a copy of the current state, keeps the fastest for this handle, restores the state and
+ * returns in *rows_per_block (may be NULL) the rows per block of the chosen shape, 0 when the
+ * one-warp-per-32-columns kernels won (teuk_launch_shape reports the whole shape). Allocates
+ * and frees one state-sized device buffer; call it before timing-critical work. */
 int teuk_tune(teuk_t h, int* rows_per_block);
 /* The step kernels' launch shape in use: threads along theta per row, rows per block, and the
  * kernel variant: 0, 1, 2 = whole rows per block with <= 255, 128, 85 registers per thread;
- * 3, 4, 5 = one warp per (row, 32 theta columns) with the same three register budgets. */
+ * 3, 4, 5 = one warp per (row, 32 theta columns) with the same three register budgets;
+ * 6, 7, 8 = balanced: as many blocks of threads_theta threads as fit on the GPU at once,
+ * each taking the same number of (row, theta) points, same three budgets. */
 int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant);
 /* Sets the launch shape explicitly (same meaning as above; threads_theta a multiple of 32,
- * threads_theta * rows_per_block <= 256; both ignored for variants 3..5). Results do not
- * depend on the shape. */
+ * threads_theta * rows_per_block <= 256; both ignored for variants 3..5, rows_per_block
+ * ignored for 6..8). Results do not depend on the shape. */
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant);
 
 /* Lax-Wendroff iterations that allocate nothing, for callers that cannot let a library

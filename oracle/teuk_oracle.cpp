@@ -114,6 +114,7 @@ struct oracle_params {
   int32_t theta_order;  // 10 (Sec. 3.D) or 2 (Sec. 3.B)
   int32_t parity;       // +1 or -1: sign of the reflection of Phi, Pi across each pole
   int32_t row_lo, row_hi;  // window of r* rows simulated (inclusive), 0 .. n_r-1 for all
+  double ko_sigma;         // r* dissipation strength (not in the paper; 0 = off), see dissipate()
 };
 
 }  // extern "C"
@@ -226,7 +227,7 @@ struct Solver {
     if (p.theta_order != 10 && p.theta_order != 2) return -1;
     if (p.parity != 1 && p.parity != -1) return -1;
     if (p.row_lo < 0 || p.row_hi >= p.n_r || p.row_hi - p.row_lo < 2) return -1;
-    if (!(p.rstar_max > p.rstar_min) || !(p.dt >= 0)) return -1;
+    if (!(p.rstar_max > p.rstar_min) || !(p.dt >= 0) || !(p.ko_sigma >= 0)) return -1;
     nrow = p.row_hi - p.row_lo + 1;
     nth = p.n_theta;
     M = T(p.M);
@@ -330,7 +331,34 @@ struct Solver {
   }
 
   // One Lax-Wendroff iteration with step dts (Eqs. lw1, lw2), then the r* boundary rows.
+  // r* dissipation (NOT part of the paper's method; off unless ko_sigma > 0). The two-step
+  // Lax-Wendroff iteration damps short r* wavelengths only at a rate ~ (dt/dr*)^2 per
+  // iteration; with several iterations per dt = 0.25 dr* that damping is too weak for the
+  // modes of near-zero numerical group velocity in the region where the lower-order terms
+  // of the r^3-scaled system (c Phi' and V/Sigma^2 Phi) make a frozen wave grow. Once per
+  // outer step, before its first iteration, every component at rows 2 .. n_r - 3 becomes
+  //   u_i - eps (u_{i-2} - 4 u_{i-1} + 6 u_i - 4 u_{i+1} + u_{i+2}),  eps = sigma dt / (16 dr*),
+  // the fourth-order Kreiss-Oliger operator integrated over dt (an O(dr*^3) change for
+  // smooth fields). Window edges stay frozen as in substep().
+  void dissipate() {
+    const T eps = T(p.ko_sigma) * dt / (T(16.0) * dr);
+    const int lo = std::max(2, 2 - p.row_lo), hi = std::min(nrow - 3, p.n_r - 3 - p.row_lo);
+    for (int c = 0; c < 4; ++c) {
+      un[c] = u[c];
+#pragma omp parallel for schedule(static)
+      for (int i = lo; i <= hi; ++i)
+        for (int j = 0; j < nth; ++j) {
+          const size_t k = (size_t)i * nth + j, n = (size_t)nth;
+          const T d4 = u[c][k - 2 * n] - T(4.0) * u[c][k - n] + T(6.0) * u[c][k] - T(4.0) * u[c][k + n] +
+                       u[c][k + 2 * n];
+          un[c][k] = u[c][k] - eps * d4;
+        }
+      std::swap(u[c], un[c]);
+    }
+  }
+
   void substep() {
+    if (p.ko_sigma > 0 && substeps_done % p.substeps == 0) dissipate();
     const T half = T(0.5);
     const T hdt = dts * half;
     // Eq. lw1: u^{n+1/2}_{i+1/2} = (u_{i+1} + u_i)/2 - dt/2 [D (u_{i+1} - u_i)/dr - S^n_{i+1/2}].

@@ -89,7 +89,7 @@ int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members) {
   b->device = b->members[0]->device;
   b->stream = b->members[0]->stream;
   for (teuk_s* h : b->members)
-    if (h->W != b->W || h->device != b->device) { delete b; return TEUK_ERR_INVALID_ARG; }
+    if (h->W != b->W || h->device != b->device || h->ko_sigma > 0) { delete b; return TEUK_ERR_INVALID_ARG; }
   // members with more iterations per outer step first: the active items of round q are a prefix
   std::stable_sort(b->members.begin(), b->members.end(), [](const teuk_s* x, const teuk_s* y) { return x->k > y->k; });
   std::vector<int> item_member;

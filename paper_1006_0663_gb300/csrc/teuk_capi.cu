@@ -26,6 +26,27 @@ int dispatch_substep(teuk_s* h, bool record, int64_t slot) {
   }
 }
 
+int dispatch_dissipate(teuk_s* h) {
+  switch (h->W) {
+    case 1: return teuk::dissipate_w1(h);
+    case 2: return teuk::dissipate_w2(h);
+    default: return teuk::dissipate_w4(h);
+  }
+}
+
+// One Lax-Wendroff iteration, preceded by the r* dissipation step when it is enabled and an
+// outer step begins (the iteration count is a multiple of k).
+int iterate(teuk_s* h, bool record, int64_t slot) {
+  if (h->ko_sigma > 0 && h->substeps_done % h->k == 0) {
+    int rc = dispatch_dissipate(h);
+    if (rc) return rc;
+  }
+  int rc = dispatch_substep(h, record, slot);
+  if (rc) return rc;
+  ++h->substeps_done;
+  return TEUK_OK;
+}
+
 int invalid(teuk_s* h, const char* msg) {
   if (h) h->last_error = msg;
   return TEUK_ERR_INVALID_ARG;
@@ -35,7 +56,7 @@ void drop_graph(teuk_s* h);
 
 void free_all(teuk_s* h) {
   double** bufs[] = {&h->u, &h->uh, &h->cn_raw, &h->ch_raw, &h->cn, &h->ch, &h->wts, &h->sin_th,
-                     &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring};
+                     &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring, &h->u_ko};
   for (double** b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -93,18 +114,26 @@ void drop_graph(teuk_s* h) {
 
 bool graphs_possible(const teuk_s* h) {
   const cudaStream_t legacy = (cudaStream_t)0x1;
-  return h->use_graphs && !h->timing && h->stream != nullptr && h->stream != legacy;
+  return h->use_graphs && !h->timing && h->stream != nullptr && h->stream != legacy &&
+         (h->ko_sigma == 0 || h->substeps_done % h->k == 0);
 }
 
 // Captures one outer step: k iterations, the last one recording the observer row at slot
 // *d_ring_counter % cap, then the counter increment.
 int build_graph(teuk_s* h, bool record) {
   drop_graph(h);
+  int prc;
+  switch (h->W) {  // host-side set-up of the launch shape stays outside the capture
+    case 1: prc = teuk::prepare_w1(h); break;
+    case 2: prc = teuk::prepare_w2(h); break;
+    default: prc = teuk::prepare_w4(h); break;
+  }
+  if (prc != TEUK_OK) return prc;
   const int64_t launches = h->launches;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return teuk::cuda_fail(h, e, "cudaStreamBeginCapture");
-  int rc = TEUK_OK;
+  int rc = h->ko_sigma > 0 ? dispatch_dissipate(h) : TEUK_OK;
   for (int q = 0; q < h->k && rc == TEUK_OK; ++q) rc = dispatch_substep(h, record && q == h->k - 1, -1);
   if (rc == TEUK_OK && record) advance_counter_kernel<<<1, 1, 0, h->stream>>>(h->d_ring_counter);
   e = cudaStreamEndCapture(h->stream, &graph);
@@ -312,9 +341,25 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
 int teuk_substep(teuk_t h, int64_t n) {
   if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
   for (int64_t t = 0; t < n; ++t) {
-    int rc = dispatch_substep(h, false, 0);
+    int rc = iterate(h, false, 0);
     if (rc) return rc;
-    ++h->substeps_done;
+  }
+  return TEUK_OK;
+}
+
+int teuk_substep_host_state(teuk_t h, double* host_planes, int64_t n) {
+  if (!h || !host_planes || n < 0) return TEUK_ERR_INVALID_ARG;
+  const size_t dpitch = (size_t)h->pitch * sizeof(double), hpitch = (size_t)h->n_th * sizeof(double);
+  const size_t height = (size_t)4 * h->W * h->n_r;
+  for (int64_t t = 0; t < n; ++t) {
+    TEUK_CUDA(h, cudaMemcpy2DAsync(h->u, dpitch, host_planes, hpitch, hpitch, height, cudaMemcpyHostToDevice,
+                                   h->stream));
+    int rc = iterate(h, false, 0);
+    if (rc) return rc;
+    TEUK_CUDA(h, cudaMemcpy2DAsync(host_planes, hpitch, h->u, dpitch, hpitch, height, cudaMemcpyDeviceToHost,
+                                   h->stream));
+    // the host loop owns the state between iterations
+    TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   return TEUK_OK;
 }
@@ -324,6 +369,22 @@ int teuk_use_graphs(teuk_t h, int enable) {
   h->use_graphs = enable != 0;
   if (!h->use_graphs) drop_graph(h);
   return TEUK_OK;
+}
+
+int teuk_set_dissipation(teuk_t h, double sigma) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (!(sigma >= 0) || !std::isfinite(sigma) || sigma > 4.0)
+    return invalid(h, "dissipation: need 0 <= sigma <= 4");
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (sigma > 0 && !h->u_ko)
+    TEUK_CUDA(h, cudaMalloc(&h->u_ko, (size_t)4 * h->W * h->n_r * h->pitch * sizeof(double)));
+  h->ko_sigma = sigma;
+  drop_graph(h);
+  switch (h->W) {
+    case 1: return teuk::dissipation_w1(h, sigma);
+    case 2: return teuk::dissipation_w2(h, sigma);
+    default: return teuk::dissipation_w4(h, sigma);
+  }
 }
 
 int teuk_step(teuk_t h, int64_t n) {
@@ -341,7 +402,7 @@ int teuk_step(teuk_t h, int64_t n) {
     }
     for (int64_t t = 0; t < n; ++t) TEUK_CUDA(h, cudaGraphLaunch(h->graph_exec, h->stream));
     h->substeps_done += n * h->k;
-    h->launches += n * 2 * h->k;
+    h->launches += n * (2 * h->k + (h->ko_sigma > 0 ? 1 : 0));
     if (record) h->n_recorded += n;
     return TEUK_OK;
   }
@@ -350,9 +411,8 @@ int teuk_step(teuk_t h, int64_t n) {
       const bool last = q == h->k - 1;
       const bool record = last && h->ring != nullptr;
       const int64_t slot = record ? h->n_recorded % h->ring_cap : 0;
-      int rc = dispatch_substep(h, record, slot);
+      int rc = iterate(h, record, slot);
       if (rc) return rc;
-      ++h->substeps_done;
     }
     if (h->ring) ++h->n_recorded;
   }
@@ -520,6 +580,11 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
     }
     // one warp per (row, 32 columns)
     if (rc == TEUK_OK) trial(1, v, 0, 0);
+    // balanced: the same number of points for every resident block
+    for (int tx = 32; tx <= tx_full && rc == TEUK_OK; tx = (tx * 2 > tx_full && tx < tx_full) ? tx_full : tx * 2) {
+      trial(2, v, tx, 1);
+      if (tx == tx_full) break;
+    }
   }
   cudaMemcpyAsync(h->u, saved, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(h->status, &status, sizeof(status), cudaMemcpyHostToDevice, h->stream);
@@ -548,6 +613,12 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
   }
   int tx = std::min(256, ((h->n_th + 31) / 32) * 32);
   if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
+  if (h->kernel_family == 2) {  // balanced: tx threads x 1 row per block, variant + 6
+    if (threads_theta) *threads_theta = tx;
+    if (rows_per_block) *rows_per_block = 1;
+    if (variant) *variant = 6 + h->kernel_variant;
+    return TEUK_OK;
+  }
   int ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
   while (ty > 1 && tx * ty > 256) ty /= 2;
   if (threads_theta) *threads_theta = tx;
@@ -557,8 +628,15 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
 }
 
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant) {
-  if (!h || variant < 0 || variant > 5) return TEUK_ERR_INVALID_ARG;
-  if (variant < 3) {
+  if (!h || variant < 0 || variant > 8) return TEUK_ERR_INVALID_ARG;
+  if (variant >= 6) {
+    if (threads_theta < 32 || threads_theta % 32 != 0 || threads_theta > 256)
+      return invalid(h, "launch shape: threads_theta a multiple of 32, at most 256");
+    h->kernel_family = 2;
+    h->kernel_variant = variant - 6;
+    h->threads_theta = threads_theta;
+    h->rows_per_block = 1;
+  } else if (variant < 3) {
     if (threads_theta < 32 || threads_theta % 32 != 0 || rows_per_block < 1 ||
         threads_theta * rows_per_block > 256)
       return invalid(h, "launch shape: threads_theta a multiple of 32, threads_theta * rows <= 256");

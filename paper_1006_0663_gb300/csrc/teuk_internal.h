@@ -18,7 +18,10 @@ struct teuk_s {
   int rows_per_block = 0;  // step-kernel launch shape: rows of theta per block (0: default)
   int threads_theta = 0;   // threads along theta per row (0: n_theta rounded up to 32, <= 256)
   int kernel_variant = 0;  // register budget of the step kernels: 0 (<= 255), 1 (<= 128), 2 (<= 85)
-  int kernel_family = 0;   // 0: rows per block (half_kernel/full_kernel), 1: one warp per 32 columns
+  int kernel_family = 0;   // 0: rows per block (half_kernel/full_kernel), 1: one warp per 32 columns,
+                           // 2: balanced (every resident block the same number of points)
+  int bal_key = -1;        // (variant, threads) the balanced grid sizes below were computed for
+  int bal_grid[2] = {0, 0};  // blocks of the balanced half / full kernels (resident capacity)
   int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;
   double dt_outer = 0;  // leading word of the outer step
   int device = 0;
@@ -62,6 +65,10 @@ struct teuk_s {
   // target-precision scalars kept as words
   double h4_w[4] = {0, 0, 0, 0}, h2_w[4] = {0, 0, 0, 0}, ln2_w[4] = {0, 0, 0, 0};
   double dr_d = 0, rsmin_d = 0;
+  double dt_w[4] = {0, 0, 0, 0}, dr_w[4] = {0, 0, 0, 0};  // outer dt and dr* as words
+  double ko_sigma = 0;                 // r* dissipation strength (0: off, the paper's scheme)
+  double ko_eps_w[4] = {0, 0, 0, 0};   // sigma dt / (16 dr*) as words
+  double* u_ko = nullptr;              // output of the dissipation step (state layout)
   std::string last_error;
 };
 
@@ -80,6 +87,15 @@ int substep_w4(teuk_s* h, bool record, int64_t slot);
 int substep_buffers_w1(teuk_s* h, const double* u_in, double* u_out, double* scratch);
 int substep_buffers_w2(teuk_s* h, const double* u_in, double* u_out, double* scratch);
 int substep_buffers_w4(teuk_s* h, const double* u_in, double* u_out, double* scratch);
+int prepare_w1(teuk_s* h);
+int prepare_w2(teuk_s* h);
+int prepare_w4(teuk_s* h);
+int dissipation_w1(teuk_s* h, double sigma);
+int dissipation_w2(teuk_s* h, double sigma);
+int dissipation_w4(teuk_s* h, double sigma);
+int dissipate_w1(teuk_s* h);
+int dissipate_w2(teuk_s* h);
+int dissipate_w4(teuk_s* h);
 int project_w1(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);
 int project_w2(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);
 int project_w4(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);

@@ -369,6 +369,40 @@ __global__ void pulse_kernel(PulseArgs a) {
   st_r(a.u + 3 * W * ws + idx, ws, r_mul(b, r_mul_d(GpY, a.amp_im)));
 }
 
+// ---- r* dissipation (not part of the paper's method; off unless enabled) -------------------
+// Once per outer step, before its first Lax-Wendroff iteration, every component at rows
+// 2 .. n_r - 3 becomes u_i - eps (u_{i-2} - 4 u_{i-1} + 6 u_i - 4 u_{i+1} + u_{i+2}),
+// eps = sigma dt / (16 dr*): the fourth-order Kreiss-Oliger operator over one outer step. The
+// other rows are copied. Several iterations per dt = 0.25 dr* leave the scheme's own damping
+// of short r* wavelengths too weak for the modes of near-zero numerical group velocity in the
+// region where the lower-order terms of the system make a frozen wave grow (long runs).
+struct DissArgs {
+  Geom g;
+  const double* u;  // [4][W][n_r][pitch]
+  double* out;      // same layout
+  double eps[4];    // eps as W words
+};
+
+template <int W>
+__global__ void dissipate_kernel(DissArgs a) {
+  using R = typename RT<W>::T;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y, c = blockIdx.z;
+  if (j >= a.g.n_th) return;
+  const size_t ws = (size_t)a.g.n_r * a.g.pitch, p = (size_t)a.g.pitch;
+  const double* base = a.u + (size_t)c * W * ws + (size_t)i * p + j;
+  R v = ld_s<R>(base, ws);
+  if (i >= 2 && i <= a.g.n_r - 3) {
+    using namespace mw;
+    R d4 = v_sub(ld_s<R>(base - 2 * p, ws), r_scale2(ld_s<R>(base - p, ws), 4.0));
+    d4 = v_add(d4, r_mul_d(v, 6.0));
+    d4 = v_sub(d4, r_scale2(ld_s<R>(base + p, ws), 4.0));
+    d4 = v_add(d4, ld_s<R>(base + 2 * p, ws));
+    v = v_sub(v, r_mul(from_words<R>(a.eps), d4));
+  }
+  st_r(a.out + (size_t)c * W * ws + (size_t)i * p + j, ws, v);
+}
+
 // ---- multipole projection of the recorded waveform (Sec. 3.C, Fig. 1) ----------------------
 struct ProjectArgs {
   int n_th, n_ell;
@@ -536,16 +570,17 @@ __device__ __forceinline__ void half_point(const StepArgs& a, int h, int j, cons
 
 template <int W>
 __device__ __forceinline__ void half_row_out(const StepArgs& a, int h, int tx, int TX, const double* sR,
-                                             const double* sI) {
+                                             const double* sI, int c0 = 0, int c1 = -1) {
   const int gstride = a.g.n_th + 2 * a.radius;
-  // two columns per iteration when a thread owns several: independent dependency chains that
-  // the scheduler interleaves (latency of chained FP64 operations)
-  int j = tx;
-  for (; j + TX < a.g.n_th; j += 2 * TX) {
+  if (c1 < 0) c1 = a.g.n_th;
+  // columns c0 .. c1-1; two per iteration when a thread owns several: independent dependency
+  // chains that the scheduler interleaves (latency of chained FP64 operations)
+  int j = c0 + tx;
+  for (; j + TX < c1; j += 2 * TX) {
     half_point<W>(a, h, j, sR + j, sI + j, gstride);
     half_point<W>(a, h, j + TX, sR + j + TX, sI + j + TX, gstride);
   }
-  if (j < a.g.n_th) half_point<W>(a, h, j, sR + j, sI + j, gstride);
+  if (j < c1) half_point<W>(a, h, j, sR + j, sI + j, gstride);
 }
 
 // Eq. lw2, first phase at node i: s_Phi = Phi_{i+1/2} + Phi_{i-1/2} into the ghosted row.
@@ -628,15 +663,16 @@ __device__ __forceinline__ bool full_point(const StepArgs& a, int i, int j, cons
 
 template <int W>
 __device__ __forceinline__ bool full_row_out(const StepArgs& a, int i, int tx, int TX, const double* sR,
-                                             const double* sI, long long slot) {
+                                             const double* sI, long long slot, int c0 = 0, int c1 = -1) {
   const int gstride = a.g.n_th + 2 * a.radius;
+  if (c1 < 0) c1 = a.g.n_th;
   bool bad = false;
-  int j = tx;
-  for (; j + TX < a.g.n_th; j += 2 * TX) {
+  int j = c0 + tx;
+  for (; j + TX < c1; j += 2 * TX) {
     bad |= full_point<W>(a, i, j, sR + j, sI + j, gstride, slot);
     bad |= full_point<W>(a, i, j + TX, sR + j + TX, sI + j + TX, gstride, slot);
   }
-  if (j < a.g.n_th) bad |= full_point<W>(a, i, j, sR + j, sI + j, gstride, slot);
+  if (j < c1) bad |= full_point<W>(a, i, j, sR + j, sI + j, gstride, slot);
   return bad;
 }
 
@@ -736,6 +772,55 @@ __global__ void __launch_bounds__(256, V + 1) full_kernel(StepArgs a) {
   long long slot = -1;
   if (a.record) slot = a.ring_slot >= 0 ? a.ring_slot : (*a.ring_counter) % a.ring_cap;
   if (full_row_out<W>(a, i, threadIdx.x, blockDim.x, sR, sI, slot)) atomicOr(a.status, 1u);
+}
+
+// ---- balanced kernels: the same number of points for every block ----------------------------
+// The launch has exactly as many blocks as fit on the GPU at once (blockDim.x threads along
+// theta, one ghosted row of shared memory each). Block b takes the points
+// [b P / G, (b + 1) P / G) of the row-major (row, theta) range of P points, so every SM gets the
+// same share of the FP64 work whatever the row count, without a partly filled last wave of
+// blocks. A block walks the rows its range touches: all its threads build the whole ghosted
+// row in shared memory, then take the range's columns of that row.
+template <int W, int V = 0>
+__global__ void __launch_bounds__(256, V + 1) half_bal_kernel(StepArgs a) {
+  extern __shared__ double sm[];
+  const int n_th = a.g.n_th, gstride = n_th + 2 * a.radius;
+  const long long total = (long long)(a.g.n_r - 1) * n_th;
+  const long long p0 = total * blockIdx.x / gridDim.x, p1 = total * (blockIdx.x + 1) / gridDim.x;
+  double* sR = sm;
+  double* sI = sm + (size_t)W * gstride;
+  for (long long p = p0; p < p1;) {
+    const int h = (int)(p / n_th), c0 = (int)(p % n_th);
+    const int c1 = (int)(p1 - p < (long long)(n_th - c0) ? c0 + (p1 - p) : n_th);
+    half_row_prep<W>(a, h, threadIdx.x, blockDim.x, sR, sI);
+    __syncthreads();
+    half_row_out<W>(a, h, threadIdx.x, blockDim.x, sR, sI, c0, c1);
+    __syncthreads();
+    p += c1 - c0;
+  }
+}
+
+template <int W, int V = 0>
+__global__ void __launch_bounds__(256, V + 1) full_bal_kernel(StepArgs a) {
+  extern __shared__ double sm[];
+  const int n_th = a.g.n_th, gstride = n_th + 2 * a.radius;
+  const long long total = (long long)(a.g.n_r - 2) * n_th;
+  const long long p0 = total * blockIdx.x / gridDim.x, p1 = total * (blockIdx.x + 1) / gridDim.x;
+  double* sR = sm;
+  double* sI = sm + (size_t)W * gstride;
+  long long slot = -1;
+  if (a.record) slot = a.ring_slot >= 0 ? a.ring_slot : (*a.ring_counter) % a.ring_cap;
+  bool bad = false;
+  for (long long p = p0; p < p1;) {
+    const int i = 1 + (int)(p / n_th), c0 = (int)(p % n_th);
+    const int c1 = (int)(p1 - p < (long long)(n_th - c0) ? c0 + (p1 - p) : n_th);
+    full_row_prep<W>(a, i, threadIdx.x, blockDim.x, sR, sI);
+    __syncthreads();
+    bad |= full_row_out<W>(a, i, threadIdx.x, blockDim.x, sR, sI, slot, c0, c1);
+    __syncthreads();
+    p += c1 - c0;
+  }
+  if (bad) atomicOr(a.status, 1u);
 }
 
 // ---- batched execution: many problems of uneven size in one cooperative launch ------------

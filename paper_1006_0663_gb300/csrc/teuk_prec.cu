@@ -60,6 +60,8 @@ int setup_impl(teuk_s* h) {
   h->dt_outer = lead(dt);
   h->dr_d = lead(dr);
   h->rsmin_d = g.rstar_min;
+  put(h->dt_w, dt);
+  put(h->dr_w, dr);
   put(h->h4_w, r_scale2(dts, 0.25));
   put(h->h2_w, r_scale2(dts, 0.5));
   put(h->ln2_w, ln2);
@@ -273,6 +275,28 @@ int project_impl(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, in
   return TEUK_OK;
 }
 
+// r* dissipation strength eps = sigma dt / (16 dr*) in the target precision.
+int dissipation_impl(teuk_s* h, double sigma) {
+  const R dt = from_words<R>(h->dt_w), dr = from_words<R>(h->dr_w);
+  put(h->ko_eps_w, r_div(r_mul(r_from<R>(sigma), dt), r_mul(r_from<R>(16.0), dr)));
+  return TEUK_OK;
+}
+
+// One dissipation step of the state (kernel into u_ko, copied back).
+int dissipate_impl(teuk_s* h) {
+  DissArgs da{};
+  da.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
+  da.u = h->u;
+  da.out = h->u_ko;
+  std::memcpy(da.eps, h->ko_eps_w, sizeof(da.eps));
+  dissipate_kernel<W><<<dim3((h->n_th + 63) / 64, h->n_r, 4), 64, 0, h->stream>>>(da);
+  TEUK_CUDA(h, cudaGetLastError());
+  TEUK_CUDA(h, cudaMemcpyAsync(h->u, h->u_ko, (size_t)4 * W * h->n_r * h->pitch * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h->stream));
+  h->launches += 1;
+  return TEUK_OK;
+}
+
 // Launch shape of the step kernels: threads along theta (x, one warp multiple up to 256) and
 // rows per block (y). Default: about 128 threads per block, so that the last wave of blocks
 // still spreads over every SM; teuk_tune picks the fastest rows-per-block instead.
@@ -280,9 +304,47 @@ void step_shape(const teuk_s* h, dim3& blk) {
   int tx = ((h->n_th + 31) / 32) * 32;
   if (tx > 256) tx = 256;
   if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
+  if (h->kernel_family == 2) {  // balanced kernels: one row of threads per block
+    blk = dim3(tx, 1);
+    return;
+  }
   int ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
   while (ty > 1 && tx * ty > 256) ty /= 2;
   blk = dim3(tx, ty);
+}
+
+// Grid of the balanced kernels: every block that fits on the GPU at once (occupancy x SMs),
+// computed once per (variant, threads) and kept in the handle.
+template <int V>
+int bal_grid(teuk_s* h, dim3 blk, size_t smem) {
+  const int key = V * 4096 + (int)blk.x;
+  if (h->bal_key == key) return TEUK_OK;
+  if (smem > 48 * 1024) {
+    TEUK_CUDA(h, cudaFuncSetAttribute(half_bal_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TEUK_CUDA(h, cudaFuncSetAttribute(full_bal_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  int sms = 0, per_h = 0, per_f = 0;
+  TEUK_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  TEUK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, half_bal_kernel<W, V>, (int)blk.x, smem));
+  TEUK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, full_bal_kernel<W, V>, (int)blk.x, smem));
+  if (per_h < 1 || per_f < 1) return cuda_fail(h, cudaErrorInvalidConfiguration, "balanced kernels do not fit");
+  h->bal_grid[0] = per_h * sms;
+  h->bal_grid[1] = per_f * sms;
+  h->bal_key = key;
+  return TEUK_OK;
+}
+
+// Host-side preparation of the current launch shape (before a graph capture).
+int prepare_impl(teuk_s* h) {
+  if (h->kernel_family != 2) return TEUK_OK;
+  dim3 blk;
+  step_shape(h, blk);
+  const size_t smem = (size_t)2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
+  switch (h->kernel_variant) {
+    case 1: return bal_grid<1>(h, blk, smem);
+    case 2: return bal_grid<2>(h, blk, smem);
+    default: return bal_grid<0>(h, blk, smem);
+  }
 }
 
 // Launches the half and full kernels of the handle's register-budget variant.
@@ -299,6 +361,20 @@ int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
     time_end(h, 0, ev);
     time_begin(h, &ev);
     full_seg_kernel<W, V><<<(unsigned)((units_f + 3) / 4), 128, seg_smem, h->stream>>>(sa, nseg);
+    time_end(h, 1, ev);
+    h->launches += 2;
+    TEUK_CUDA(h, cudaGetLastError());
+    return TEUK_OK;
+  }
+  if (h->kernel_family == 2) {
+    const int rc = bal_grid<V>(h, blk, smem);
+    if (rc != TEUK_OK) return rc;
+    cudaEvent_t ev = nullptr;
+    time_begin(h, &ev);
+    half_bal_kernel<W, V><<<h->bal_grid[0], blk.x, smem, h->stream>>>(sa);
+    time_end(h, 0, ev);
+    time_begin(h, &ev);
+    full_bal_kernel<W, V><<<h->bal_grid[1], blk.x, smem, h->stream>>>(sa);
     time_end(h, 1, ev);
     h->launches += 2;
     TEUK_CUDA(h, cudaGetLastError());
@@ -482,6 +558,9 @@ int TEUK_SUFFIX(pulse_w)(teuk_s* h, double center, double width, double ar, doub
   return pulse_impl(h, center, width, ar, ai, ell);
 }
 int TEUK_SUFFIX(substep_w)(teuk_s* h, bool record, int64_t slot) { return substep_impl(h, record, slot); }
+int TEUK_SUFFIX(prepare_w)(teuk_s* h) { return prepare_impl(h); }
+int TEUK_SUFFIX(dissipation_w)(teuk_s* h, double sigma) { return dissipation_impl(h, sigma); }
+int TEUK_SUFFIX(dissipate_w)(teuk_s* h) { return dissipate_impl(h); }
 int TEUK_SUFFIX(project_w)(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first) {
   return project_impl(h, ell_min, ell_max, out, n, first);
 }

@@ -27,7 +27,8 @@ SYMBOLS = [
     "teuk_mw_eval", "teuk_timing", "teuk_kernel_times", "teuk_fp64_peak", "teuk_substep_noalloc",
     "teuk_tune", "teuk_batch_create", "teuk_batch_step", "teuk_batch_sync", "teuk_batch_info",
     "teuk_batch_destroy", "teuk_use_graphs", "teuk_launch_shape",
-    "teuk_set_launch_shape", "teuk_read_multipoles",
+    "teuk_set_launch_shape", "teuk_read_multipoles", "teuk_substep_host_state",
+    "teuk_set_dissipation",
 ]
 
 
@@ -73,6 +74,8 @@ def lib(build_if_missing: bool = True):
         L.teuk_set_observer.argtypes = [vp, d, i64]
         L.teuk_read_waveform.argtypes = [vp, dp, P(i64)]
         L.teuk_read_multipoles.argtypes = [vp, i32, i32, dp, P(i64)]
+        L.teuk_substep_host_state.argtypes = [vp, dp, i64]
+        L.teuk_set_dissipation.argtypes = [vp, d]
         L.teuk_get_state.argtypes = [vp, dp, P(i64)]
         L.teuk_set_state.argtypes = [vp, dp, i64]
         L.teuk_get_state_device.argtypes = [vp, vp]
@@ -154,10 +157,13 @@ class Teuk:
 
     @classmethod
     def from_problem(cls, p, precision=None, **kw):
-        return cls(M=p.M, a=p.a, s=p.s, m=p.m, rstar_min=p.rstar_min, rstar_max=p.rstar_max,
-                   n_r=p.n_r, n_theta=p.n_theta, dt=0.0, substeps=p.substeps,
-                   theta_order=p.theta_order, parity=p.parity,
-                   precision=precision if precision is not None else p.words, **kw)
+        g = cls(M=p.M, a=p.a, s=p.s, m=p.m, rstar_min=p.rstar_min, rstar_max=p.rstar_max,
+                n_r=p.n_r, n_theta=p.n_theta, dt=0.0, substeps=p.substeps,
+                theta_order=p.theta_order, parity=p.parity,
+                precision=precision if precision is not None else p.words, **kw)
+        if getattr(p, "ko_sigma", 0.0):
+            g.set_dissipation(p.ko_sigma)
+        return g
 
     def close(self):
         if getattr(self, "_h", None):
@@ -211,6 +217,19 @@ class Teuk:
         if n.value:
             _check(lib().teuk_read_waveform(self._h, _dp(out), ctypes.byref(n)), self._h)
         return out
+
+    def set_dissipation(self, sigma):
+        """r* Kreiss-Oliger dissipation once per outer step (not part of the paper's scheme;
+        0 = off)."""
+        _check(lib().teuk_set_dissipation(self._h, float(sigma)), self._h)
+
+    def substep_host_state(self, planes, n=1):
+        """n iterations with the state held in host memory (the paper's first CUDA design's
+        data flow, Sec. 4): planes [4][words][n_r][n_theta], C-contiguous float64, updated
+        in place (pass page-locked memory for full link speed)."""
+        assert planes.flags.c_contiguous and planes.dtype == np.float64
+        assert planes.shape == (4, self.words, self.n_r, self.n_theta)
+        _check(lib().teuk_substep_host_state(self._h, _dp(planes), int(n)), self._h)
 
     def read_multipoles(self, ell_min, ell_max):
         """Multipoles c_l(t) of the recorded waveform, computed on the device in the handle's

@@ -92,6 +92,7 @@ class Problem:
     width: float = 4.0
     rstar_obs: float = 300.0
     theta_order: int = 10
+    ko_sigma: float = 0.0  # r* dissipation (not in the paper; 0 = the paper's scheme)
 
     @property
     def dr(self) -> float:

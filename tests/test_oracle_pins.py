@@ -308,3 +308,44 @@ def test_schwarzschild_tail_exponent(oracle_mod):
     assert np.all(np.abs(n_vel - 3.0) < 0.05), n_vel
     n_sym = _tail_index(oracle_mod, False)
     assert np.all(np.abs(n_sym - 4.0) < 0.05), n_sym
+
+
+def test_r_dissipation_step_by_linearity(oracle_mod):
+    """The oracle's r* dissipation step (not part of the paper's scheme): one iteration with
+    sigma minus one without equals -eps times one iteration (without) applied to the fourth
+    difference of the data, eps = sigma dt / (16 dr*), rows 2 .. n_r - 3 only (the scheme is
+    linear); a cubic in r* is left unchanged; sigma = 0 changes nothing."""
+    n_r, nth, sigma = 23, 8, 1.5
+    p = dict(M=1.0, a=0.7, s=-1, m=1, rstar_min=-10.0, rstar_max=12.0, n_r=n_r, n_theta=nth, dt=0.0,
+             substeps=1, theta_order=10, parity=1)
+    rng = np.random.default_rng(4)
+    u = rng.uniform(-1, 1, (4, 1, n_r, nth))
+    u[:, :, [0, -1]] = 0.0
+    d4 = np.zeros_like(u)
+    d4[:, :, 2:-2] = u[:, :, :-4] - 4 * u[:, :, 1:-3] + 6 * u[:, :, 2:-2] - 4 * u[:, :, 3:-1] + u[:, :, 4:]
+
+    def one(state, ko):
+        o = oracle_mod.Oracle(**p, bits=256, ko_sigma=ko)
+        o.set_state(state)
+        o.step(1)
+        return o.get_state(words=4)
+
+    def val(w):
+        return np.sum(w, axis=1)  # word sums in double: the tolerance below is far above that
+
+    with_ko, without = one(u, sigma), one(u, 0.0)
+    of_d4 = one(d4, 0.0)
+    eps = sigma * 0.25 / 16.0  # dt = 0.25 dr*
+    lhs = (with_ko - without)
+    lhs = lhs[:, 0] + lhs[:, 1] + lhs[:, 2] + lhs[:, 3]
+    rhs = -eps * val(of_d4)
+    assert np.abs(lhs - rhs).max() < 1e-13 * np.abs(rhs).max()
+    assert np.abs(rhs).max() > 1e-3
+    # a cubic in the row index is in the kernel of the fourth difference
+    i = np.arange(n_r, dtype=float)
+    cubic = np.zeros_like(u)
+    cubic[:] = ((3 + i - 2 * i ** 2 + i ** 3) / 1024.0)[None, None, :, None]  # exact doubles
+    cubic[:, :, [0, -1]] = 0.0
+    # the fourth difference vanishes at rows 3 .. n_r - 4 (away from the zeroed rows 0, n_r - 1);
+    # one iteration spreads a difference by one row
+    np.testing.assert_array_equal(one(cubic, sigma)[:, :, 4:-4], one(cubic, 0.0)[:, :, 4:-4])
