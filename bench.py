@@ -311,6 +311,31 @@ def run_design_a(prob, words, iters, torch, teuk):
             "link_gbps_effective": link * iters / (t_a - t_r) / 1e9 if t_a > t_r else None}
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu / /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline_others(prob, seconds_target=4.0):
+    """Bounded samples of the same oracle window on one core (256-bit) and of the FP64 oracle
+    on all cores, beside the main baseline (context for the cost of the arithmetic)."""
+    import oracle
+    n_all = oracle.max_threads()
+    oracle.set_threads(1)
+    one = cpu_baseline(prob, 2, seconds_target)
+    oracle.set_threads(n_all)
+    f64 = cpu_baseline(prob, 1, seconds_target)
+    return {"bits256_one_core": {"value": one["value"], "cores": 1, "sample": one["sample"]},
+            "fp64_all_cores": {"value": f64["value"], "cores": f64["cores"], "sample": f64["sample"]}}
+
+
 def cpu_baseline(prob, words, seconds_target=15.0):
     """The oracle (256-bit MPFR for dd/qd workloads, FP64 for FP64) on all host cores, on a
     window of rows of the same workload for a bounded number of iterations."""
@@ -569,6 +594,10 @@ def main():
             variants["design_a_host_state"] = run_design_a(prob, W, 2 * prob.substeps, torch, teuk)
         batched = None if args.no_batch else run_c4(torch, teuk, workloads)
         cpu = None if args.no_cpu else cpu_baseline(prob, W)
+        if cpu is not None:
+            cpu["cpu_model"] = cpu_model()
+            if W > 1:
+                cpu["other_runs"] = cpu_baseline_others(prob)
         parity = None if args.no_cpu else stated_error(prob, W, teuk)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -49,17 +49,38 @@ def local_power_index(t: np.ndarray, amp: np.ndarray, stride: int = 1) -> np.nda
     return n
 
 
+def velocity_data(p: workloads.Problem, words: int) -> np.ndarray:
+    """Generic (not time-symmetric) initial data of an l' = 0 scalar field: Phi = 0 and
+    Pi = Phi_t + b Phi_{r*} = A exp(-((r* - c)/w)^2), constant in theta, as word planes
+    [4][words][n_r][n_theta] of exact doubles (rows 0 and n_r - 1 zero)."""
+    if (p.s, p.m, p.ell) != (0, 0, 0):
+        raise ValueError("velocity data are defined here for s = m = l' = 0")
+    rs = p.rstar_min + np.arange(p.n_r) * p.dr
+    G = np.exp(-((rs - p.center) / p.width) ** 2)
+    G[[0, -1]] = 0.0
+    ar, ai = p.amps
+    planes = np.zeros((4, words, p.n_r, p.n_theta))
+    planes[2, 0] = (ar * G)[:, None]
+    planes[3, 0] = (ai * G)[:, None]
+    return planes
+
+
 def run(p: workloads.Problem = workloads.TAILS, precision: int | None = None, ell_max: int = 8,
-        steps: int | None = None, chunk: int = 500, tune: bool = True, log=None) -> dict:
+        steps: int | None = None, chunk: int = 500, tune: bool = True, log=None,
+        data: str = "pulse") -> dict:
     """Evolves p for `steps` outer steps (default p.steps) recording Phi at p.rstar_obs every
-    step, then projects the record onto sY_lm, l = max(|m|, |s|) .. ell_max, on the device."""
+    step, then projects the record onto sY_lm, l = max(|m|, |s|) .. ell_max, on the device.
+    data: "pulse" (the workloads' time-symmetric Gaussian) or "velocity" (velocity_data)."""
     W = precision or p.words
     steps = p.steps if steps is None else steps
     lo = max(abs(p.m), abs(p.s))
     g = teuk.Teuk.from_problem(p, precision=W)
     try:
         ar, ai = p.amps
-        g.set_initial_pulse(p.center, p.width, ar, ai, p.ell)
+        if data == "velocity":
+            g.set_initial(velocity_data(p, W))
+        else:
+            g.set_initial_pulse(p.center, p.width, ar, ai, p.ell)
         g.set_observer(p.rstar_obs, capacity=steps)
         shape = None
         if tune:
@@ -82,14 +103,25 @@ def run(p: workloads.Problem = workloads.TAILS, precision: int | None = None, el
     t = (np.arange(c.shape[0]) + 1) * p.dt
     amp = np.hypot(c[:, :, 0, 0], c[:, :, 1, 0])  # |c_l(t)| from the leading words
     updates = float(p.n_r) * p.n_theta * p.substeps * steps
-    return dict(problem=p, words=W, ell=list(range(lo, ell_max + 1)), t=t, amp=amp, coeffs=c,
+    return dict(problem=p, words=W, data=data, ell=list(range(lo, ell_max + 1)), t=t, amp=amp, coeffs=c,
                 rstar_obs_used=used, wall_s=wall, updates_per_s=updates / wall, launch_shape=shape,
                 reflection_free_until=reflection_free_until(p))
 
 
-def summarize(res: dict, times=(300.0, 500.0, 750.0, 1000.0, 1250.0, 1450.0), window: float = 0.05) -> dict:
+def power_law_fit(t: np.ndarray, amp: np.ndarray, t0: float, t1: float):
+    """Least-squares n of |c| ~ t^-n over t0 <= t <= t1 (None without enough positive samples)."""
+    sel = (t >= t0) & (t <= t1) & (amp > 0)
+    if sel.sum() < 8:
+        return None
+    slope = np.polyfit(np.log(t[sel]), np.log(amp[sel]), 1)[0]
+    return float(-slope)
+
+
+def summarize(res: dict, times=(300.0, 500.0, 750.0, 1000.0, 1250.0, 1450.0), window: float = 0.05,
+              fit=(1000.0, 1450.0)) -> dict:
     """Per multipole: |c_l| and the local power index averaged over ln t in [ln T - window,
-    ln T + window] around each requested T (within the recorded, reflection-free span)."""
+    ln T + window] around each requested T (within the recorded, reflection-free span), and
+    the power-law index fitted over the late window `fit`."""
     t, amp = res["t"], res["amp"]
     t_ok = min(t[-1], res["reflection_free_until"])
     out = {}
@@ -105,6 +137,8 @@ def summarize(res: dict, times=(300.0, 500.0, 750.0, 1000.0, 1250.0, 1450.0), wi
             i = int(np.argmin(np.abs(t - T)))
             row[f"{T:g}"] = {"abs_c": float(amp[i, k]),
                              "n": float(np.mean(vals)) if vals.size else None}
+        row["fit"] = {"t0": fit[0], "t1": min(fit[1], t_ok),
+                      "n": power_law_fit(t, amp[:, k], fit[0], min(fit[1], t_ok))}
         out[ell] = row
     return out
 
@@ -114,22 +148,35 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 4])
     ap.add_argument("--steps", type=int, default=0, help="outer steps (default: the workload's)")
     ap.add_argument("--ell-max", type=int, default=8)
+    ap.add_argument("--data", default="pulse", choices=["pulse", "velocity"],
+                    help="time-symmetric Gaussian pulse, or Phi = 0 with a Gaussian Pi")
+    ap.add_argument("--refine", type=int, default=1,
+                    help="divide dr* (and dt = 0.25 dr*) by this factor, same domain and end time")
+    ap.add_argument("--substeps", type=int, default=0,
+                    help="Lax-Wendroff iterations per outer step (default: the workload's)")
     ap.add_argument("--out", default="")
     args = ap.parse_args(argv)
     p = workloads.TAILS
+    if args.refine > 1:
+        p = p.with_(n_r=(p.n_r - 1) * args.refine + 1, steps=p.steps * args.refine)
+    if args.substeps:
+        p = p.with_(substeps=args.substeps)
     res = run(p, precision=args.precision or None, ell_max=args.ell_max, steps=args.steps or None,
-              log=lambda s: print(s, flush=True))
+              log=lambda s: print(s, flush=True), data=args.data)
     summ = summarize(res)
     l0 = p.ell
-    print(f"tails: {p.name}, words={res['words']}, {res['updates_per_s']:.3e} updates/s, "
+    print(f"tails: {p.name} ({args.data} data, dr*={p.dr:g}, k={p.substeps}), words={res['words']}, "
+          f"{res['updates_per_s']:.3e} updates/s, "
           f"{res['wall_s']:.1f} s, reflection-free until t = {res['reflection_free_until']:.0f} M")
     for ell, row in summ.items():
         cells = "  ".join(f"t={T}: |c|={v['abs_c']:.3e} n={v['n'] if v['n'] is None else round(v['n'], 3)}"
-                          for T, v in row.items())
-        print(f"  l={ell} (l+l'+3 = {ell + l0 + 3}): {cells}")
+                          for T, v in row.items() if T != "fit")
+        fn = row["fit"]["n"]
+        print(f"  l={ell} (l+l'+3 = {ell + l0 + 3}): fit n={fn if fn is None else round(fn, 3)}  {cells}")
     if args.out:
         stride = max(1, len(res["t"]) // 3000)
-        doc = {"workload": p.name, "words": res["words"], "updates_per_s": res["updates_per_s"],
+        doc = {"workload": p.name, "data": args.data, "dr": p.dr, "substeps": p.substeps, "n_r": p.n_r,
+               "words": res["words"], "updates_per_s": res["updates_per_s"],
                "wall_s": res["wall_s"], "launch_shape": res["launch_shape"],
                "rstar_obs_used": res["rstar_obs_used"],
                "reflection_free_until": res["reflection_free_until"], "ell": res["ell"],

@@ -35,3 +35,20 @@ def test_study_domain_is_reflection_free_for_the_whole_run():
     assert (p.s, p.m, p.ell) == (0, 0, 0) and p.words == 4
     # observer inside the domain, pulse ahead of it
     assert p.rstar_min < p.center < p.rstar_obs < p.rstar_max
+
+
+def test_power_law_fit():
+    t = np.linspace(500.0, 1500.0, 2001)
+    assert abs(tails.power_law_fit(t, 3e-20 * t ** -7.0, 1000.0, 1450.0) - 7.0) < 1e-9
+    assert tails.power_law_fit(t, np.zeros_like(t), 1000.0, 1450.0) is None
+
+
+def test_velocity_data_planes():
+    p = workloads.TAILS.with_(n_r=41, n_theta=8, rstar_min=-10.0, rstar_max=30.0)
+    planes = tails.velocity_data(p, 4)
+    assert planes.shape == (4, 4, 41, 8)
+    assert not planes[:2].any() and not planes[:, 1:].any()    # Phi = 0, single-word values
+    assert not planes[:, :, [0, -1]].any()                      # zero r* boundary rows
+    ar, _ = p.amps
+    i = int(round((p.center - p.rstar_min) / p.dr))
+    assert planes[2, 0, i, 3] == ar                              # Gaussian peak, theta-constant
