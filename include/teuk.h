@@ -186,14 +186,16 @@ int teuk_batch_destroy(teuk_batch_t b);
  * and frees one state-sized device buffer; call it before timing-critical work. */
 int teuk_tune(teuk_t h, int* rows_per_block);
 /* The step kernels' launch shape in use: threads along theta per row, rows per block, and the
- * kernel variant: 0, 1, 2 = whole rows per block with <= 255, 128, 85 registers per thread;
- * 3, 4, 5 = one warp per (row, 32 theta columns) with the same three register budgets;
+ * kernel variant: 0, 1, 2 = whole rows per block with <= 255 and <= 128 registers per thread
+ * (blocks of up to 256 threads), or <= 102 registers in blocks of up to 128 threads;
+ * 3, 4, 5 = one warp per (row, 32 theta columns) with <= 255, 128, 85 registers;
  * 6, 7, 8 = balanced: as many blocks of threads_theta threads as fit on the GPU at once,
- * each taking the same number of (row, theta) points, same three budgets. */
+ * each taking the same number of (row, theta) points, budgets as for 0, 1, 2. */
 int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant);
 /* Sets the launch shape explicitly (same meaning as above; threads_theta a multiple of 32,
  * threads_theta * rows_per_block <= 256; both ignored for variants 3..5, rows_per_block
- * ignored for 6..8). Results do not depend on the shape. */
+ * ignored for 6..8; with variants 2 and 8 the block is cut to 128 threads). Results do not
+ * depend on the shape. */
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant);
 
 /* Lax-Wendroff iterations that allocate nothing, for callers that cannot let a library

@@ -574,16 +574,19 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   };
   for (int v = 0; v < 3 && rc == TEUK_OK; ++v) {
     // rows-per-block kernels: threads along theta x rows per block, at most 256 threads
-    for (int tx = 32; tx <= tx_full && rc == TEUK_OK; tx = (tx * 2 > tx_full && tx < tx_full) ? tx_full : tx * 2) {
-      for (int ty = 1; ty <= 8 && tx * ty <= 256 && rc == TEUK_OK; ty *= 2) trial(0, v, tx, ty);
-      if (tx == tx_full) break;
+    // (128 with register budget 2)
+    const int cap = v == 2 ? 128 : 256;
+    const int tx_top = std::min(tx_full, cap);
+    for (int tx = 32; tx <= tx_top && rc == TEUK_OK; tx = (tx * 2 > tx_top && tx < tx_top) ? tx_top : tx * 2) {
+      for (int ty = 1; ty <= 8 && tx * ty <= cap && rc == TEUK_OK; ty *= 2) trial(0, v, tx, ty);
+      if (tx == tx_top) break;
     }
     // one warp per (row, 32 columns)
     if (rc == TEUK_OK) trial(1, v, 0, 0);
     // balanced: the same number of points for every resident block
-    for (int tx = 32; tx <= tx_full && rc == TEUK_OK; tx = (tx * 2 > tx_full && tx < tx_full) ? tx_full : tx * 2) {
+    for (int tx = 32; tx <= tx_top && rc == TEUK_OK; tx = (tx * 2 > tx_top && tx < tx_top) ? tx_top : tx * 2) {
       trial(2, v, tx, 1);
-      if (tx == tx_full) break;
+      if (tx == tx_top) break;
     }
   }
   cudaMemcpyAsync(h->u, saved, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
@@ -611,19 +614,12 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
     if (variant) *variant = 3 + h->kernel_variant;
     return TEUK_OK;
   }
-  int tx = std::min(256, ((h->n_th + 31) / 32) * 32);
-  if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
-  if (h->kernel_family == 2) {  // balanced: tx threads x 1 row per block, variant + 6
-    if (threads_theta) *threads_theta = tx;
-    if (rows_per_block) *rows_per_block = 1;
-    if (variant) *variant = 6 + h->kernel_variant;
-    return TEUK_OK;
-  }
-  int ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
-  while (ty > 1 && tx * ty > 256) ty /= 2;
+  int tx, ty;
+  teuk::row_block_shape(h, tx, ty);
   if (threads_theta) *threads_theta = tx;
   if (rows_per_block) *rows_per_block = ty;
-  if (variant) *variant = h->kernel_variant;
+  // balanced kernels are reported as variant + 6
+  if (variant) *variant = (h->kernel_family == 2 ? 6 : 0) + h->kernel_variant;
   return TEUK_OK;
 }
 

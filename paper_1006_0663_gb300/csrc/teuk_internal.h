@@ -17,7 +17,8 @@ struct teuk_s {
   int W = 1;            // words per real
   int rows_per_block = 0;  // step-kernel launch shape: rows of theta per block (0: default)
   int threads_theta = 0;   // threads along theta per row (0: n_theta rounded up to 32, <= 256)
-  int kernel_variant = 0;  // register budget of the step kernels: 0 (<= 255), 1 (<= 128), 2 (<= 85)
+  int kernel_variant = 0;  // register budget of the step kernels: 0 (<= 255), 1 (<= 128), 2 (rows:
+                           // <= 102 in blocks of <= 128 threads; warp segments: <= 85)
   int kernel_family = 0;   // 0: rows per block (half_kernel/full_kernel), 1: one warp per 32 columns,
                            // 2: balanced (every resident block the same number of points)
   int bal_key = -1;        // (variant, threads) the balanced grid sizes below were computed for
@@ -107,6 +108,22 @@ int mw_eval_w4(int op, int device, const double* a, const double* b, double* out
 cudaEvent_t take_event(teuk_s* h);
 void time_begin(teuk_s* h, cudaEvent_t* a);
 void time_end(teuk_s* h, int kind, cudaEvent_t a);
+
+// Block shape of the row-family and balanced step kernels for the handle's launch shape:
+// threads along theta (a multiple of 32 up to 256, or the row width) x rows per block. The
+// register budget 2 allows at most 128 threads per block.
+inline void row_block_shape(const teuk_s* h, int& tx, int& ty) {
+  const int cap = h->kernel_variant == 2 ? 128 : 256;
+  tx = ((h->n_th + 31) / 32) * 32;
+  if (tx > cap) tx = cap;
+  if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
+  if (h->kernel_family == 2) {  // balanced kernels: one row of threads per block
+    ty = 1;
+    return;
+  }
+  ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
+  while (ty > 1 && tx * ty > cap) ty /= 2;
+}
 
 inline int cuda_fail(teuk_s* h, cudaError_t e, const char* what) {
   if (h) h->last_error = std::string(what) + ": " + cudaGetErrorString(e);

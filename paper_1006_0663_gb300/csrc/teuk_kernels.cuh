@@ -743,10 +743,13 @@ __global__ void __launch_bounds__(128, 2 * (V + 1)) full_seg_kernel(StepArgs a, 
 }
 
 // ---- single-problem kernels: blockDim.y rows per block, blockDim.x threads along theta ------
-// V selects the register budget (launch bounds: at least V + 1 blocks of 256 threads per SM,
-// i.e. <= 255, 128 or 85 registers); the autotuner picks the fastest variant per problem.
+// V selects the register budget: V = 0, 1: at least V + 1 blocks of up to 256 threads per SM
+// (<= 255, 128 registers); V = 2: at least 5 blocks of up to 128 threads (<= 102 registers,
+// 20 warps per SM). The autotuner picks the fastest variant per problem.
+template <int V> struct RowBounds { static constexpr int threads = 256, blocks = V + 1; };
+template <> struct RowBounds<2> { static constexpr int threads = 128, blocks = 5; };
 template <int W, int V = 0>
-__global__ void __launch_bounds__(256, V + 1) half_kernel(StepArgs a) {
+__global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) half_kernel(StepArgs a) {
   extern __shared__ double sm[];
   const int gstride = a.g.n_th + 2 * a.radius;
   const int h = blockIdx.x * blockDim.y + threadIdx.y;
@@ -759,7 +762,7 @@ __global__ void __launch_bounds__(256, V + 1) half_kernel(StepArgs a) {
 }
 
 template <int W, int V = 0>
-__global__ void __launch_bounds__(256, V + 1) full_kernel(StepArgs a) {
+__global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) full_kernel(StepArgs a) {
   extern __shared__ double sm[];
   const int gstride = a.g.n_th + 2 * a.radius;
   const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
@@ -782,7 +785,7 @@ __global__ void __launch_bounds__(256, V + 1) full_kernel(StepArgs a) {
 // blocks. A block walks the rows its range touches: all its threads build the whole ghosted
 // row in shared memory, then take the range's columns of that row.
 template <int W, int V = 0>
-__global__ void __launch_bounds__(256, V + 1) half_bal_kernel(StepArgs a) {
+__global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) half_bal_kernel(StepArgs a) {
   extern __shared__ double sm[];
   const int n_th = a.g.n_th, gstride = n_th + 2 * a.radius;
   const long long total = (long long)(a.g.n_r - 1) * n_th;
@@ -801,7 +804,7 @@ __global__ void __launch_bounds__(256, V + 1) half_bal_kernel(StepArgs a) {
 }
 
 template <int W, int V = 0>
-__global__ void __launch_bounds__(256, V + 1) full_bal_kernel(StepArgs a) {
+__global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) full_bal_kernel(StepArgs a) {
   extern __shared__ double sm[];
   const int n_th = a.g.n_th, gstride = n_th + 2 * a.radius;
   const long long total = (long long)(a.g.n_r - 2) * n_th;

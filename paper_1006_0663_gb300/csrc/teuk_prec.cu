@@ -301,15 +301,8 @@ int dissipate_impl(teuk_s* h) {
 // rows per block (y). Default: about 128 threads per block, so that the last wave of blocks
 // still spreads over every SM; teuk_tune picks the fastest rows-per-block instead.
 void step_shape(const teuk_s* h, dim3& blk) {
-  int tx = ((h->n_th + 31) / 32) * 32;
-  if (tx > 256) tx = 256;
-  if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
-  if (h->kernel_family == 2) {  // balanced kernels: one row of threads per block
-    blk = dim3(tx, 1);
-    return;
-  }
-  int ty = h->rows_per_block > 0 ? h->rows_per_block : (tx >= 128 ? 1 : 128 / tx);
-  while (ty > 1 && tx * ty > 256) ty /= 2;
+  int tx, ty;
+  row_block_shape(h, tx, ty);
   blk = dim3(tx, ty);
 }
 
