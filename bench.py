@@ -49,9 +49,11 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
            ("c3", "full_kernel<4, 0>"): (34.35e6, "32 x 1", "profiles/step_kernels_qd_c3.txt")}
 
 
-def kernel_name(dom, W, shape):
+def kernel_name(dom, W, shape, engine=0):
     """The step kernel a launch shape selects (teuk_launch_shape variants 0..8)."""
     v = shape["variant"]
+    if engine == 1:
+        return f"{dom}_ix_kernel<{v % 3}>"
     fam = "" if v < 3 else ("seg_" if v < 6 else "bal_")
     return f"{dom}_{fam}kernel<{W}, {v % 3}>"
 
@@ -72,6 +74,8 @@ def parse():
                     help="workload of the main line (default c2, the benchmark configuration)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 4],
                     help="words per real (0: the workload's own precision)")
+    ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
+                    help="double-double arithmetic: 0 FP64 error-free transforms, 1 integer engine")
     ap.add_argument("--shape", default="",
                     help="pin the step kernels' launch shape 'threads_theta,rows,variant' "
                          "instead of autotuning (profiling)")
@@ -125,9 +129,11 @@ def stop_clock_sampler(p, f, path, device_index):
 
 
 # ---------------------------------------------------------------------------------------------
-def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=True, shape=""):
+def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=True, shape="", engine=0):
     """Device-resident timing of `steps` outer steps; returns a dict of measurements."""
     g = teuk.Teuk.from_problem(prob, precision=words)
+    if engine:
+        g.set_engine(engine)
     ar, ai = prob.amps
     g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
     g.set_observer(prob.rstar_obs, capacity=steps + warmup + 1)
@@ -529,7 +535,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     sampler = start_clock_sampler()
-    res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush, shape=args.shape)
+    res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush, shape=args.shape,
+                       engine=args.engine if W == 2 else 0)
     clocks = stop_clock_sampler(*sampler, device_index=local)
     torch.cuda.synchronize()
     updates_per_rank = res["points"] * res["substeps"] * args.steps
@@ -554,7 +561,7 @@ def main():
         peak = 2.0 * sms * mhz * 1e6
         probe = teuk.fp64_peak()
         achieved = ops / (avg * 1e-3)
-        kname = kernel_name(dom, W, res["rows_per_block"])
+        kname = kernel_name(dom, W, res["rows_per_block"], args.engine if W == 2 else 0)
         tr = TRAFFIC.get((args.workload, kname))
         roofline = {
             "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",

@@ -61,6 +61,10 @@ void free_all(teuk_s* h) {
     if (*b) cudaFree(*b);
     *b = nullptr;
   }
+  if (h->ix_m) cudaFree(h->ix_m);
+  if (h->ix_e) cudaFree(h->ix_e);
+  h->ix_m = nullptr;
+  h->ix_e = nullptr;
   if (h->status) cudaFree(h->status);
   h->status = nullptr;
   if (h->d_ring_counter) cudaFree(h->d_ring_counter);
@@ -371,6 +375,21 @@ int teuk_use_graphs(teuk_t h, int enable) {
   return TEUK_OK;
 }
 
+int teuk_set_engine(teuk_t h, int engine) {
+  if (!h || engine < 0 || engine > 1) return TEUK_ERR_INVALID_ARG;
+  if (engine == 1 && h->W != 2) return invalid(h, "the integer engine is for double-double handles");
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  if (engine == 1) h->kernel_family = 0;
+  switch (h->W) {
+    case 1: return teuk::engine_w1(h, engine);
+    case 2: return teuk::engine_w2(h, engine);
+    default: return teuk::engine_w4(h, engine);
+  }
+}
+
+int teuk_engine(teuk_t h) { return h ? h->engine : TEUK_ERR_INVALID_ARG; }
+
 int teuk_set_dissipation(teuk_t h, double sigma) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   if (!(sigma >= 0) || !std::isfinite(sigma) || sigma > 4.0)
@@ -581,6 +600,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
       for (int ty = 1; ty <= 8 && tx * ty <= cap && rc == TEUK_OK; ty *= 2) trial(0, v, tx, ty);
       if (tx == tx_top) break;
     }
+    if (h->engine == 1) continue;  // the integer engine has the rows-per-block kernels only
     // one warp per (row, 32 columns)
     if (rc == TEUK_OK) trial(1, v, 0, 0);
     // balanced: the same number of points for every resident block
@@ -625,6 +645,8 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
 
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant) {
   if (!h || variant < 0 || variant > 8) return TEUK_ERR_INVALID_ARG;
+  if (h->engine == 1 && variant >= 3)
+    return invalid(h, "launch shape: the integer engine has the rows-per-block kernels only (variants 0..2)");
   if (variant >= 6) {
     if (threads_theta < 32 || threads_theta % 32 != 0 || threads_theta > 256)
       return invalid(h, "launch shape: threads_theta a multiple of 32, at most 256");
@@ -700,7 +722,7 @@ int teuk_fp64_peak(double* ops_per_second) {
 }
 
 int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out, int64_t n) {
-  if (!a || !b || !out || n < 0 || op < 0 || op > 8) return TEUK_ERR_INVALID_ARG;
+  if (!a || !b || !out || n < 0 || op < 0 || op > 9) return TEUK_ERR_INVALID_ARG;
   switch (words) {
     case 1: return teuk::mw_eval_w1(op, device, a, b, out, n);
     case 2: return teuk::mw_eval_w2(op, device, a, b, out, n);

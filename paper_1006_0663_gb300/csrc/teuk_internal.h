@@ -70,6 +70,10 @@ struct teuk_s {
   double ko_sigma = 0;                 // r* dissipation strength (0: off, the paper's scheme)
   double ko_eps_w[4] = {0, 0, 0, 0};   // sigma dt / (16 dr*) as words
   double* u_ko = nullptr;              // output of the dissipation step (state layout)
+  int engine = 0;                      // double-double arithmetic: 0 FP64 error-free transforms,
+                                       // 1 integer engine (ix.cuh)
+  uint4* ix_m = nullptr;               // integer-engine tables: node coefficients, half-node
+  int* ix_e = nullptr;                 // coefficients, stencil weights (mantissas, exponent-sign)
   std::string last_error;
 };
 
@@ -91,6 +95,9 @@ int substep_buffers_w4(teuk_s* h, const double* u_in, double* u_out, double* scr
 int prepare_w1(teuk_s* h);
 int prepare_w2(teuk_s* h);
 int prepare_w4(teuk_s* h);
+int engine_w1(teuk_s* h, int engine);
+int engine_w2(teuk_s* h, int engine);
+int engine_w4(teuk_s* h, int engine);
 int dissipation_w1(teuk_s* h, double sigma);
 int dissipation_w2(teuk_s* h, double sigma);
 int dissipation_w4(teuk_s* h, double sigma);

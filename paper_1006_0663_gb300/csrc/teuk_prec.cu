@@ -4,8 +4,12 @@
 #include <cstring>
 #include <vector>
 
+#include "ix.cuh"
 #include "teuk_internal.h"
 #include "teuk_kernels.cuh"
+#if TEUK_WORDS == 2
+#include "teuk_ix.cuh"
+#endif
 
 #ifndef TEUK_WORDS
 #error "TEUK_WORDS must be 1, 2 or 4"
@@ -297,6 +301,37 @@ int dissipate_impl(teuk_s* h) {
   return TEUK_OK;
 }
 
+// Arithmetic engine of the double-double step (0: FP64 error-free transforms, 1: integer
+// engine). The integer engine keeps the coefficient tables and stencil weights in its own
+// format, converted here once from the double-double tables.
+int engine_impl(teuk_s* h, int engine) {
+  if (engine == 0) {
+    h->engine = 0;
+    return TEUK_OK;
+  }
+#if TEUK_WORDS == 2
+  if (!h->ix_m) {
+    const size_t ncn = (size_t)8 * h->n_r * h->pitch, nch = (size_t)8 * (h->n_r - 1) * h->pitch;
+    const size_t nw = (size_t)(2 * h->radius + 1) * h->n_th, total = ncn + nch + nw;
+    TEUK_CUDA(h, cudaMalloc(&h->ix_m, total * sizeof(uint4)));
+    TEUK_CUDA(h, cudaMalloc(&h->ix_e, total * sizeof(int)));
+    const size_t ws = (size_t)h->n_r * h->pitch, hs = (size_t)(h->n_r - 1) * h->pitch;
+    ix_table_kernel<<<(unsigned)((ncn + 255) / 256), 256, 0, h->stream>>>(h->cn, ws, ws, ncn, h->ix_m, h->ix_e);
+    ix_table_kernel<<<(unsigned)((nch + 255) / 256), 256, 0, h->stream>>>(h->ch, hs, hs, nch, h->ix_m + ncn,
+                                                                          h->ix_e + ncn);
+    ix_table_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, h->stream>>>(h->wts, h->n_th, h->n_th, nw,
+                                                                         h->ix_m + ncn + nch, h->ix_e + ncn + nch);
+    TEUK_CUDA(h, cudaGetLastError());
+    TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  h->engine = 1;
+  return TEUK_OK;
+#else
+  h->last_error = "the integer engine is for double-double handles";
+  return TEUK_ERR_INVALID_ARG;
+#endif
+}
+
 // Launch shape of the step kernels: threads along theta (x, one warp multiple up to 256) and
 // rows per block (y). Default: about 128 threads per block, so that the last wave of blocks
 // still spreads over every SM; teuk_tune picks the fastest rows-per-block instead.
@@ -344,6 +379,28 @@ int prepare_impl(teuk_s* h) {
 template <int V>
 int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
   const int nh = h->n_r - 1, nf = h->n_r - 2;
+#if TEUK_WORDS == 2
+  if (h->engine == 1) {
+    // integer engine: the row family's block shape, shared rows in the engine's format
+    const size_t ncn = (size_t)8 * h->n_r * h->pitch, nch = (size_t)8 * (h->n_r - 1) * h->pitch;
+    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + ncn, h->ix_e + ncn, h->ix_m + ncn + nch, h->ix_e + ncn + nch};
+    const size_t ism = (size_t)blk.y * 2 * (h->n_th + 2 * h->radius) * (sizeof(uint4) + sizeof(int));
+    if (ism > 48 * 1024) {
+      TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+      TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+    }
+    cudaEvent_t ev = nullptr;
+    time_begin(h, &ev);
+    half_ix_kernel<V><<<(nh + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+    time_end(h, 0, ev);
+    time_begin(h, &ev);
+    full_ix_kernel<V><<<(nf + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+    time_end(h, 1, ev);
+    h->launches += 2;
+    TEUK_CUDA(h, cudaGetLastError());
+    return TEUK_OK;
+  }
+#endif
   if (h->kernel_family == 1) {
     const int nseg = (h->n_th + 31) / 32;
     const size_t seg_smem = (size_t)4 * 2 * W * (32 + 2 * h->radius) * sizeof(double);
@@ -487,13 +544,35 @@ __host__ __device__ R dot11(const double* a, const double* b, const double* out,
   return acc.get();
 }
 
+// op 9 (double-double only): the same sum through the integer engine (ix.cuh): the 11
+// products and the initial value as terms of one exact dot product, rounded once.
+__host__ __device__ R ix_dot11(const double* a, const double* b, const double* out, int64_t n, int64_t t) {
+  if (W != 2) return r_from<R>(0.0);
+  uint32_t bad = 0;
+  ix::Num c[12], v[12];
+  const ix::Num one{{0u, 0u, 0u, 0x40000000u}, -126, 0u};
+  c[0] = one;
+  v[0] = ix::from_dd(out[t], out[n + t], bad);
+  for (int q = 0; q < 11; ++q) {
+    const int64_t u = (t + q) % n;
+    c[q + 1] = ix::from_dd(a[u], a[n + u], bad);
+    v[q + 1] = ix::from_dd(b[u], b[n + u], bad);
+  }
+  ix::Acc acc;
+  int B;
+  ix::dot<12>(c, v, acc, B);
+  const mw::dd r = ix::to_dd(acc, B);
+  double w[4] = {r.h, r.l, 0.0, 0.0};
+  return from_words<R>(w);
+}
+
 __global__ void mw_eval_kernel(int op, const double* a, const double* b, double* out, double* res, int64_t n,
                                R ln2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0};
-  if (op == 8) {
-    to_words(dot11(a, b, out, n, t), wo);
+  if (op == 8 || op == 9) {
+    to_words(op == 8 ? dot11(a, b, out, n, t) : ix_dot11(a, b, out, n, t), wo);
     for (int k = 0; k < W; ++k) res[k * n + t] = wo[k];
     return;
   }
@@ -505,11 +584,12 @@ __global__ void mw_eval_kernel(int op, const double* a, const double* b, double*
 
 int mw_eval_impl(int op, int device, const double* a, const double* b, double* out, int64_t n) {
   const R ln2 = r_ln2<R>();
-  if (!device && op == 8) {
+  if (op == 9 && W != 2) return TEUK_ERR_INVALID_ARG;
+  if (!device && (op == 8 || op == 9)) {
     std::vector<double> res((size_t)W * n);
     for (int64_t t = 0; t < n; ++t) {
       double wo[4];
-      to_words(dot11(a, b, out, n, t), wo);
+      to_words(op == 8 ? dot11(a, b, out, n, t) : ix_dot11(a, b, out, n, t), wo);
       for (int k = 0; k < W; ++k) res[k * n + t] = wo[k];
     }
     std::memcpy(out, res.data(), res.size() * sizeof(double));
@@ -552,6 +632,7 @@ int TEUK_SUFFIX(pulse_w)(teuk_s* h, double center, double width, double ar, doub
 }
 int TEUK_SUFFIX(substep_w)(teuk_s* h, bool record, int64_t slot) { return substep_impl(h, record, slot); }
 int TEUK_SUFFIX(prepare_w)(teuk_s* h) { return prepare_impl(h); }
+int TEUK_SUFFIX(engine_w)(teuk_s* h, int engine) { return engine_impl(h, engine); }
 int TEUK_SUFFIX(dissipation_w)(teuk_s* h, double sigma) { return dissipation_impl(h, sigma); }
 int TEUK_SUFFIX(dissipate_w)(teuk_s* h) { return dissipate_impl(h); }
 int TEUK_SUFFIX(project_w)(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first) {

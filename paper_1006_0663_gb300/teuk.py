@@ -28,7 +28,7 @@ SYMBOLS = [
     "teuk_tune", "teuk_batch_create", "teuk_batch_step", "teuk_batch_sync", "teuk_batch_info",
     "teuk_batch_destroy", "teuk_use_graphs", "teuk_launch_shape",
     "teuk_set_launch_shape", "teuk_read_multipoles", "teuk_substep_host_state",
-    "teuk_set_dissipation",
+    "teuk_set_dissipation", "teuk_set_engine", "teuk_engine",
 ]
 
 
@@ -76,6 +76,8 @@ def lib(build_if_missing: bool = True):
         L.teuk_read_multipoles.argtypes = [vp, i32, i32, dp, P(i64)]
         L.teuk_substep_host_state.argtypes = [vp, dp, i64]
         L.teuk_set_dissipation.argtypes = [vp, d]
+        L.teuk_set_engine.argtypes = [vp, i32]
+        L.teuk_engine.argtypes = [vp]
         L.teuk_get_state.argtypes = [vp, dp, P(i64)]
         L.teuk_set_state.argtypes = [vp, dp, i64]
         L.teuk_get_state_device.argtypes = [vp, vp]
@@ -217,6 +219,14 @@ class Teuk:
         if n.value:
             _check(lib().teuk_read_waveform(self._h, _dp(out), ctypes.byref(n)), self._h)
         return out
+
+    def set_engine(self, engine):
+        """Double-double arithmetic engine: 0 FP64 error-free transforms, 1 integer engine."""
+        _check(lib().teuk_set_engine(self._h, int(engine)), self._h)
+
+    @property
+    def engine(self) -> int:
+        return int(lib().teuk_engine(self._h))
 
     def set_dissipation(self, sigma):
         """r* Kreiss-Oliger dissipation once per outer step (not part of the paper's scheme;

@@ -519,3 +519,105 @@ def test_dissipation_parity(oracle_mod, W):
     np.testing.assert_array_equal(g0.get_state(), g1.get_state())
     with pytest.raises(teuk.TeukError):
         g1.set_dissipation(-1.0)
+
+
+def test_integer_engine_dot_device_matches_host():
+    rng = np.random.default_rng(21)
+    n = 2048
+    a = np.zeros((2, n)); b = np.zeros((2, n)); o = np.zeros((2, n))
+    for x in (a, b, o):
+        x[0] = rng.uniform(-2, 2, n) * 2.0 ** rng.integers(-60, 60, n)
+        x[1] = x[0] * rng.uniform(-1, 1, n) * 2.0 ** -54
+    a[:, ::17] = 0.0
+    h = teuk.mw_eval(9, 2, a, b, out=o, device=False)
+    d = teuk.mw_eval(9, 2, a, b, out=o, device=True)
+    np.testing.assert_array_equal(h, d)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_integer_engine_evolution_parity(oracle_mod, case):
+    """Double-double through the integer engine (every dot product exact on the integer pipe,
+    rounded once) against the 256-bit oracle, the same cases as the FP64-transform engine."""
+    p = small(**CASES[case])
+    g, o = make_pair(oracle_mod, p, 2)
+    g.set_engine(1)
+    assert g.engine == 1
+    ell = max(abs(p["m"]), abs(p["s"]))
+    g.set_initial_pulse(12.0, 4.0, 0.8, 0.55, ell)
+    o.pulse(12.0, 4.0, 0.8, 0.55, ell)
+    g.step(3)
+    g.sync()
+    o.step(3 * p["substeps"])
+    err, umax = o.max_rel_err(g.get_state())
+    assert umax > 0.05
+    assert err < TOL[2], err
+
+
+def test_integer_engine_full_size_window(oracle_mod):
+    """c2 at full size on the integer engine, in the benchmark's launch configuration, against a
+    256-bit oracle window around the pulse after 12 iterations."""
+    prob = workloads.CONFIGS["c2"]
+    p = dict(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min, rstar_max=prob.rstar_max,
+             n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0, substeps=prob.substeps, theta_order=10, parity=0)
+    g = teuk.Teuk(precision=2, **p)
+    g.set_engine(1)
+    g.tune()
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    nsub = 12
+    g.substep(nsub)
+    g.sync()
+    full = g.get_state()
+    ic = int(round((prob.center - prob.rstar_min) / prob.dr))
+    lo, hi = ic - 12, ic + 12
+    wlo, whi = lo - nsub - 1, hi + nsub + 1
+    o = oracle_mod.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
+                          rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
+                          substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=256)
+    o.pulse(prob.center, prob.width, ar, ai, prob.ell)
+    o.step(nsub)
+    err, umax = o.max_rel_err(np.ascontiguousarray(full[:, :, wlo:whi + 1]), lo - wlo, hi - wlo)
+    assert umax > 0 and err < TOL[2], err
+
+
+@pytest.mark.parametrize("n_theta", [24, 70])
+def test_integer_engine_launch_shapes_and_graphs_bitwise(n_theta):
+    """Within the integer engine every launch shape and register budget, and graph replay,
+    give the same bits (integer arithmetic per point does not depend on the launch)."""
+    p = small(n_r=37, n_theta=n_theta)
+    ref = None
+    for tx, ty, v, graphs in [(32, 1, 0, True), (64, 2, 1, False), (32, 4, 2, True), (128, 1, 1, True)]:
+        g = teuk.Teuk(precision=2, **p)
+        g.set_engine(1)
+        g.set_launch_shape(tx, ty, v)
+        g.use_graphs(graphs)
+        g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+        g.set_observer(5.0, capacity=4)
+        g.step(2)
+        g.sync()
+        st = (g.get_state(), g.read_waveform())
+        if ref is None:
+            ref = st
+        else:
+            np.testing.assert_array_equal(st[0], ref[0], err_msg=str((tx, ty, v)))
+            np.testing.assert_array_equal(st[1], ref[1], err_msg=str((tx, ty, v)))
+        g.close()
+
+
+def test_integer_engine_reports_nonfinite_and_rejects_other_precisions():
+    p = small()
+    g = teuk.Teuk(precision=2, **p)
+    g.set_engine(1)
+    g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+    st = g.get_state()
+    st[0, 0, 20, 5] = np.inf
+    g.set_state(st)
+    g.step(1)
+    with pytest.raises(teuk.TeukError) as e:
+        g.sync()
+    assert e.value.code == teuk.ERR_NONFINITE
+    for W in (1, 4):
+        h = teuk.Teuk(precision=W, **p)
+        with pytest.raises(teuk.TeukError):
+            h.set_engine(1)
+        assert h.engine == 0

@@ -160,3 +160,45 @@ def test_dot11_accumulator_with_cancellation_host(words):
         got = _words_value(out, t)
         worst = max(worst, float(abs(got - want) / sum(abs(x) for x in terms)))
     assert worst < BOUND[words], worst
+
+
+def test_integer_engine_dot_host():
+    """The integer engine's dot product (op 9: out + 11 products, double-double operands of
+    exponents spread over +-200 binades, zeros, repeated terms) against mpmath: the error
+    stays within 2^-104 of the exact result plus 2^-150 of the largest term, and the result
+    is a normalised double-double."""
+    mpm.mp.prec = 600
+    rng = np.random.default_rng(11)
+    n = 200
+
+    def rand_dd(e):
+        v = mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** int(e)
+        for k in range(1, 4):
+            v += mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** (int(e) - 53 * k)
+        h = float(v)
+        return h, float(v - h)
+
+    a = np.zeros((2, n)); b = np.zeros((2, n)); o = np.zeros((2, n))
+    for t in range(n):
+        a[:, t] = rand_dd(rng.integers(-200, 200))
+        b[:, t] = rand_dd(rng.integers(-200, 200))
+        o[:, t] = rand_dd(rng.integers(-400, 400))
+    a[:, 5] = 0; b[:, 7] = 0; o[:, 9] = 0; a[:, 40:60] = 0; o[:, 45] = 0
+    a[:, 100:111] = a[:, 100:101]; b[:, 100:111] = -b[:, 100:101]
+    r = teuk.mw_eval(9, 2, a, b, out=o, device=False)
+
+    def val(x, t):
+        return mpm.mpf(float(x[0, t])) + mpm.mpf(float(x[1, t]))
+
+    for t in range(n):
+        terms = [val(a, (t + q) % n) * val(b, (t + q) % n) for q in range(11)] + [val(o, t)]
+        exact = mpm.fsum(terms)
+        big = max(abs(x) for x in terms)
+        got = val(r, t)
+        if big == 0:
+            assert got == 0
+            continue
+        assert abs(got - exact) <= abs(exact) * mpm.mpf(2) ** -104 + big * mpm.mpf(2) ** -150, t
+        assert abs(r[1, t]) <= np.spacing(abs(r[0, t])) / 2, t
+    with pytest.raises(teuk.TeukError):
+        teuk.mw_eval(9, 4, np.zeros((4, 3)), np.zeros((4, 3)), device=False)
