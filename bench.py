@@ -39,6 +39,7 @@ OPS_FULL = {1: 50, 2: 498, 4: 3734}
 BYTES_HALF = {w: (4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
 BYTES_FULL = {w: (4 + 4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
 DTYPE = {1: "f64", 2: "f64x2 (double-double)", 4: "f64x4 (quad-double)"}
+ENGINE_NAME = {0: "FP64 error-free transforms", 1: "integer engine"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the kernel as it stands: (workload, kernel function) -> (bytes, launch shape captured, summary).
 TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profiles/step_kernels_dd_c2.txt"),
@@ -47,6 +48,12 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
            ("c5", "full_kernel<1, 0>"): (1085.83e6 + 247.52e6, "64 x 1", "profiles/step_kernels_f64_c5.txt"),
            ("c3", "half_kernel<4, 0>"): (25.95e6, "32 x 1", "profiles/step_kernels_qd_c3.txt"),
            ("c3", "full_kernel<4, 0>"): (34.35e6, "32 x 1", "profiles/step_kernels_qd_c3.txt")}
+
+
+# Integer-engine kernels (double-double): executed thread instructions per grid point for one
+# launch (ncu smsp__inst_executed.sum x smsp__thread_inst_executed_per_inst_executed / points).
+IX_INST = {"half": (5635, "profiles/step_kernels_ix_dd_c2.txt"),
+           "full": (6055, "profiles/step_kernels_ix_dd_c2.txt")}
 
 
 def kernel_name(dom, W, shape, engine=0):
@@ -74,8 +81,9 @@ def parse():
                     help="workload of the main line (default c2, the benchmark configuration)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 4],
                     help="words per real (0: the workload's own precision)")
-    ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
-                    help="double-double arithmetic: 0 FP64 error-free transforms, 1 integer engine")
+    ap.add_argument("--engine", type=int, default=-1, choices=[-1, 0, 1],
+                    help="double-double arithmetic: 0 FP64 error-free transforms, 1 integer engine "
+                         "(default -1: the integer engine for double-double)")
     ap.add_argument("--shape", default="",
                     help="pin the step kernels' launch shape 'threads_theta,rows,variant' "
                          "instead of autotuning (profiling)")
@@ -171,13 +179,15 @@ def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=Tru
     return out
 
 
-def stated_error(prob, words, teuk, nsub=12):
+def stated_error(prob, words, teuk, nsub=12, engine=0):
     """Error of this workload's GPU state against the 256-bit oracle (FP64 oracle for FP64)
     after nsub Lax-Wendroff iterations, on a window of rows around the pulse, where the window
     interior is exact (domain of dependence)."""
     import oracle
     oracle.build()
     g = teuk.Teuk.from_problem(prob, precision=words)
+    if engine:
+        g.set_engine(engine)
     ar, ai = prob.amps
     g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
     g.substep(nsub)
@@ -195,7 +205,7 @@ def stated_error(prob, words, teuk, nsub=12):
     o.step(nsub)
     err, _ = o.max_rel_err(full[:, :, wlo:whi + 1].copy(), lo - wlo, hi - wlo)
     return {"max_rel_err": err, "oracle_bits": bits, "iterations": nsub,
-            "rows": f"{lo}..{hi} of {prob.n_r}", "tolerance": TOL[words]}
+            "rows": f"{lo}..{hi} of {prob.n_r}", "tolerance": TOL[words], "engine": engine}
 
 
 def run_batch1(prob, words, steps, torch, teuk):
@@ -256,11 +266,13 @@ def run_c4(torch, teuk, workloads):
             "one_at_a_time_ms_per_step": t_seq * 1e3, "grid_blocks": info["grid"]}
 
 
-def run_e2e(prob, words, steps, torch, teuk):
+def run_e2e(prob, words, steps, torch, teuk, engine=0):
     """Through the public API with host buffers: per step H2D of the state from pinned host
     memory, one outer step, D2H of the observer row."""
     import numpy as np
     g = teuk.Teuk.from_problem(prob, precision=words)
+    if engine:
+        g.set_engine(engine)
     ar, ai = prob.amps
     g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
     g.tune()
@@ -284,12 +296,14 @@ def run_e2e(prob, words, steps, torch, teuk):
                 d2h_bytes_per_step=int(obs.nbytes))
 
 
-def run_design_a(prob, words, iters, torch, teuk):
+def run_design_a(prob, words, iters, torch, teuk, engine=0):
     """The data flow of the paper's first CUDA design (Sec. 4) on this machine's CPU-GPU link:
     the host keeps the state and every Lax-Wendroff iteration copies it to the device and
     back (page-locked host memory, one cudaMemcpy2DAsync each way, the host waits), with all
     arithmetic on the device. Against the same iterations with the state resident in HBM."""
     g = teuk.Teuk.from_problem(prob, precision=words)
+    if engine:
+        g.set_engine(engine)
     ar, ai = prob.amps
     g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
     g.tune()
@@ -315,6 +329,49 @@ def run_design_a(prob, words, iters, torch, teuk):
     return {"updates_per_s": upd / t_a, "resident_updates_per_s": upd / t_r, "slowdown": t_a / t_r,
             "iterations": iters, "link_bytes_per_iteration": link,
             "link_gbps_effective": link * iters / (t_a - t_r) / 1e9 if t_a > t_r else None}
+
+
+def roofline_for(res, prob, W, engine, clocks, sms, probe, workload):
+    """Roofline of the dominant step kernel of a run (live CUDA-event launch durations).
+
+    FP64 error-free-transform kernels: bound by the FP64 pipe, 2 operations per SM per cycle
+    (ncu sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per cycle for
+    152 SMs), counted from the scheme's operation list. Integer-engine kernels (double-double):
+    bound by instruction issue, 4 warp instructions = 128 thread instructions per SM per cycle,
+    counted as the executed thread instructions per point of the ncu capture."""
+    ms_h, ms_f, n_h, n_f = res["kernel_times"]
+    pts_h = (prob.n_r - 1) * prob.n_theta
+    pts_f = (prob.n_r - 2) * prob.n_theta
+    avg_h = ms_h / max(n_h, 1)
+    avg_f = ms_f / max(n_f, 1)
+    dom = "half" if ms_h >= ms_f else "full"
+    avg = avg_h if dom == "half" else avg_f
+    pts = pts_h if dom == "half" else pts_f
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    kname = kernel_name(dom, W, res["rows_per_block"], engine)
+    tr = TRAFFIC.get((workload, kname))
+    if engine == 1:
+        ops_pt, ops_src = IX_INST[dom]
+        peak = 128.0 * sms * mhz * 1e6
+        peak_source = f"4 warp instructions/SM/cycle x 32 threads x {sms} SMs x {mhz:.0f} MHz (issue limit)"
+        op_unit = f"executed thread instructions per point, ncu capture ({ops_src})"
+    else:
+        ops_pt = OPS_HALF[W] if dom == "half" else OPS_FULL[W]
+        peak = 2.0 * sms * mhz * 1e6
+        peak_source = f"2 FP64 ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (SM clock sampled during the timed region)"
+        op_unit = "FP64 pipe operations (add, mul, fma count one each)"
+    achieved = ops_pt * pts / (avg * 1e-3)
+    return {
+        "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+        "unit": "T inst/s" if engine == 1 else "Tops/s",
+        "frac": achieved / peak, "traffic": tr[0] if tr else None,
+        "traffic_source": f"{tr[2]} (launch shape {tr[1]})" if tr else None,
+        "kernel": kname, "avg_launch_ms": avg, "launch_shape": res["rows_per_block"],
+        "ops_per_point": ops_pt, "peak_source": peak_source, "op_unit": op_unit,
+        "fma_chain_probe_tops": probe / 1e12,
+        "hbm_achieved_gbs": (BYTES_HALF[W] if dom == "half" else BYTES_FULL[W]) * pts / (avg * 1e-3) / 1e9,
+        "fraction_of_step_in_dominant_kernel": (ms_h if dom == "half" else ms_f) / max(res["ms_total"], 1e-9),
+    }
 
 
 def cpu_model():
@@ -535,8 +592,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     sampler = start_clock_sampler()
-    res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush, shape=args.shape,
-                       engine=args.engine if W == 2 else 0)
+    engine = (1 if W == 2 else 0) if args.engine < 0 else (args.engine if W == 2 else 0)
+    res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush, shape=args.shape, engine=engine)
     clocks = stop_clock_sampler(*sampler, device_index=local)
     torch.cuda.synchronize()
     updates_per_rank = res["points"] * res["substeps"] * args.steps
@@ -545,48 +602,16 @@ def main():
     out = None
     if rank == 0:
         describe_w = describe(prob) if W == prob.words else describe(prob).replace(DTYPE[prob.words], DTYPE[W])
-        ms_h, ms_f, n_h, n_f = res["kernel_times"]
-        pts_h = (prob.n_r - 1) * prob.n_theta
-        pts_f = (prob.n_r - 2) * prob.n_theta
-        avg_h = ms_h / max(n_h, 1)
-        avg_f = ms_f / max(n_f, 1)
-        dom = "half" if ms_h >= ms_f else "full"
-        ops = (OPS_HALF[W] * pts_h if dom == "half" else OPS_FULL[W] * pts_f)
-        avg = avg_h if dom == "half" else avg_f
-        # FP64 pipe peak: 2 operations per SM per cycle (ncu
-        # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per cycle for
-        # 152 SMs) x SMs x the SM clock sampled during the timed region.
         sms = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
-        peak = 2.0 * sms * mhz * 1e6
-        probe = teuk.fp64_peak()
-        achieved = ops / (avg * 1e-3)
-        kname = kernel_name(dom, W, res["rows_per_block"], args.engine if W == 2 else 0)
-        tr = TRAFFIC.get((args.workload, kname))
-        roofline = {
-            "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": tr[0] if tr else None,
-            "traffic_source": f"{tr[2]} (launch shape {tr[1]})" if tr else None,
-            "kernel": kname, "avg_launch_ms": avg,
-            "launch_shape": res["rows_per_block"],
-            "ops_per_point": OPS_HALF[W] if dom == "half" else OPS_FULL[W],
-            "peak_source": f"2 FP64 ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (SM clock sampled "
-                           "during the timed region)",
-            "fma_chain_probe_tops": probe / 1e12,
-            "op_unit": "FP64 pipe operations (add, mul, fma count one each)",
-            "hbm_achieved_gbs": (BYTES_HALF[W] * pts_h if dom == "half" else BYTES_FULL[W] * pts_f)
-            / (avg * 1e-3) / 1e9,
-            "fraction_of_step_in_dominant_kernel": (ms_h if dom == "half" else ms_f)
-            / max(res["ms_total"], 1e-9),
-        }
-        e2e = run_e2e(prob, W, max(3, args.steps // 2), torch, teuk)
+        roofline = roofline_for(res, prob, W, engine, clocks, sms, teuk.fp64_peak(), args.workload)
+        e2e = run_e2e(prob, W, max(3, args.steps // 2), torch, teuk, engine)
         if W != prob.words or args.workload != WORKLOAD:
             args.no_variants = args.no_batch = True
         variants = {}
         if not args.no_variants:
             for name, w, nst in (("c1", 1, 20), ("c5", 1, 2), ("c3", 4, 2), ("c5", 2, 1)):
                 p = workloads.CONFIGS[name]
-                r = run_workload(p, w, nst, 1, torch, teuk, flush, with_timing=False)
+                r = run_workload(p, w, nst, 1, torch, teuk, flush, with_timing=False, engine=engine if w == 2 else 0)
                 variants[f"{name}/{DTYPE[w].split(' ')[0]}"] = {
                     "updates_per_s": p.n_r * p.n_theta * p.substeps * nst / (r["ms_total"] * 1e-3),
                     "ms_per_step": r["ms_total"] / nst, "launch": "CUDA graph per outer step"}
@@ -598,19 +623,26 @@ def main():
             variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} 2nd-order theta"] = {
                 "updates_per_s": p2.points * p2.substeps * 2 / (r["ms_total"] * 1e-3),
                 "ms_per_step": r["ms_total"] / 2, "launch": "CUDA graph per outer step"}
-            variants["design_a_host_state"] = run_design_a(prob, W, 2 * prob.substeps, torch, teuk)
+            variants["design_a_host_state"] = run_design_a(prob, W, 2 * prob.substeps, torch, teuk, engine)
+            if W == 2:
+                other = 1 - engine
+                r0 = run_workload(prob, W, max(2, args.steps // 2), 2, torch, teuk, flush, engine=other)
+                variants[f"{prob.name}/f64x2 {ENGINE_NAME[other]}"] = {
+                    "updates_per_s": r0["points"] * r0["substeps"] * max(2, args.steps // 2) / (r0["ms_total"] * 1e-3),
+                    "roofline": roofline_for(r0, prob, W, other, clocks, sms, teuk.fp64_peak(), args.workload)}
         batched = None if args.no_batch else run_c4(torch, teuk, workloads)
         cpu = None if args.no_cpu else cpu_baseline(prob, W)
         if cpu is not None:
             cpu["cpu_model"] = cpu_model()
             if W > 1:
                 cpu["other_runs"] = cpu_baseline_others(prob)
-        parity = None if args.no_cpu else stated_error(prob, W, teuk)
+        parity = None if args.no_cpu else stated_error(prob, W, teuk, engine=engine)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[W], "data": "synthetic",
             "config": {"workload": describe_w,
+                       "arithmetic": ENGINE_NAME[engine] if W == 2 else "FP64 error-free transforms",
                        "l2": "256 MiB buffer written between timed steps (outside the timed "
                              "interval); the 100 MB working set is L2-resident within a step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -335,17 +335,59 @@ MW_HD void dot(const Num* c, const Num* v, Acc& acc, int& B) {
   B = acc_base(maxE);
 }
 
-// Exact-to-2^-126 sum / difference of two Nums (the smaller is aligned to the larger and cut).
+// Sum or difference a + (-1)^negate_b b of two Nums with mantissas below 2^127 (made from
+// double-doubles): the operand of smaller exponent is shifted to the larger one's exponent
+// (bits below its last are cut: relative error < 2^-126 of the larger) and the mantissas are
+// added or subtracted; the result keeps the larger exponent (mantissa below 2^128).
 MW_HD Num add(const Num& a, const Num& b, uint32_t negate_b) {
-  // treat the sum as a two-term dot product with the constant one (2^126 * 2^-126)
-  const Num one{{0u, 0u, 0u, 0x40000000u}, -126, 0u};
-  Num c[2] = {one, one};
-  c[1].neg = negate_b;
-  Num v[2] = {a, b};
-  Acc acc;
-  int B;
-  dot<2>(c, v, acc, B);
-  return to_num(acc, B);
+  const uint32_t bneg = b.neg ^ negate_b;
+  if (b.e == kZeroE) { Num r = a; return r; }
+  if (a.e == kZeroE) { Num r = b; r.neg = bneg; return r; }
+  const bool swap = b.e > a.e;
+  uint32_t big[4], sm[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    big[k] = swap ? b.m[k] : a.m[k];
+    sm[k] = swap ? a.m[k] : b.m[k];
+  }
+  const int e = swap ? b.e : a.e;
+  const uint32_t nbig = swap ? bneg : a.neg, nsm = swap ? a.neg : bneg;
+  const int s = swap ? b.e - a.e : a.e - b.e;
+  // sm >>= s (s >= 128 clears it)
+  const bool s128 = s >= 128, s64 = (s & 64) != 0, s32 = (s & 32) != 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sm[k] = s128 ? 0u : sm[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sm[k] = s64 ? (k + 2 < 4 ? sm[k + 2] : 0u) : sm[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sm[k] = s32 ? (k + 1 < 4 ? sm[k + 1] : 0u) : sm[k];
+  const uint32_t bs = (uint32_t)s & 31u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sm[k] = fshr(sm[k], k + 1 < 4 ? sm[k + 1] : 0u, bs);
+  // big +- sm as a signed 160-bit value
+  const uint32_t sub = nbig ^ nsm, mask = 0u - sub;
+  uint32_t r[5];
+  uint64_t c = sub;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t t = (uint64_t)big[k] + (sm[k] ^ mask) + c;
+    r[k] = lo32(t);
+    c = t >> 32;
+  }
+  r[4] = lo32(c + mask);  // 0 or 1 for a sum; 0 (no borrow) or 0xffffffff (negative) for a difference
+  const uint32_t flip = r[4] >> 31, fm = 0u - flip;
+  Num out;
+  uint64_t cc = flip;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t t = (uint64_t)(r[k] ^ fm) + cc;
+    out.m[k] = lo32(t);
+    cc = t >> 32;
+  }
+  out.e = e;
+  out.neg = nbig ^ flip;
+  if ((out.m[0] | out.m[1] | out.m[2] | out.m[3]) == 0) return zero();
+  return out;
 }
 
 }  // namespace ix

@@ -130,26 +130,25 @@ __device__ __forceinline__ void ix_half_point(const IxArgs& x, int h, int j, con
   const ix::Num LR = ix_theta(x, sRm + j, sRe + j, j), LI = ix_theta(x, sIm + j, sIe + j, j);
   const size_t ci = (size_t)h * pitch + j;
   int ce[8];
-  uint4 cm[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    ce[q] = __ldg(x.che + q * hs + ci);
-    cm[q] = __ldg(x.chm + q * hs + ci);
-  }
+  for (int q = 0; q < 8; ++q) ce[q] = __ldg(x.che + q * hs + ci);
+  // coefficient mantissas are read at each use (L1 hits) to keep fewer registers live
+  const uint4* cmp = x.chm + ci;
+#define CM(q) __ldg(cmp + (q) * hs)
   ix::Acc acc;
   int mx;
   // Phi_R = s_PhiR/2 - H0 d_PhiR + (h/4) s_PiR
   mx = imax(imax(ix::prod_exp(half.e, sPR.e), ix_texp(ce[0], dPR)), ix::prod_exp(h4.e, sQR.e));
   ix::acc_zero(acc);
   ix_term(acc, half, sPR, 0u, mx);
-  ix_term(acc, cm[0], ce[0], dPR, 1u, mx);
+  ix_term(acc, CM(0), ce[0], dPR, 1u, mx);
   ix_term(acc, h4, sQR, 0u, mx);
   ix_store_dd(a.uh + 0 * hs + ci, hs, ix::to_dd(acc, ix::acc_base(mx)), bad);
   // Phi_I
   mx = imax(imax(ix::prod_exp(half.e, sPI.e), ix_texp(ce[0], dPI)), ix::prod_exp(h4.e, sQI.e));
   ix::acc_zero(acc);
   ix_term(acc, half, sPI, 0u, mx);
-  ix_term(acc, cm[0], ce[0], dPI, 1u, mx);
+  ix_term(acc, CM(0), ce[0], dPI, 1u, mx);
   ix_term(acc, h4, sQI, 0u, mx);
   ix_store_dd(a.uh + 2 * hs + ci, hs, ix::to_dd(acc, ix::acc_base(mx)), bad);
   // Pi_R = H3 s_PiR + H4 s_PiI + H0 (Pi_R,h+1 - Pi_R,h) + H1 d_PhiR + H2 d_PhiI + H5 L_R + H6 s_PhiR - H7 s_PhiI
@@ -157,31 +156,32 @@ __device__ __forceinline__ void ix_half_point(const IxArgs& x, int h, int j, con
             imax(imax(ix_texp(ce[1], dPR), ix_texp(ce[2], dPI)),
                  imax(ix_texp(ce[5], LR), imax(ix_texp(ce[6], sPR), ix_texp(ce[7], sPI)))));
   ix::acc_zero(acc);
-  ix_term(acc, cm[3], ce[3], sQR, 0u, mx);
-  ix_term(acc, cm[4], ce[4], sQI, 0u, mx);
-  ix_term(acc, cm[0], ce[0], uQR1, 0u, mx);
-  ix_term(acc, cm[0], ce[0], uQR0, 1u, mx);
-  ix_term(acc, cm[1], ce[1], dPR, 0u, mx);
-  ix_term(acc, cm[2], ce[2], dPI, 0u, mx);
-  ix_term(acc, cm[5], ce[5], LR, 0u, mx);
-  ix_term(acc, cm[6], ce[6], sPR, 0u, mx);
-  ix_term(acc, cm[7], ce[7], sPI, 1u, mx);
+  ix_term(acc, CM(3), ce[3], sQR, 0u, mx);
+  ix_term(acc, CM(4), ce[4], sQI, 0u, mx);
+  ix_term(acc, CM(0), ce[0], uQR1, 0u, mx);
+  ix_term(acc, CM(0), ce[0], uQR0, 1u, mx);
+  ix_term(acc, CM(1), ce[1], dPR, 0u, mx);
+  ix_term(acc, CM(2), ce[2], dPI, 0u, mx);
+  ix_term(acc, CM(5), ce[5], LR, 0u, mx);
+  ix_term(acc, CM(6), ce[6], sPR, 0u, mx);
+  ix_term(acc, CM(7), ce[7], sPI, 1u, mx);
   ix_store_dd(a.uh + 4 * hs + ci, hs, ix::to_dd(acc, ix::acc_base(mx)), bad);
   // Pi_I = H3 s_PiI - H4 s_PiR + H0 (Pi_I,h+1 - Pi_I,h) + H1 d_PhiI - H2 d_PhiR + H5 L_I + H6 s_PhiI + H7 s_PhiR
   mx = imax(imax(imax(ix_texp(ce[3], sQI), ix_texp(ce[4], sQR)), imax(ix_texp(ce[0], uQI1), ix_texp(ce[0], uQI0))),
             imax(imax(ix_texp(ce[1], dPI), ix_texp(ce[2], dPR)),
                  imax(ix_texp(ce[5], LI), imax(ix_texp(ce[6], sPI), ix_texp(ce[7], sPR)))));
   ix::acc_zero(acc);
-  ix_term(acc, cm[3], ce[3], sQI, 0u, mx);
-  ix_term(acc, cm[4], ce[4], sQR, 1u, mx);
-  ix_term(acc, cm[0], ce[0], uQI1, 0u, mx);
-  ix_term(acc, cm[0], ce[0], uQI0, 1u, mx);
-  ix_term(acc, cm[1], ce[1], dPI, 0u, mx);
-  ix_term(acc, cm[2], ce[2], dPR, 1u, mx);
-  ix_term(acc, cm[5], ce[5], LI, 0u, mx);
-  ix_term(acc, cm[6], ce[6], sPI, 0u, mx);
-  ix_term(acc, cm[7], ce[7], sPR, 0u, mx);
+  ix_term(acc, CM(3), ce[3], sQI, 0u, mx);
+  ix_term(acc, CM(4), ce[4], sQR, 1u, mx);
+  ix_term(acc, CM(0), ce[0], uQI1, 0u, mx);
+  ix_term(acc, CM(0), ce[0], uQI0, 1u, mx);
+  ix_term(acc, CM(1), ce[1], dPI, 0u, mx);
+  ix_term(acc, CM(2), ce[2], dPR, 1u, mx);
+  ix_term(acc, CM(5), ce[5], LI, 0u, mx);
+  ix_term(acc, CM(6), ce[6], sPI, 0u, mx);
+  ix_term(acc, CM(7), ce[7], sPR, 0u, mx);
   ix_store_dd(a.uh + 6 * hs + ci, hs, ix::to_dd(acc, ix::acc_base(mx)), bad);
+#undef CM
 }
 
 // Eq. lw2, first phase: s_Phi = Phi_{i+1/2} + Phi_{i-1/2} into the ghosted engine-format row.
@@ -221,12 +221,10 @@ __device__ __forceinline__ bool ix_full_point(const IxArgs& x, int i, int j, con
   const ix::Num PR = ix_load(a.u_in + 0 * ws + ci, ws, bad), PI = ix_load(a.u_in + 2 * ws + ci, ws, bad);
   const ix::Num QR = ix_load(a.u_in + 4 * ws + ci, ws, bad), QI = ix_load(a.u_in + 6 * ws + ci, ws, bad);
   int ce[8];
-  uint4 cm[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    ce[q] = __ldg(x.cne + q * ws + ci);
-    cm[q] = __ldg(x.cnm + q * ws + ci);
-  }
+  for (int q = 0; q < 8; ++q) ce[q] = __ldg(x.cne + q * ws + ci);
+  const uint4* cmp = x.cnm + ci;
+#define CM(q) __ldg(cmp + (q) * ws)
   ix::Acc acc;
   int mx;
   mw::dd out[4];
@@ -234,14 +232,14 @@ __device__ __forceinline__ bool ix_full_point(const IxArgs& x, int i, int j, con
   mx = imax(imax(ix::prod_exp(one.e, PR.e), ix_texp(ce[0], dPR)), ix::prod_exp(h2.e, sQR.e));
   ix::acc_zero(acc);
   ix_term(acc, one, PR, 0u, mx);
-  ix_term(acc, cm[0], ce[0], dPR, 1u, mx);
+  ix_term(acc, CM(0), ce[0], dPR, 1u, mx);
   ix_term(acc, h2, sQR, 0u, mx);
   out[0] = ix::to_dd(acc, ix::acc_base(mx));
   // Phi_I'
   mx = imax(imax(ix::prod_exp(one.e, PI.e), ix_texp(ce[0], dPI)), ix::prod_exp(h2.e, sQI.e));
   ix::acc_zero(acc);
   ix_term(acc, one, PI, 0u, mx);
-  ix_term(acc, cm[0], ce[0], dPI, 1u, mx);
+  ix_term(acc, CM(0), ce[0], dPI, 1u, mx);
   ix_term(acc, h2, sQI, 0u, mx);
   out[1] = ix::to_dd(acc, ix::acc_base(mx));
   // Pi_R' = Pi_R + N0 (h_PiR,i+1/2 - h_PiR,i-1/2) + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L_R
@@ -251,15 +249,15 @@ __device__ __forceinline__ bool ix_full_point(const IxArgs& x, int i, int j, con
                  imax(imax(ix_texp(ce[4], sQI), ix_texp(ce[5], LR)), imax(ix_texp(ce[6], sPR), ix_texp(ce[7], sPI)))));
   ix::acc_zero(acc);
   ix_term(acc, one, QR, 0u, mx);
-  ix_term(acc, cm[0], ce[0], hQR1, 0u, mx);
-  ix_term(acc, cm[0], ce[0], hQR0, 1u, mx);
-  ix_term(acc, cm[1], ce[1], dPR, 0u, mx);
-  ix_term(acc, cm[2], ce[2], dPI, 0u, mx);
-  ix_term(acc, cm[3], ce[3], sQR, 0u, mx);
-  ix_term(acc, cm[4], ce[4], sQI, 0u, mx);
-  ix_term(acc, cm[5], ce[5], LR, 0u, mx);
-  ix_term(acc, cm[6], ce[6], sPR, 0u, mx);
-  ix_term(acc, cm[7], ce[7], sPI, 1u, mx);
+  ix_term(acc, CM(0), ce[0], hQR1, 0u, mx);
+  ix_term(acc, CM(0), ce[0], hQR0, 1u, mx);
+  ix_term(acc, CM(1), ce[1], dPR, 0u, mx);
+  ix_term(acc, CM(2), ce[2], dPI, 0u, mx);
+  ix_term(acc, CM(3), ce[3], sQR, 0u, mx);
+  ix_term(acc, CM(4), ce[4], sQI, 0u, mx);
+  ix_term(acc, CM(5), ce[5], LR, 0u, mx);
+  ix_term(acc, CM(6), ce[6], sPR, 0u, mx);
+  ix_term(acc, CM(7), ce[7], sPI, 1u, mx);
   out[2] = ix::to_dd(acc, ix::acc_base(mx));
   // Pi_I' = Pi_I + N0 (h_PiI,i+1/2 - h_PiI,i-1/2) + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L_I
   //         + N6 s_PhiI + N7 s_PhiR
@@ -268,16 +266,17 @@ __device__ __forceinline__ bool ix_full_point(const IxArgs& x, int i, int j, con
                  imax(imax(ix_texp(ce[4], sQR), ix_texp(ce[5], LI)), imax(ix_texp(ce[6], sPI), ix_texp(ce[7], sPR)))));
   ix::acc_zero(acc);
   ix_term(acc, one, QI, 0u, mx);
-  ix_term(acc, cm[0], ce[0], hQI1, 0u, mx);
-  ix_term(acc, cm[0], ce[0], hQI0, 1u, mx);
-  ix_term(acc, cm[1], ce[1], dPI, 0u, mx);
-  ix_term(acc, cm[2], ce[2], dPR, 1u, mx);
-  ix_term(acc, cm[3], ce[3], sQI, 0u, mx);
-  ix_term(acc, cm[4], ce[4], sQR, 1u, mx);
-  ix_term(acc, cm[5], ce[5], LI, 0u, mx);
-  ix_term(acc, cm[6], ce[6], sPI, 0u, mx);
-  ix_term(acc, cm[7], ce[7], sPR, 0u, mx);
+  ix_term(acc, CM(0), ce[0], hQI1, 0u, mx);
+  ix_term(acc, CM(0), ce[0], hQI0, 1u, mx);
+  ix_term(acc, CM(1), ce[1], dPI, 0u, mx);
+  ix_term(acc, CM(2), ce[2], dPR, 1u, mx);
+  ix_term(acc, CM(3), ce[3], sQI, 0u, mx);
+  ix_term(acc, CM(4), ce[4], sQR, 1u, mx);
+  ix_term(acc, CM(5), ce[5], LI, 0u, mx);
+  ix_term(acc, CM(6), ce[6], sPI, 0u, mx);
+  ix_term(acc, CM(7), ce[7], sPR, 0u, mx);
   out[3] = ix::to_dd(acc, ix::acc_base(mx));
+#undef CM
   for (int c = 0; c < 4; ++c) ix_store_dd(a.u_out + 2 * c * ws + ci, ws, out[c], bad);
   if (slot >= 0 && i == a.i_obs && !bad) {
     double* dst = a.ring + (size_t)slot * 2 * 2 * n_th;

@@ -566,13 +566,29 @@ __host__ __device__ R ix_dot11(const double* a, const double* b, const double* o
   return from_words<R>(w);
 }
 
+// ops 10 / 11 (double-double only): a + b / a - b through the integer engine's sum of two
+// numbers, then rounded to double-double.
+__host__ __device__ R ix_addsub(int op, const double* a, const double* b, int64_t n, int64_t t) {
+  if (W != 2) return r_from<R>(0.0);
+  uint32_t bad = 0;
+  const ix::Num one{{0u, 0u, 0u, 0x40000000u}, -126, 0u};
+  ix::Num c[1] = {one};
+  ix::Num v[1] = {ix::add(ix::from_dd(a[t], a[n + t], bad), ix::from_dd(b[t], b[n + t], bad), op == 11 ? 1u : 0u)};
+  ix::Acc acc;
+  int B;
+  ix::dot<1>(c, v, acc, B);
+  const mw::dd r = ix::to_dd(acc, B);
+  double w[4] = {r.h, r.l, 0.0, 0.0};
+  return from_words<R>(w);
+}
+
 __global__ void mw_eval_kernel(int op, const double* a, const double* b, double* out, double* res, int64_t n,
                                R ln2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0}, wo[4] = {0, 0, 0, 0};
-  if (op == 8 || op == 9) {
-    to_words(op == 8 ? dot11(a, b, out, n, t) : ix_dot11(a, b, out, n, t), wo);
+  if (op >= 8) {
+    to_words(op == 8 ? dot11(a, b, out, n, t) : op == 9 ? ix_dot11(a, b, out, n, t) : ix_addsub(op, a, b, n, t), wo);
     for (int k = 0; k < W; ++k) res[k * n + t] = wo[k];
     return;
   }
@@ -584,12 +600,13 @@ __global__ void mw_eval_kernel(int op, const double* a, const double* b, double*
 
 int mw_eval_impl(int op, int device, const double* a, const double* b, double* out, int64_t n) {
   const R ln2 = r_ln2<R>();
-  if (op == 9 && W != 2) return TEUK_ERR_INVALID_ARG;
-  if (!device && (op == 8 || op == 9)) {
+  if (op >= 9 && W != 2) return TEUK_ERR_INVALID_ARG;
+  if (!device && op >= 8) {
     std::vector<double> res((size_t)W * n);
     for (int64_t t = 0; t < n; ++t) {
       double wo[4];
-      to_words(op == 8 ? dot11(a, b, out, n, t) : ix_dot11(a, b, out, n, t), wo);
+      to_words(op == 8 ? dot11(a, b, out, n, t) : op == 9 ? ix_dot11(a, b, out, n, t) : ix_addsub(op, a, b, n, t),
+               wo);
       for (int k = 0; k < W; ++k) res[k * n + t] = wo[k];
     }
     std::memcpy(out, res.data(), res.size() * sizeof(double));

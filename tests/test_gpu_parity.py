@@ -529,9 +529,11 @@ def test_integer_engine_dot_device_matches_host():
         x[0] = rng.uniform(-2, 2, n) * 2.0 ** rng.integers(-60, 60, n)
         x[1] = x[0] * rng.uniform(-1, 1, n) * 2.0 ** -54
     a[:, ::17] = 0.0
-    h = teuk.mw_eval(9, 2, a, b, out=o, device=False)
-    d = teuk.mw_eval(9, 2, a, b, out=o, device=True)
-    np.testing.assert_array_equal(h, d)
+    b[:, 5::13] = a[:, 5::13]
+    for op in (9, 10, 11):
+        h = teuk.mw_eval(op, 2, a, b, out=o, device=False)
+        d = teuk.mw_eval(op, 2, a, b, out=o, device=True)
+        np.testing.assert_array_equal(h, d, err_msg=f"op {op}")
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))

@@ -202,3 +202,38 @@ def test_integer_engine_dot_host():
         assert abs(r[1, t]) <= np.spacing(abs(r[0, t])) / 2, t
     with pytest.raises(teuk.TeukError):
         teuk.mw_eval(9, 4, np.zeros((4, 3)), np.zeros((4, 3)), device=False)
+
+
+@pytest.mark.parametrize("op", [10, 11])
+def test_integer_engine_sum_host(op):
+    """a + b and a - b through the integer engine (the smaller operand cut at 2^-126 of the
+    larger, then rounded to double-double): within 2^-104 of the exact result plus 2^-125 of
+    the larger operand, exact cancellation gives zero."""
+    mpm.mp.prec = 600
+    rng = np.random.default_rng(3 + op)
+    n = 600
+
+    def rand_dd(e):
+        v = mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** int(e)
+        for k in range(1, 4):
+            v += mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** (int(e) - 53 * k)
+        h = float(v)
+        return h, float(v - h)
+
+    a = np.zeros((2, n)); b = np.zeros((2, n))
+    for t in range(n):
+        ea = int(rng.integers(-60, 60))
+        a[:, t] = rand_dd(ea)
+        b[:, t] = rand_dd(ea + (int(rng.integers(-140, 140)) if t % 3 else 0))
+    b[:, 10] = a[:, 10]; b[:, 11] = -a[:, 11]; a[:, 12] = 0; b[:, 13] = 0
+    r = teuk.mw_eval(op, 2, a, b, device=False)
+
+    def val(x, t):
+        return mpm.mpf(float(x[0, t])) + mpm.mpf(float(x[1, t]))
+
+    for t in range(n):
+        exact = val(a, t) + (val(b, t) if op == 10 else -val(b, t))
+        big = max(abs(val(a, t)), abs(val(b, t)))
+        got = val(r, t)
+        assert abs(got - exact) <= abs(exact) * mpm.mpf(2) ** -104 + big * mpm.mpf(2) ** -125, t
+    assert r[0, 11 if op == 10 else 10] == 0.0
