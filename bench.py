@@ -52,15 +52,16 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
 
 # Integer-engine kernels (double-double): executed thread instructions per grid point for one
 # launch (ncu smsp__inst_executed.sum x smsp__thread_inst_executed_per_inst_executed / points).
-IX_INST = {"half": (5635, "profiles/step_kernels_ix_dd_c2.txt"),
-           "full": (6055, "profiles/step_kernels_ix_dd_c2.txt")}
+IX_INST = {2: {"half": (5635, "profiles/step_kernels_ix_dd_c2.txt"),
+               "full": (6055, "profiles/step_kernels_ix_dd_c2.txt")},
+           4: {}}
 
 
 def kernel_name(dom, W, shape, engine=0):
     """The step kernel a launch shape selects (teuk_launch_shape variants 0..8)."""
     v = shape["variant"]
     if engine == 1:
-        return f"{dom}_ix_kernel<{v % 3}>"
+        return f"{dom}_ix_kernel<{W}, {v % 3}>"
     fam = "" if v < 3 else ("seg_" if v < 6 else "bal_")
     return f"{dom}_{fam}kernel<{W}, {v % 3}>"
 
@@ -82,8 +83,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 4],
                     help="words per real (0: the workload's own precision)")
     ap.add_argument("--engine", type=int, default=-1, choices=[-1, 0, 1],
-                    help="double-double arithmetic: 0 FP64 error-free transforms, 1 integer engine "
-                         "(default -1: the integer engine for double-double)")
+                    help="multi-word arithmetic: 0 FP64 error-free transforms, 1 integer engine "
+                         "(default -1: the integer engine for double-double and quad-double)")
     ap.add_argument("--shape", default="",
                     help="pin the step kernels' launch shape 'threads_theta,rows,variant' "
                          "instead of autotuning (profiling)")
@@ -351,7 +352,7 @@ def roofline_for(res, prob, W, engine, clocks, sms, probe, workload):
     kname = kernel_name(dom, W, res["rows_per_block"], engine)
     tr = TRAFFIC.get((workload, kname))
     if engine == 1:
-        ops_pt, ops_src = IX_INST[dom]
+        ops_pt, ops_src = IX_INST[W].get(dom, (None, "not captured"))
         peak = 128.0 * sms * mhz * 1e6
         peak_source = f"4 warp instructions/SM/cycle x 32 threads x {sms} SMs x {mhz:.0f} MHz (issue limit)"
         op_unit = f"executed thread instructions per point, ncu capture ({ops_src})"
@@ -360,11 +361,11 @@ def roofline_for(res, prob, W, engine, clocks, sms, probe, workload):
         peak = 2.0 * sms * mhz * 1e6
         peak_source = f"2 FP64 ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (SM clock sampled during the timed region)"
         op_unit = "FP64 pipe operations (add, mul, fma count one each)"
-    achieved = ops_pt * pts / (avg * 1e-3)
+    achieved = ops_pt * pts / (avg * 1e-3) if ops_pt else None
     return {
-        "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+        "bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
         "unit": "T inst/s" if engine == 1 else "Tops/s",
-        "frac": achieved / peak, "traffic": tr[0] if tr else None,
+        "frac": achieved / peak if achieved else None, "traffic": tr[0] if tr else None,
         "traffic_source": f"{tr[2]} (launch shape {tr[1]})" if tr else None,
         "kernel": kname, "avg_launch_ms": avg, "launch_shape": res["rows_per_block"],
         "ops_per_point": ops_pt, "peak_source": peak_source, "op_unit": op_unit,
@@ -592,7 +593,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     sampler = start_clock_sampler()
-    engine = (1 if W == 2 else 0) if args.engine < 0 else (args.engine if W == 2 else 0)
+    engine = (1 if W > 1 else 0) if args.engine < 0 else (args.engine if W > 1 else 0)
     res = run_workload(prob, W, args.steps, args.warmup, torch, teuk, flush, shape=args.shape, engine=engine)
     clocks = stop_clock_sampler(*sampler, device_index=local)
     torch.cuda.synchronize()
@@ -611,7 +612,7 @@ def main():
         if not args.no_variants:
             for name, w, nst in (("c1", 1, 20), ("c5", 1, 2), ("c3", 4, 2), ("c5", 2, 1)):
                 p = workloads.CONFIGS[name]
-                r = run_workload(p, w, nst, 1, torch, teuk, flush, with_timing=False, engine=engine if w == 2 else 0)
+                r = run_workload(p, w, nst, 1, torch, teuk, flush, with_timing=False, engine=1 if w > 1 else 0)
                 variants[f"{name}/{DTYPE[w].split(' ')[0]}"] = {
                     "updates_per_s": p.n_r * p.n_theta * p.substeps * nst / (r["ms_total"] * 1e-3),
                     "ms_per_step": r["ms_total"] / nst, "launch": "CUDA graph per outer step"}
@@ -619,15 +620,15 @@ def main():
             variants["c1/f64 batched kernel"] = {"updates_per_s": ups, "ms_per_step": msps,
                                                  "launch": "one cooperative launch, 20 steps"}
             p2 = prob.with_(theta_order=2)
-            r = run_workload(p2, W, 2, 1, torch, teuk, flush, with_timing=False)
+            r = run_workload(p2, W, 2, 1, torch, teuk, flush, with_timing=False, engine=engine)
             variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} 2nd-order theta"] = {
                 "updates_per_s": p2.points * p2.substeps * 2 / (r["ms_total"] * 1e-3),
                 "ms_per_step": r["ms_total"] / 2, "launch": "CUDA graph per outer step"}
             variants["design_a_host_state"] = run_design_a(prob, W, 2 * prob.substeps, torch, teuk, engine)
-            if W == 2:
+            if W > 1:
                 other = 1 - engine
                 r0 = run_workload(prob, W, max(2, args.steps // 2), 2, torch, teuk, flush, engine=other)
-                variants[f"{prob.name}/f64x2 {ENGINE_NAME[other]}"] = {
+                variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} {ENGINE_NAME[other]}"] = {
                     "updates_per_s": r0["points"] * r0["substeps"] * max(2, args.steps // 2) / (r0["ms_total"] * 1e-3),
                     "roofline": roofline_for(r0, prob, W, other, clocks, sms, teuk.fp64_peak(), args.workload)}
         batched = None if args.no_batch else run_c4(torch, teuk, workloads)
@@ -642,7 +643,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[W], "data": "synthetic",
             "config": {"workload": describe_w,
-                       "arithmetic": ENGINE_NAME[engine] if W == 2 else "FP64 error-free transforms",
+                       "arithmetic": ENGINE_NAME[engine] if W > 1 else "FP64",
                        "l2": "256 MiB buffer written between timed steps (outside the timed "
                              "interval); the 100 MB working set is L2-resident within a step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

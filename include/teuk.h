@@ -81,15 +81,15 @@ int teuk_set_initial(teuk_t h, const double* phi_pi);
 int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re, double amp_im,
                            int ell);
 
-/* Arithmetic engine of a double-double handle (the paper's "quadruple" precision, Sec. 3.D):
- * 0 = FP64 error-free transforms (Dot2-style accumulators; the default), 1 = integer engine:
- * every dot product of the step is formed exactly in 128-bit fixed-point mantissas on the
- * integer pipe and rounded once to double-double (error about 2^-105 of the result plus
- * 2^-150 of the largest term; subnormal operands count as zero). GB300 issues far more
- * integer than FP64 operations per cycle. Results of the two engines agree to double-double
- * rounding, not bit for bit. Engine 1 converts the coefficient tables once (about 1.25x their
- * double-double size of extra device memory) and runs the rows-per-block kernels (launch-shape
- * variants 0..2). Quad-double and FP64 handles accept 0 only. */
+/* Arithmetic engine of a double-double or quad-double handle (the paper's "quadruple" and
+ * "octal" precisions, Sec. 3.D): 0 = FP64 error-free transforms (the default), 1 = integer
+ * engine: every dot product of the step is formed exactly in fixed-point mantissas (128-bit
+ * for dd, 256-bit for qd) on the integer pipe and rounded once (error about 2^-105 / 2^-208
+ * of the result plus 2^-150 / 2^-270 of the largest term; subnormal operands count as zero).
+ * GB300 issues far more integer than FP64 operations per cycle. Results of the two engines
+ * agree to the precision's rounding, not bit for bit. Engine 1 converts the coefficient tables
+ * once (about 1.25x their size of extra device memory) and runs the rows-per-block kernels
+ * (launch-shape variants 0..2). FP64 handles accept 0 only. */
 int teuk_set_engine(teuk_t h, int engine);
 int teuk_engine(teuk_t h);
 
@@ -247,7 +247,7 @@ const char* teuk_last_error(teuk_t h);
 /* Multi-word arithmetic self-test: applies op (0 add, 1 sub, 2 mul, 3 div, 4 sqrt, 5 exp,
  * 6 log, 7 dot-accumulate a*b + out, 8 out[t] + sum_{q<11} a[t+q] b[t+q] (indices mod n) through
  * one accumulator, 9 the same sum through the integer engine, 10 / 11 a + b / a - b through
- * the integer engine; 9..11 double-double only)
+ * the integer engine; 9..11 for double-double and quad-double)
  * elementwise to n values of precision w, on the host (device = 0) or the current CUDA
  * device (device = 1). a, b, out: [w][n] host arrays. */
 int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out,

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libteuk.so")
 ROOT = os.path.dirname(HERE)
-HEADERS = ["mw.cuh", "mw_func.cuh", "ix.cuh", "teuk_ix.cuh", "teuk_kernels.cuh", "teuk_internal.h"]
+HEADERS = ["mw.cuh", "mw_func.cuh", "ix.cuh", "ixq.cuh", "teuk_ix.cuh", "teuk_kernels.cuh", "teuk_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 

@@ -377,7 +377,7 @@ int teuk_use_graphs(teuk_t h, int enable) {
 
 int teuk_set_engine(teuk_t h, int engine) {
   if (!h || engine < 0 || engine > 1) return TEUK_ERR_INVALID_ARG;
-  if (engine == 1 && h->W != 2) return invalid(h, "the integer engine is for double-double handles");
+  if (engine == 1 && h->W == 1) return invalid(h, "the integer engine is for double-double and quad-double handles");
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graph(h);
   if (engine == 1) h->kernel_family = 0;

@@ -7,7 +7,7 @@
 #include "ix.cuh"
 #include "teuk_internal.h"
 #include "teuk_kernels.cuh"
-#if TEUK_WORDS == 2
+#if TEUK_WORDS != 1
 #include "teuk_ix.cuh"
 #endif
 
@@ -309,25 +309,26 @@ int engine_impl(teuk_s* h, int engine) {
     h->engine = 0;
     return TEUK_OK;
   }
-#if TEUK_WORDS == 2
+#if TEUK_WORDS != 1
   if (!h->ix_m) {
+    constexpr int U = IxT<W>::kU4;
     const size_t ncn = (size_t)8 * h->n_r * h->pitch, nch = (size_t)8 * (h->n_r - 1) * h->pitch;
     const size_t nw = (size_t)(2 * h->radius + 1) * h->n_th, total = ncn + nch + nw;
-    TEUK_CUDA(h, cudaMalloc(&h->ix_m, total * sizeof(uint4)));
+    TEUK_CUDA(h, cudaMalloc(&h->ix_m, total * U * sizeof(uint4)));
     TEUK_CUDA(h, cudaMalloc(&h->ix_e, total * sizeof(int)));
     const size_t ws = (size_t)h->n_r * h->pitch, hs = (size_t)(h->n_r - 1) * h->pitch;
-    ix_table_kernel<<<(unsigned)((ncn + 255) / 256), 256, 0, h->stream>>>(h->cn, ws, ws, ncn, h->ix_m, h->ix_e);
-    ix_table_kernel<<<(unsigned)((nch + 255) / 256), 256, 0, h->stream>>>(h->ch, hs, hs, nch, h->ix_m + ncn,
-                                                                          h->ix_e + ncn);
-    ix_table_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, h->stream>>>(h->wts, h->n_th, h->n_th, nw,
-                                                                         h->ix_m + ncn + nch, h->ix_e + ncn + nch);
+    ix_table_kernel<W><<<(unsigned)((ncn + 255) / 256), 256, 0, h->stream>>>(h->cn, ws, ws, ncn, h->ix_m, h->ix_e);
+    ix_table_kernel<W><<<(unsigned)((nch + 255) / 256), 256, 0, h->stream>>>(h->ch, hs, hs, nch, h->ix_m + U * ncn,
+                                                                             h->ix_e + ncn);
+    ix_table_kernel<W><<<(unsigned)((nw + 255) / 256), 256, 0, h->stream>>>(
+        h->wts, h->n_th, h->n_th, nw, h->ix_m + U * (ncn + nch), h->ix_e + ncn + nch);
     TEUK_CUDA(h, cudaGetLastError());
     TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   h->engine = 1;
   return TEUK_OK;
 #else
-  h->last_error = "the integer engine is for double-double handles";
+  h->last_error = "the integer engine is for double-double and quad-double handles";
   return TEUK_ERR_INVALID_ARG;
 #endif
 }
@@ -379,22 +380,23 @@ int prepare_impl(teuk_s* h) {
 template <int V>
 int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
   const int nh = h->n_r - 1, nf = h->n_r - 2;
-#if TEUK_WORDS == 2
+#if TEUK_WORDS != 1
   if (h->engine == 1) {
     // integer engine: the row family's block shape, shared rows in the engine's format
+    constexpr int U = IxT<W>::kU4;
     const size_t ncn = (size_t)8 * h->n_r * h->pitch, nch = (size_t)8 * (h->n_r - 1) * h->pitch;
-    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + ncn, h->ix_e + ncn, h->ix_m + ncn + nch, h->ix_e + ncn + nch};
-    const size_t ism = (size_t)blk.y * 2 * (h->n_th + 2 * h->radius) * (sizeof(uint4) + sizeof(int));
+    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, h->ix_m + U * (ncn + nch), h->ix_e + ncn + nch};
+    const size_t ism = (size_t)blk.y * 2 * (h->n_th + 2 * h->radius) * (U * sizeof(uint4) + sizeof(int));
     if (ism > 48 * 1024) {
-      TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
-      TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+      TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+      TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
     }
     cudaEvent_t ev = nullptr;
     time_begin(h, &ev);
-    half_ix_kernel<V><<<(nh + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+    half_ix_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
     time_end(h, 0, ev);
     time_begin(h, &ev);
-    full_ix_kernel<V><<<(nf + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+    full_ix_kernel<W, V><<<(nf + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
     time_end(h, 1, ev);
     h->launches += 2;
     TEUK_CUDA(h, cudaGetLastError());
@@ -544,43 +546,47 @@ __host__ __device__ R dot11(const double* a, const double* b, const double* out,
   return acc.get();
 }
 
-// op 9 (double-double only): the same sum through the integer engine (ix.cuh): the 11
-// products and the initial value as terms of one exact dot product, rounded once.
+// op 9 (double-double and quad-double): the same sum through the integer engine (ix.cuh,
+// ixq.cuh): the 11 products and the initial value as terms of one exact dot product, rounded
+// once. ops 10 / 11: a + b / a - b through the engine's sum of two numbers, then rounded.
+#if TEUK_WORDS != 1
 __host__ __device__ R ix_dot11(const double* a, const double* b, const double* out, int64_t n, int64_t t) {
-  if (W != 2) return r_from<R>(0.0);
+  using T = IxT<W>;
   uint32_t bad = 0;
-  ix::Num c[12], v[12];
-  const ix::Num one{{0u, 0u, 0u, 0x40000000u}, -126, 0u};
-  c[0] = one;
-  v[0] = ix::from_dd(out[t], out[n + t], bad);
+  typename T::Num c[12], v[12];
+  c[0] = ix_pow2<W>(0);
+  v[0] = T::load(out + t, n, bad);
   for (int q = 0; q < 11; ++q) {
     const int64_t u = (t + q) % n;
-    c[q + 1] = ix::from_dd(a[u], a[n + u], bad);
-    v[q + 1] = ix::from_dd(b[u], b[n + u], bad);
+    c[q + 1] = T::load(a + u, n, bad);
+    v[q + 1] = T::load(b + u, n, bad);
   }
-  ix::Acc acc;
-  int B;
-  ix::dot<12>(c, v, acc, B);
-  const mw::dd r = ix::to_dd(acc, B);
-  double w[4] = {r.h, r.l, 0.0, 0.0};
+  int mx = 2 * ix::kZeroE;
+  for (int q = 0; q < 12; ++q) mx = imax(mx, T::pexp(c[q].e, v[q].e));
+  typename T::Acc acc;
+  T::zero(acc);
+  for (int q = 0; q < 12; ++q) T::prod(acc, c[q].m, v[q].m, c[q].neg ^ v[q].neg, T::pexp(c[q].e, v[q].e), mx);
+  double w[4] = {0, 0, 0, 0};
+  T::to_words(acc, T::base(mx), w);
   return from_words<R>(w);
 }
-
-// ops 10 / 11 (double-double only): a + b / a - b through the integer engine's sum of two
-// numbers, then rounded to double-double.
 __host__ __device__ R ix_addsub(int op, const double* a, const double* b, int64_t n, int64_t t) {
-  if (W != 2) return r_from<R>(0.0);
+  using T = IxT<W>;
   uint32_t bad = 0;
-  const ix::Num one{{0u, 0u, 0u, 0x40000000u}, -126, 0u};
-  ix::Num c[1] = {one};
-  ix::Num v[1] = {ix::add(ix::from_dd(a[t], a[n + t], bad), ix::from_dd(b[t], b[n + t], bad), op == 11 ? 1u : 0u)};
-  ix::Acc acc;
-  int B;
-  ix::dot<1>(c, v, acc, B);
-  const mw::dd r = ix::to_dd(acc, B);
-  double w[4] = {r.h, r.l, 0.0, 0.0};
+  const typename T::Num one = ix_pow2<W>(0);
+  const typename T::Num v = T::add(T::load(a + t, n, bad), T::load(b + t, n, bad), op == 11 ? 1u : 0u);
+  const int mx = T::pexp(one.e, v.e);
+  typename T::Acc acc;
+  T::zero(acc);
+  T::prod(acc, one.m, v.m, v.neg, mx, mx);
+  double w[4] = {0, 0, 0, 0};
+  T::to_words(acc, T::base(mx), w);
   return from_words<R>(w);
 }
+#else
+__host__ __device__ R ix_dot11(const double*, const double*, const double*, int64_t, int64_t) { return 0.0; }
+__host__ __device__ R ix_addsub(int, const double*, const double*, int64_t, int64_t) { return 0.0; }
+#endif
 
 __global__ void mw_eval_kernel(int op, const double* a, const double* b, double* out, double* res, int64_t n,
                                R ln2) {
@@ -600,7 +606,7 @@ __global__ void mw_eval_kernel(int op, const double* a, const double* b, double*
 
 int mw_eval_impl(int op, int device, const double* a, const double* b, double* out, int64_t n) {
   const R ln2 = r_ln2<R>();
-  if (op >= 9 && W != 2) return TEUK_ERR_INVALID_ARG;
+  if (op >= 9 && W == 1) return TEUK_ERR_INVALID_ARG;
   if (!device && op >= 8) {
     std::vector<double> res((size_t)W * n);
     for (int64_t t = 0; t < n; ++t) {

@@ -221,7 +221,7 @@ class Teuk:
         return out
 
     def set_engine(self, engine):
-        """Double-double arithmetic engine: 0 FP64 error-free transforms, 1 integer engine."""
+        """Multi-word arithmetic engine: 0 FP64 error-free transforms, 1 integer engine (dd, qd)."""
         _check(lib().teuk_set_engine(self._h, int(engine)), self._h)
 
     @property

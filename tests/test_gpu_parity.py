@@ -521,27 +521,31 @@ def test_dissipation_parity(oracle_mod, W):
         g1.set_dissipation(-1.0)
 
 
-def test_integer_engine_dot_device_matches_host():
-    rng = np.random.default_rng(21)
+@pytest.mark.parametrize("W", [2, 4])
+def test_integer_engine_ops_device_matches_host(W):
+    rng = np.random.default_rng(21 + W)
     n = 2048
-    a = np.zeros((2, n)); b = np.zeros((2, n)); o = np.zeros((2, n))
+    a = np.zeros((W, n)); b = np.zeros((W, n)); o = np.zeros((W, n))
     for x in (a, b, o):
         x[0] = rng.uniform(-2, 2, n) * 2.0 ** rng.integers(-60, 60, n)
-        x[1] = x[0] * rng.uniform(-1, 1, n) * 2.0 ** -54
+        for k in range(1, W):
+            x[k] = x[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -54
     a[:, ::17] = 0.0
     b[:, 5::13] = a[:, 5::13]
     for op in (9, 10, 11):
-        h = teuk.mw_eval(op, 2, a, b, out=o, device=False)
-        d = teuk.mw_eval(op, 2, a, b, out=o, device=True)
+        h = teuk.mw_eval(op, W, a, b, out=o, device=False)
+        d = teuk.mw_eval(op, W, a, b, out=o, device=True)
         np.testing.assert_array_equal(h, d, err_msg=f"op {op}")
 
 
+@pytest.mark.parametrize("W", [2, 4])
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_integer_engine_evolution_parity(oracle_mod, case):
-    """Double-double through the integer engine (every dot product exact on the integer pipe,
-    rounded once) against the 256-bit oracle, the same cases as the FP64-transform engine."""
+def test_integer_engine_evolution_parity(oracle_mod, W, case):
+    """Double-double and quad-double through the integer engine (every dot product exact on the
+    integer pipe, rounded once) against the 256-bit oracle, the same cases as the FP64-transform
+    engine."""
     p = small(**CASES[case])
-    g, o = make_pair(oracle_mod, p, 2)
+    g, o = make_pair(oracle_mod, p, W)
     g.set_engine(1)
     assert g.engine == 1
     ell = max(abs(p["m"]), abs(p["s"]))
@@ -552,21 +556,21 @@ def test_integer_engine_evolution_parity(oracle_mod, case):
     o.step(3 * p["substeps"])
     err, umax = o.max_rel_err(g.get_state())
     assert umax > 0.05
-    assert err < TOL[2], err
+    assert err < TOL[W], err
 
 
-def test_integer_engine_full_size_window(oracle_mod):
-    """c2 at full size on the integer engine, in the benchmark's launch configuration, against a
-    256-bit oracle window around the pulse after 12 iterations."""
-    prob = workloads.CONFIGS["c2"]
+@pytest.mark.parametrize("W,name,nsub", [(2, "c2", 12), (4, "c3", 8)])
+def test_integer_engine_full_size_window(oracle_mod, W, name, nsub):
+    """Full-size workloads on the integer engine, in the benchmark's launch configuration (tuned),
+    against a 256-bit oracle window around the pulse (domain of dependence)."""
+    prob = workloads.CONFIGS[name]
     p = dict(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min, rstar_max=prob.rstar_max,
              n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0, substeps=prob.substeps, theta_order=10, parity=0)
-    g = teuk.Teuk(precision=2, **p)
+    g = teuk.Teuk(precision=W, **p)
     g.set_engine(1)
     g.tune()
     ar, ai = prob.amps
     g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
-    nsub = 12
     g.substep(nsub)
     g.sync()
     full = g.get_state()
@@ -579,17 +583,18 @@ def test_integer_engine_full_size_window(oracle_mod):
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     o.step(nsub)
     err, umax = o.max_rel_err(np.ascontiguousarray(full[:, :, wlo:whi + 1]), lo - wlo, hi - wlo)
-    assert umax > 0 and err < TOL[2], err
+    assert umax > 0 and err < TOL[W], err
 
 
+@pytest.mark.parametrize("W", [2, 4])
 @pytest.mark.parametrize("n_theta", [24, 70])
-def test_integer_engine_launch_shapes_and_graphs_bitwise(n_theta):
+def test_integer_engine_launch_shapes_and_graphs_bitwise(W, n_theta):
     """Within the integer engine every launch shape and register budget, and graph replay,
     give the same bits (integer arithmetic per point does not depend on the launch)."""
     p = small(n_r=37, n_theta=n_theta)
     ref = None
     for tx, ty, v, graphs in [(32, 1, 0, True), (64, 2, 1, False), (32, 4, 2, True), (128, 1, 1, True)]:
-        g = teuk.Teuk(precision=2, **p)
+        g = teuk.Teuk(precision=W, **p)
         g.set_engine(1)
         g.set_launch_shape(tx, ty, v)
         g.use_graphs(graphs)
@@ -606,9 +611,10 @@ def test_integer_engine_launch_shapes_and_graphs_bitwise(n_theta):
         g.close()
 
 
-def test_integer_engine_reports_nonfinite_and_rejects_other_precisions():
+@pytest.mark.parametrize("W", [2, 4])
+def test_integer_engine_reports_nonfinite_and_rejects_fp64(W):
     p = small()
-    g = teuk.Teuk(precision=2, **p)
+    g = teuk.Teuk(precision=W, **p)
     g.set_engine(1)
     g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
     st = g.get_state()
@@ -618,8 +624,7 @@ def test_integer_engine_reports_nonfinite_and_rejects_other_precisions():
     with pytest.raises(teuk.TeukError) as e:
         g.sync()
     assert e.value.code == teuk.ERR_NONFINITE
-    for W in (1, 4):
-        h = teuk.Teuk(precision=W, **p)
-        with pytest.raises(teuk.TeukError):
-            h.set_engine(1)
-        assert h.engine == 0
+    h = teuk.Teuk(precision=1, **p)
+    with pytest.raises(teuk.TeukError):
+        h.set_engine(1)
+    assert h.engine == 0

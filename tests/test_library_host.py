@@ -162,78 +162,75 @@ def test_dot11_accumulator_with_cancellation_host(words):
     assert worst < BOUND[words], worst
 
 
-def test_integer_engine_dot_host():
-    """The integer engine's dot product (op 9: out + 11 products, double-double operands of
-    exponents spread over +-200 binades, zeros, repeated terms) against mpmath: the error
-    stays within 2^-104 of the exact result plus 2^-150 of the largest term, and the result
-    is a normalised double-double."""
-    mpm.mp.prec = 600
-    rng = np.random.default_rng(11)
-    n = 200
+ENGINE_BOUNDS = {2: (-104, -150, -125), 4: (-208, -270, -253)}  # result, largest term, larger operand
 
-    def rand_dd(e):
-        v = mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** int(e)
-        for k in range(1, 4):
-            v += mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** (int(e) - 53 * k)
-        h = float(v)
-        return h, float(v - h)
 
-    a = np.zeros((2, n)); b = np.zeros((2, n)); o = np.zeros((2, n))
+def _rand_expansion(rng, words, e):
+    v = mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** int(e)
+    for k in range(1, words + 2):
+        v += mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** (int(e) - 53 * k)
+    out = []
+    for _ in range(words):
+        out.append(float(v))
+        v -= mpm.mpf(out[-1])
+    return out
+
+
+def _val(x, t):
+    return mpm.fsum(mpm.mpf(float(x[k, t])) for k in range(x.shape[0]))
+
+
+@pytest.mark.parametrize("words", [2, 4])
+def test_integer_engine_dot_host(words):
+    """The integer engine's dot product (op 9: out + 11 products, operands with exponents spread
+    over +-200 binades, zeros, repeated terms that cancel) against mpmath: the error stays within
+    2^-104 (dd) / 2^-208 (qd) of the exact result plus 2^-150 / 2^-270 of the largest term."""
+    mpm.mp.prec = 900
+    rng = np.random.default_rng(11 + words)
+    n = 160
+    a = np.zeros((words, n)); b = np.zeros((words, n)); o = np.zeros((words, n))
     for t in range(n):
-        a[:, t] = rand_dd(rng.integers(-200, 200))
-        b[:, t] = rand_dd(rng.integers(-200, 200))
-        o[:, t] = rand_dd(rng.integers(-400, 400))
+        a[:, t] = _rand_expansion(rng, words, rng.integers(-200, 200))
+        b[:, t] = _rand_expansion(rng, words, rng.integers(-200, 200))
+        o[:, t] = _rand_expansion(rng, words, rng.integers(-400, 400))
     a[:, 5] = 0; b[:, 7] = 0; o[:, 9] = 0; a[:, 40:60] = 0; o[:, 45] = 0
     a[:, 100:111] = a[:, 100:101]; b[:, 100:111] = -b[:, 100:101]
-    r = teuk.mw_eval(9, 2, a, b, out=o, device=False)
-
-    def val(x, t):
-        return mpm.mpf(float(x[0, t])) + mpm.mpf(float(x[1, t]))
-
+    r = teuk.mw_eval(9, words, a, b, out=o, device=False)
+    er, eb, _ = ENGINE_BOUNDS[words]
     for t in range(n):
-        terms = [val(a, (t + q) % n) * val(b, (t + q) % n) for q in range(11)] + [val(o, t)]
+        terms = [_val(a, (t + q) % n) * _val(b, (t + q) % n) for q in range(11)] + [_val(o, t)]
         exact = mpm.fsum(terms)
         big = max(abs(x) for x in terms)
-        got = val(r, t)
+        got = _val(r, t)
         if big == 0:
             assert got == 0
             continue
-        assert abs(got - exact) <= abs(exact) * mpm.mpf(2) ** -104 + big * mpm.mpf(2) ** -150, t
+        assert abs(got - exact) <= abs(exact) * mpm.mpf(2) ** er + big * mpm.mpf(2) ** eb, t
         assert abs(r[1, t]) <= np.spacing(abs(r[0, t])) / 2, t
     with pytest.raises(teuk.TeukError):
-        teuk.mw_eval(9, 4, np.zeros((4, 3)), np.zeros((4, 3)), device=False)
+        teuk.mw_eval(9, 1, np.zeros((1, 3)), np.zeros((1, 3)), device=False)
 
 
+@pytest.mark.parametrize("words", [2, 4])
 @pytest.mark.parametrize("op", [10, 11])
-def test_integer_engine_sum_host(op):
-    """a + b and a - b through the integer engine (the smaller operand cut at 2^-126 of the
-    larger, then rounded to double-double): within 2^-104 of the exact result plus 2^-125 of
-    the larger operand, exact cancellation gives zero."""
-    mpm.mp.prec = 600
-    rng = np.random.default_rng(3 + op)
-    n = 600
-
-    def rand_dd(e):
-        v = mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** int(e)
-        for k in range(1, 4):
-            v += mpm.mpf(rng.uniform(-1, 1)) * mpm.mpf(2) ** (int(e) - 53 * k)
-        h = float(v)
-        return h, float(v - h)
-
-    a = np.zeros((2, n)); b = np.zeros((2, n))
+def test_integer_engine_sum_host(op, words):
+    """a + b and a - b through the integer engine (the smaller operand cut below the larger's
+    last mantissa bit, then rounded): within 2^-104 / 2^-208 of the exact result plus
+    2^-125 / 2^-253 of the larger operand; exact cancellation gives zero."""
+    mpm.mp.prec = 900
+    rng = np.random.default_rng(3 + op + words)
+    n = 300
+    a = np.zeros((words, n)); b = np.zeros((words, n))
     for t in range(n):
         ea = int(rng.integers(-60, 60))
-        a[:, t] = rand_dd(ea)
-        b[:, t] = rand_dd(ea + (int(rng.integers(-140, 140)) if t % 3 else 0))
+        a[:, t] = _rand_expansion(rng, words, ea)
+        b[:, t] = _rand_expansion(rng, words, ea + (int(rng.integers(-280, 280)) if t % 3 else 0))
     b[:, 10] = a[:, 10]; b[:, 11] = -a[:, 11]; a[:, 12] = 0; b[:, 13] = 0
-    r = teuk.mw_eval(op, 2, a, b, device=False)
-
-    def val(x, t):
-        return mpm.mpf(float(x[0, t])) + mpm.mpf(float(x[1, t]))
-
+    r = teuk.mw_eval(op, words, a, b, device=False)
+    er, _, eo = ENGINE_BOUNDS[words]
     for t in range(n):
-        exact = val(a, t) + (val(b, t) if op == 10 else -val(b, t))
-        big = max(abs(val(a, t)), abs(val(b, t)))
-        got = val(r, t)
-        assert abs(got - exact) <= abs(exact) * mpm.mpf(2) ** -104 + big * mpm.mpf(2) ** -125, t
+        exact = _val(a, t) + (_val(b, t) if op == 10 else -_val(b, t))
+        big = max(abs(_val(a, t)), abs(_val(b, t)))
+        got = _val(r, t)
+        assert abs(got - exact) <= abs(exact) * mpm.mpf(2) ** er + big * mpm.mpf(2) ** eo, t
     assert r[0, 11 if op == 10 else 10] == 0.0
