@@ -67,7 +67,7 @@ def velocity_data(p: workloads.Problem, words: int) -> np.ndarray:
 
 def run(p: workloads.Problem = workloads.TAILS, precision: int | None = None, ell_max: int = 8,
         steps: int | None = None, chunk: int = 500, tune: bool = True, log=None,
-        data: str = "pulse") -> dict:
+        data: str = "pulse", engine: int = 0) -> dict:
     """Evolves p for `steps` outer steps (default p.steps) recording Phi at p.rstar_obs every
     step, then projects the record onto sY_lm, l = max(|m|, |s|) .. ell_max, on the device.
     data: "pulse" (the workloads' time-symmetric Gaussian) or "velocity" (velocity_data)."""
@@ -76,6 +76,8 @@ def run(p: workloads.Problem = workloads.TAILS, precision: int | None = None, el
     lo = max(abs(p.m), abs(p.s))
     g = teuk.Teuk.from_problem(p, precision=W)
     try:
+        if engine:
+            g.set_engine(engine)
         ar, ai = p.amps
         if data == "velocity":
             g.set_initial(velocity_data(p, W))
@@ -154,6 +156,8 @@ def main(argv=None) -> int:
                     help="divide dr* (and dt = 0.25 dr*) by this factor, same domain and end time")
     ap.add_argument("--substeps", type=int, default=0,
                     help="Lax-Wendroff iterations per outer step (default: the workload's)")
+    ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
+                    help="multi-word arithmetic: 0 FP64 error-free transforms, 1 integer engine")
     ap.add_argument("--out", default="")
     args = ap.parse_args(argv)
     p = workloads.TAILS
@@ -162,7 +166,7 @@ def main(argv=None) -> int:
     if args.substeps:
         p = p.with_(substeps=args.substeps)
     res = run(p, precision=args.precision or None, ell_max=args.ell_max, steps=args.steps or None,
-              log=lambda s: print(s, flush=True), data=args.data)
+              log=lambda s: print(s, flush=True), data=args.data, engine=args.engine)
     summ = summarize(res)
     l0 = p.ell
     print(f"tails: {p.name} ({args.data} data, dr*={p.dr:g}, k={p.substeps}), words={res['words']}, "
@@ -175,7 +179,8 @@ def main(argv=None) -> int:
         print(f"  l={ell} (l+l'+3 = {ell + l0 + 3}): fit n={fn if fn is None else round(fn, 3)}  {cells}")
     if args.out:
         stride = max(1, len(res["t"]) // 3000)
-        doc = {"workload": p.name, "data": args.data, "dr": p.dr, "substeps": p.substeps, "n_r": p.n_r,
+        doc = {"workload": p.name, "data": args.data, "engine": args.engine, "dr": p.dr, "substeps": p.substeps,
+               "n_r": p.n_r,
                "words": res["words"], "updates_per_s": res["updates_per_s"],
                "wall_s": res["wall_s"], "launch_shape": res["launch_shape"],
                "rstar_obs_used": res["rstar_obs_used"],
