@@ -223,6 +223,9 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   const Num uQI0 = T::load(u + 3 * W * ws + i0, ws, bad), uQI1 = T::load(u + 3 * W * ws + i1, ws, bad);
   const Num dPR = T::add(uPR1, uPR0, 1u), dPI = T::add(uPI1, uPI0, 1u);
   const Num sQR = T::add(uQR1, uQR0, 0u), sQI = T::add(uQI1, uQI0, 0u);
+  // one exact difference and one product are cheaper here than two products, and free the
+  // four Pi values early
+  const Num dQR = T::add(uQR1, uQR0, 1u), dQI = T::add(uQI1, uQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
   const Num LR = ix_theta<W>(x, sR, gstride, j), LI = ix_theta<W>(x, sI, gstride, j);
   const size_t ci = (size_t)h * pitch + j;
@@ -249,17 +252,17 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   ix_nterm<W>(acc, h4, sQI, 0u, mx);
   ix_store<W>(a.uh + 1 * W * hs + ci, hs, acc, T::base(mx), bad, w);
   // Pi_R = H3 s_PiR + H4 s_PiI + H0 (Pi_R,h+1 - Pi_R,h) + H1 d_PhiR + H2 d_PhiI + H5 L_R + H6 s_PhiR - H7 s_PhiI
-  mx = imax(imax(imax(TE(3, sQR), TE(4, sQI)), imax(TE(0, uQR1), TE(0, uQR0))),
+  mx = imax(imax(imax(TE(3, sQR), TE(4, sQI)), TE(0, dQR)),
             imax(imax(TE(1, dPR), TE(2, dPI)), imax(TE(5, LR), imax(TE(6, sPR), TE(7, sPI)))));
   T::zero(acc);
-  TT(3, sQR, 0u); TT(4, sQI, 0u); TT(0, uQR1, 0u); TT(0, uQR0, 1u); TT(1, dPR, 0u);
+  TT(3, sQR, 0u); TT(4, sQI, 0u); TT(0, dQR, 0u); TT(1, dPR, 0u);
   TT(2, dPI, 0u); TT(5, LR, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
   ix_store<W>(a.uh + 2 * W * hs + ci, hs, acc, T::base(mx), bad, w);
   // Pi_I = H3 s_PiI - H4 s_PiR + H0 (Pi_I,h+1 - Pi_I,h) + H1 d_PhiI - H2 d_PhiR + H5 L_I + H6 s_PhiI + H7 s_PhiR
-  mx = imax(imax(imax(TE(3, sQI), TE(4, sQR)), imax(TE(0, uQI1), TE(0, uQI0))),
+  mx = imax(imax(imax(TE(3, sQI), TE(4, sQR)), TE(0, dQI)),
             imax(imax(TE(1, dPI), TE(2, dPR)), imax(TE(5, LI), imax(TE(6, sPI), TE(7, sPR)))));
   T::zero(acc);
-  TT(3, sQI, 0u); TT(4, sQR, 1u); TT(0, uQI1, 0u); TT(0, uQI0, 1u); TT(1, dPI, 0u);
+  TT(3, sQI, 0u); TT(4, sQR, 1u); TT(0, dQI, 0u); TT(1, dPI, 0u);
   TT(2, dPR, 1u); TT(5, LI, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
   ix_store<W>(a.uh + 3 * W * hs + ci, hs, acc, T::base(mx), bad, w);
 #undef TT
@@ -299,6 +302,7 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   const Num hQI1 = T::load(uh + 3 * W * hs + p, hs, bad), hQI0 = T::load(uh + 3 * W * hs + m, hs, bad);
   const Num dPR = T::add(hPR1, hPR0, 1u), dPI = T::add(hPI1, hPI0, 1u);
   const Num sQR = T::add(hQR1, hQR0, 0u), sQI = T::add(hQI1, hQI0, 0u);
+  const Num dQR = T::add(hQR1, hQR0, 1u), dQI = T::add(hQI1, hQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
   const Num LR = ix_theta<W>(x, sR, gstride, j), LI = ix_theta<W>(x, sI, gstride, j);
   const size_t ci = (size_t)i * pitch + j;
@@ -328,21 +332,21 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   ix_store<W>(a.u_out + 1 * W * ws + ci, ws, acc, T::base(mx), bad, o1);
   // Pi_R' = Pi_R + N0 (h_PiR,i+1/2 - h_PiR,i-1/2) + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L_R
   //         + N6 s_PhiR - N7 s_PhiI
-  mx = imax(imax(imax(T::pexp(one.e, QR.e), TE(0, hQR1)), imax(TE(0, hQR0), TE(1, dPR))),
+  mx = imax(imax(T::pexp(one.e, QR.e), imax(TE(0, dQR), TE(1, dPR))),
             imax(imax(TE(2, dPI), TE(3, sQR)), imax(imax(TE(4, sQI), TE(5, LR)), imax(TE(6, sPR), TE(7, sPI)))));
   T::zero(acc);
   ix_nterm<W>(acc, one, QR, 0u, mx);
-  TT(0, hQR1, 0u); TT(0, hQR0, 1u); TT(1, dPR, 0u); TT(2, dPI, 0u); TT(3, sQR, 0u);
+  TT(0, dQR, 0u); TT(1, dPR, 0u); TT(2, dPI, 0u); TT(3, sQR, 0u);
   TT(4, sQI, 0u); TT(5, LR, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
   ix_store<W>(a.u_out + 2 * W * ws + ci, ws, acc, T::base(mx), bad, w);
   const bool bad2 = nonfinite(w[0]);
   // Pi_I' = Pi_I + N0 (h_PiI,i+1/2 - h_PiI,i-1/2) + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L_I
   //         + N6 s_PhiI + N7 s_PhiR
-  mx = imax(imax(imax(T::pexp(one.e, QI.e), TE(0, hQI1)), imax(TE(0, hQI0), TE(1, dPI))),
+  mx = imax(imax(T::pexp(one.e, QI.e), imax(TE(0, dQI), TE(1, dPI))),
             imax(imax(TE(2, dPR), TE(3, sQI)), imax(imax(TE(4, sQR), TE(5, LI)), imax(TE(6, sPI), TE(7, sPR)))));
   T::zero(acc);
   ix_nterm<W>(acc, one, QI, 0u, mx);
-  TT(0, hQI1, 0u); TT(0, hQI0, 1u); TT(1, dPI, 0u); TT(2, dPR, 1u); TT(3, sQI, 0u);
+  TT(0, dQI, 0u); TT(1, dPI, 0u); TT(2, dPR, 1u); TT(3, sQI, 0u);
   TT(4, sQR, 1u); TT(5, LI, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
   ix_store<W>(a.u_out + 3 * W * ws + ci, ws, acc, T::base(mx), bad, w);
 #undef TT
