@@ -55,7 +55,7 @@ int invalid(teuk_s* h, const char* msg) {
 void drop_graph(teuk_s* h);
 
 void free_all(teuk_s* h) {
-  double** bufs[] = {&h->u, &h->uh, &h->cn_raw, &h->ch_raw, &h->cn, &h->ch, &h->wts, &h->sin_th,
+  double** bufs[] = {&h->u, &h->uh, &h->cn_raw, &h->ch_raw, &h->cn, &h->ch, &h->wts, &h->lfac, &h->sin_th,
                      &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring, &h->u_ko};
   for (double** b : bufs) {
     if (*b) cudaFree(*b);
@@ -270,6 +270,7 @@ int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
       {&h->u, 4 * W * nr * P},      {&h->uh, 4 * W * nh * P},     {&h->cn_raw, 8 * W * nr * P},
       {&h->ch_raw, 8 * W * nh * P}, {&h->cn, 8 * W * nr * P},     {&h->ch, 8 * W * nh * P},
       {&h->wts, (size_t)(2 * h->radius + 1) * W * h->n_th},     {&h->sin_th, (size_t)W * h->n_th},
+      {&h->lfac, (size_t)2 * W * h->n_th},
       {&h->cos_th, (size_t)W * h->n_th}, {&h->x_node, W * nr},  {&h->x_half, W * nh},
       {&h->rs_node, W * nr},        {&h->prof, (size_t)W * h->n_th}};
   for (auto& al : allocs) {

@@ -37,6 +37,7 @@ struct teuk_s {
   double* ch = nullptr;      // folded half tables
   double* wts = nullptr;     // [2*radius+1][W][n_th]
   double* sin_th = nullptr;  // [W][n_th]
+  double* lfac = nullptr;    // [2][W][n_th]: the theta operator's factors A2 and A1 cot(theta_j)
   double* cos_th = nullptr;  // [W][n_th]
   double* x_node = nullptr;  // [W][n_r]
   double* x_half = nullptr;  // [W][n_r-1]

@@ -2,9 +2,17 @@
 // same two kernels per Lax-Wendroff iteration as teuk_kernels.cuh (Eqs. lw1, lw2 with the
 // folded coefficient tables and the 10th/2nd-order theta stencil, Sec. 3.B-3.D), with every
 // dot product formed exactly on the integer pipe and rounded once to the handle's precision.
-// The state and the half-step rows stay multi-word doubles in HBM; the coefficient tables and
-// stencil weights are kept in the engine's format: the mantissa as 1 (dd) or 2 (qd) uint4 per
-// value in planes of their own, the exponent and sign as one int (e * 2 + neg).
+// The state and the half-step rows stay multi-word doubles in HBM; the coefficient tables are
+// kept in the engine's format: the mantissa as 1 (dd) or 2 (qd) uint4 per value in planes of
+// their own, the exponent and sign as one int (e * 2 + neg).
+//
+// The theta operator is evaluated in its factored form L = A2 D2 + (A1 cot theta) D1 with the
+// integer stencils D2 = sum_q d2_q s_{j+q}, D1 = sum_q d1_q s_{j+q} (the weights of the
+// 11-point stencil are A2 d2_q + A1 d1_q cot theta_j, d2 and d1 integers): each shared theta
+// row is held in block-floating form (one exponent per row, every value a K-limb two's
+// complement integer aligned to the row's largest), so D2 and D1 are exact integer
+// multiply-adds, and the factors H5 A2, H5 A1 cot theta (N5 ... in the full step) are folded
+// into the coefficient tables at set-up.
 #pragma once
 
 #include "ix.cuh"
@@ -22,6 +30,8 @@ template <> struct IxT<2> {
   using Num = ix::Num;
   using Acc = ix::Acc;
   static constexpr int kLimbs = 4, kU4 = 1, kTop = 126;  // leading bit of a converted value
+  static constexpr int kBlk = 6;                          // limbs of a block-floating row value
+  static IXHD void shift_in(Acc& acc, const uint32_t* p, uint32_t neg, int r) { ix::acc_add(acc, p, neg, r); }
   static IXHD Num load(const double* p, size_t ws, uint32_t& bad) { return ix::from_dd(p[0], p[ws], bad); }
   static IXHD Num add(const Num& a, const Num& b, uint32_t nb) { return ix::add(a, b, nb); }
   static IXHD int pexp(int ec, int ev) { return ix::prod_exp(ec, ev); }
@@ -42,6 +52,8 @@ template <> struct IxT<4> {
   using Num = ix::Num8;
   using Acc = ix::Acc10;
   static constexpr int kLimbs = 8, kU4 = 2, kTop = 254;
+  static constexpr int kBlk = 10;
+  static IXHD void shift_in(Acc& acc, const uint32_t* p, uint32_t neg, int r) { ix::acc_add10(acc, p, neg, r); }
   static IXHD Num load(const double* p, size_t ws, uint32_t& bad) {
     return ix::from_qd(p[0], p[ws], p[2 * ws], p[3 * ws], bad);
   }
@@ -70,14 +82,17 @@ IXHD typename IxT<W>::Num ix_pow2(int k) {
   return r;
 }
 
+// Planes of the engine's coefficient tables: the eight folded coefficients of the step, with
+// plane 5 (H5 / N5, the factor of the theta operator) replaced by H5 A2 and plane 8 holding
+// H5 A1 cot theta_j.
+constexpr int kIxPlanes = 9;
+
 struct IxArgs {
   StepArgs a;           // geometry, state, half-step rows, ring, status
-  const uint4* cnm;     // folded node coefficients [8][kU4][n_r][pitch]: mantissas
-  const int* cne;       //   exponent-sign words [8][n_r][pitch]
-  const uint4* chm;     // folded half-node coefficients [8][kU4][n_r - 1][pitch]
+  const uint4* cnm;     // node coefficients [kIxPlanes][kU4][n_r][pitch]: mantissas
+  const int* cne;       //   exponent-sign words [kIxPlanes][n_r][pitch]
+  const uint4* chm;     // half-node coefficients [kIxPlanes][kU4][n_r - 1][pitch]
   const int* che;
-  const uint4* wm;      // theta weights [2 radius + 1][kU4][n_th]
-  const int* we;
 };
 
 template <class N>
@@ -108,11 +123,151 @@ __global__ void ix_table_kernel(const double* src, size_t ws, size_t per_plane, 
   de[k] = ix_en(x);
 }
 
-// Ghosted shared row of one component: mantissas [kU4][gstride] (uint4), exponent-sign
-// words [gstride] (int).
+// Exact product x y of two engine values, cut to the engine's mantissa.
+template <int W>
+IXHD typename IxT<W>::Num ix_mul(const typename IxT<W>::Num& x, const typename IxT<W>::Num& y) {
+  typename IxT<W>::Acc acc;
+  IxT<W>::zero(acc);
+  const int ep = IxT<W>::pexp(x.e, y.e);
+  IxT<W>::prod(acc, x.m, y.m, x.neg ^ y.neg, ep, ep);
+  return IxT<W>::to_num(acc, IxT<W>::base(ep));
+}
+
+// Folds the theta operator's factors into plane 5 of a converted table (set-up): plane 5
+// becomes c5 A2 and plane 8 c5 A1 cot theta_j, for the values c5 of plane 5 at rows of
+// `pitch` columns (lfac: [2][W][n_th] as A2, A1 cot theta_j; padding columns get zero).
+template <int W>
+__global__ void ix_fold_kernel(uint4* dm, int* de, size_t per_plane, int pitch, int n_th, const double* lfac) {
+  using T = IxT<W>;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= per_plane) return;
+  const int j = (int)(k % (size_t)pitch);
+  typename T::Num p5 = T::zero_num(), p8 = T::zero_num();
+  if (j < n_th) {
+    typename T::Num c5;
+#pragma unroll
+    for (int u = 0; u < T::kU4; ++u) {
+      const uint4 v = dm[(5 * T::kU4 + u) * per_plane + k];
+      c5.m[4 * u] = v.x; c5.m[4 * u + 1] = v.y; c5.m[4 * u + 2] = v.z; c5.m[4 * u + 3] = v.w;
+    }
+    const int en = de[5 * per_plane + k];
+    c5.e = en >> 1;
+    c5.neg = (uint32_t)en & 1u;
+    uint32_t bad = 0;
+    p5 = ix_mul<W>(c5, T::load(lfac + j, n_th, bad));
+    p8 = ix_mul<W>(c5, T::load(lfac + (size_t)W * n_th + j, n_th, bad));
+  }
+#pragma unroll
+  for (int u = 0; u < T::kU4; ++u) {
+    dm[(5 * T::kU4 + u) * per_plane + k] = make_uint4(p5.m[4 * u], p5.m[4 * u + 1], p5.m[4 * u + 2], p5.m[4 * u + 3]);
+    dm[(8 * T::kU4 + u) * per_plane + k] = make_uint4(p8.m[4 * u], p8.m[4 * u + 1], p8.m[4 * u + 2], p8.m[4 * u + 3]);
+  }
+  de[5 * per_plane + k] = p5.e * 2 + (int)p5.neg;
+  de[8 * per_plane + k] = p8.e * 2 + (int)p8.neg;
+}
+
+// K-limb two's-complement integers (mod 2^(32 K)): in-place sum, difference and multiply-add
+// by a 32-bit constant, as carry chains.
+template <int K> struct Kl;
+template <> struct Kl<6> {
+  static IXD void add_to(uint32_t* d, const uint32_t* b) {
+    asm("add.cc.u32 %0, %0, %6;\n\t"
+        "addc.cc.u32 %1, %1, %7;\n\t"
+        "addc.cc.u32 %2, %2, %8;\n\t"
+        "addc.cc.u32 %3, %3, %9;\n\t"
+        "addc.cc.u32 %4, %4, %10;\n\t"
+        "addc.u32 %5, %5, %11;"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]));
+  }
+  static IXD void sub_from(uint32_t* d, const uint32_t* b) {
+    asm("sub.cc.u32 %0, %0, %6;\n\t"
+        "subc.cc.u32 %1, %1, %7;\n\t"
+        "subc.cc.u32 %2, %2, %8;\n\t"
+        "subc.cc.u32 %3, %3, %9;\n\t"
+        "subc.cc.u32 %4, %4, %10;\n\t"
+        "subc.u32 %5, %5, %11;"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]));
+  }
+  static IXD void mac(uint32_t* d, uint32_t c, const uint32_t* p) {
+    asm("mad.lo.cc.u32 %0, %6, %7, %0;\n\t"
+        "madc.lo.cc.u32 %1, %6, %8, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %9, %2;\n\t"
+        "madc.lo.cc.u32 %3, %6, %10, %3;\n\t"
+        "madc.lo.cc.u32 %4, %6, %11, %4;\n\t"
+        "madc.lo.u32 %5, %6, %12, %5;\n\t"
+        "mad.hi.cc.u32 %1, %6, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %6, %8, %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %9, %3;\n\t"
+        "madc.hi.cc.u32 %4, %6, %10, %4;\n\t"
+        "madc.hi.u32 %5, %6, %11, %5;"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5])
+        : "r"(c), "r"(p[0]), "r"(p[1]), "r"(p[2]), "r"(p[3]), "r"(p[4]), "r"(p[5]));
+  }
+};
+template <> struct Kl<10> {
+  static IXD void add_to(uint32_t* d, const uint32_t* b) {
+    asm("add.cc.u32 %0, %0, %10;\n\t"
+        "addc.cc.u32 %1, %1, %11;\n\t"
+        "addc.cc.u32 %2, %2, %12;\n\t"
+        "addc.cc.u32 %3, %3, %13;\n\t"
+        "addc.cc.u32 %4, %4, %14;\n\t"
+        "addc.cc.u32 %5, %5, %15;\n\t"
+        "addc.cc.u32 %6, %6, %16;\n\t"
+        "addc.cc.u32 %7, %7, %17;\n\t"
+        "addc.cc.u32 %8, %8, %18;\n\t"
+        "addc.u32 %9, %9, %19;"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7]), "+r"(d[8]), "+r"(d[9])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]));
+  }
+  static IXD void sub_from(uint32_t* d, const uint32_t* b) {
+    asm("sub.cc.u32 %0, %0, %10;\n\t"
+        "subc.cc.u32 %1, %1, %11;\n\t"
+        "subc.cc.u32 %2, %2, %12;\n\t"
+        "subc.cc.u32 %3, %3, %13;\n\t"
+        "subc.cc.u32 %4, %4, %14;\n\t"
+        "subc.cc.u32 %5, %5, %15;\n\t"
+        "subc.cc.u32 %6, %6, %16;\n\t"
+        "subc.cc.u32 %7, %7, %17;\n\t"
+        "subc.cc.u32 %8, %8, %18;\n\t"
+        "subc.u32 %9, %9, %19;"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7]), "+r"(d[8]), "+r"(d[9])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]));
+  }
+  static IXD void mac(uint32_t* d, uint32_t c, const uint32_t* p) {
+    asm("mad.lo.cc.u32 %0, %10, %11, %0;\n\t"
+        "madc.lo.cc.u32 %1, %10, %12, %1;\n\t"
+        "madc.lo.cc.u32 %2, %10, %13, %2;\n\t"
+        "madc.lo.cc.u32 %3, %10, %14, %3;\n\t"
+        "madc.lo.cc.u32 %4, %10, %15, %4;\n\t"
+        "madc.lo.cc.u32 %5, %10, %16, %5;\n\t"
+        "madc.lo.cc.u32 %6, %10, %17, %6;\n\t"
+        "madc.lo.cc.u32 %7, %10, %18, %7;\n\t"
+        "madc.lo.cc.u32 %8, %10, %19, %8;\n\t"
+        "madc.lo.u32 %9, %10, %20, %9;\n\t"
+        "mad.hi.cc.u32 %1, %10, %11, %1;\n\t"
+        "madc.hi.cc.u32 %2, %10, %12, %2;\n\t"
+        "madc.hi.cc.u32 %3, %10, %13, %3;\n\t"
+        "madc.hi.cc.u32 %4, %10, %14, %4;\n\t"
+        "madc.hi.cc.u32 %5, %10, %15, %5;\n\t"
+        "madc.hi.cc.u32 %6, %10, %16, %6;\n\t"
+        "madc.hi.cc.u32 %7, %10, %17, %7;\n\t"
+        "madc.hi.cc.u32 %8, %10, %18, %8;\n\t"
+        "madc.hi.u32 %9, %10, %19, %9;"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7]), "+r"(d[8]), "+r"(d[9])
+        : "r"(c), "r"(p[0]), "r"(p[1]), "r"(p[2]), "r"(p[3]), "r"(p[4]), "r"(p[5]), "r"(p[6]), "r"(p[7]), "r"(p[8]), "r"(p[9]));
+  }
+};
+
+// Shared row of one component: the values as engine numbers (mantissas [kU4][gstride] uint4,
+// exponent-sign words [gstride] int; only the row's own columns are read), and the ghosted
+// block-floating row (b: [kBlk / 2][gstride] uint2, value = b * 2^(E - 32)).
 struct IxRow {
   uint4* m;
   int* e;
+  uint2* b;
+  int E;  // largest exponent of the row (kZeroE for a row of zeros)
 };
 template <int W>
 IXD typename IxT<W>::Num ix_row_get(const IxRow& row, int gstride, int idx) {
@@ -134,16 +289,6 @@ IXD void ix_row_put(const IxRow& row, int gstride, int idx, const typename IxT<W
     row.m[u * gstride + idx] = make_uint4(v.m[4 * u], v.m[4 * u + 1], v.m[4 * u + 2], v.m[4 * u + 3]);
   row.e[idx] = en;
 }
-// Writes v as column j of a ghosted row (and its parity images across the poles).
-template <int W>
-IXD void ix_put_ghosted(const IxRow& row, int gstride, int n_th, int radius, int parity, int j,
-                        const typename IxT<W>::Num& v) {
-  const int en = ix_en(v), pen = parity > 0 ? en : (en ^ 1);
-  ix_row_put<W>(row, gstride, j + radius, v, en);
-  if (j < radius) ix_row_put<W>(row, gstride, radius - 1 - j, v, pen);
-  if (j >= n_th - radius) ix_row_put<W>(row, gstride, 2 * n_th - 1 - j + radius, v, pen);
-}
-
 IXHD int imax(int a, int b) { return a > b ? a : b; }
 
 // One term c * v with c from a coefficient table (plane q, index ci), sign flipped if flip.
@@ -170,28 +315,124 @@ IXD void ix_store(double* p, size_t ws, const typename IxT<W>::Acc& acc, int B, 
   for (int k = 0; k < W; ++k) p[k * ws] = bad ? nan : w[k];
 }
 
-// Theta operator at column j of a ghosted engine-format row.
-template <int W, int RAD>
-IXD typename IxT<W>::Num ix_theta(const IxArgs& x, const IxRow& row, int gstride, int j) {
-  const size_t n_th = (size_t)x.a.g.n_th;
-  int mx = 2 * ix::kZeroE;
+// v as a block-floating value of a row of largest exponent E, sign flipped if flip:
+// (-1)^neg (m 2^32) >> (E - e) in kBlk limbs (bits below the last are cut).
+template <int W>
+IXD void ix_to_block(const typename IxT<W>::Num& v, int E, uint32_t flip, uint32_t* out) {
+  using T = IxT<W>;
+  uint32_t p[T::kLimbs + 1];
 #pragma unroll
-  for (int q = 0; q < 2 * RAD + 1; ++q) mx = imax(mx, IxT<W>::pexp(__ldg(x.we + q * n_th + j) >> 1, row.e[j + q] >> 1));
-  typename IxT<W>::Acc acc;
-  IxT<W>::zero(acc);
+  for (int k = 0; k < T::kLimbs; ++k) p[k] = v.m[k];
+  p[T::kLimbs] = 0;
+  typename T::Acc acc;
+  T::zero(acc);
+  T::shift_in(acc, p, v.neg ^ flip, E - v.e);
 #pragma unroll
-  for (int q = 0; q < 2 * RAD + 1; ++q)
-    ix_tterm<W>(acc, x.wm, n_th, q, j, __ldg(x.we + q * n_th + j), ix_row_get<W>(row, gstride, j + q), 0u, mx);
-  return IxT<W>::to_num(acc, IxT<W>::base(mx));
+  for (int k = 0; k < T::kBlk; ++k) out[k] = acc.a[k];
 }
 template <int W>
-IXD typename IxT<W>::Num ix_theta(const IxArgs& x, const IxRow& row, int gstride, int j) {
-  return x.a.radius == 5 ? ix_theta<W, 5>(x, row, gstride, j) : ix_theta<W, 1>(x, row, gstride, j);
+IXD void ix_block_put(const IxRow& row, int gstride, int idx, const uint32_t* s) {
+#pragma unroll
+  for (int u = 0; u < IxT<W>::kBlk / 2; ++u) row.b[u * gstride + idx] = make_uint2(s[2 * u], s[2 * u + 1]);
+}
+template <int W>
+IXD void ix_block_get(const IxRow& row, int gstride, int idx, uint32_t* s) {
+#pragma unroll
+  for (int u = 0; u < IxT<W>::kBlk / 2; ++u) {
+    const uint2 v = row.b[u * gstride + idx];
+    s[2 * u] = v.x;
+    s[2 * u + 1] = v.y;
+  }
+}
+
+// Second phase of a row's set-up: the largest exponent of each component's row from the
+// per-warp maxima, then the thread's columns (and their parity images across the poles) into
+// the block-floating rows.
+template <int W>
+IXD void ix_block_rows(const IxArgs& x, int tx, int TX, IxRow& sR, IxRow& sI, int gstride, const int* wmax) {
+  const StepArgs& a = x.a;
+  const int n_th = a.g.n_th, rad = a.radius, nw = (TX + 31) / 32;
+  int ER = ix::kZeroE, EI = ix::kZeroE;
+  for (int w = 0; w < nw; ++w) {
+    ER = imax(ER, wmax[w]);
+    EI = imax(EI, wmax[8 + w]);
+  }
+  sR.E = ER;
+  sI.E = EI;
+  const uint32_t pflip = a.g.parity > 0 ? 0u : 1u;
+  for (int j = tx; j < n_th; j += TX) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const IxRow& row = c == 0 ? sR : sI;
+      const typename IxT<W>::Num v = ix_row_get<W>(row, gstride, j + rad);
+      uint32_t b[IxT<W>::kBlk];
+      ix_to_block<W>(v, row.E, 0u, b);
+      ix_block_put<W>(row, gstride, j + rad, b);
+      if (j < rad || j >= n_th - rad) {  // (a narrow row can need both images)
+        ix_to_block<W>(v, row.E, pflip, b);
+        if (j < rad) ix_block_put<W>(row, gstride, rad - 1 - j, b);
+        if (j >= n_th - rad) ix_block_put<W>(row, gstride, 2 * n_th - 1 - j + rad, b);
+      }
+    }
+  }
+}
+
+// Integer stencils of the theta operator at column j of a block-floating row: D2 = sum_q
+// d2_q s_{j+q}, D1 = sum_q d1_q s_{j+q} (10th order: d2 / 25200, d1 / 2520; 2nd order:
+// {1, -2, 1}, {-1, 0, 1} / 2; Sec. 3.B, 3.D), exact, returned as engine numbers. The
+// symmetric d2 and antisymmetric d1 take the sums and differences of the pairs j +- q.
+template <int W, int RAD>
+IXD void ix_stencil(const IxRow& row, int gstride, int j, typename IxT<W>::Num& D2, typename IxT<W>::Num& D1) {
+  using T = IxT<W>;
+  using L = Kl<T::kBlk>;
+  constexpr int K = T::kBlk;
+  // d2_0 .. d2_RAD and d1_1 .. d1_RAD
+  constexpr int d2[6] = {RAD == 5 ? -73766 : -2, RAD == 5 ? 42000 : 1, -6000, 1000, -125, 8};
+  constexpr int d1[6] = {0, RAD == 5 ? 2100 : 1, -600, 150, -25, 2};
+  uint32_t pos[K], neg[K], dd1[K], s0[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) pos[k] = neg[k] = dd1[k] = 0;
+  ix_block_get<W>(row, gstride, j + RAD, s0);
+  L::mac(neg, (uint32_t)(-d2[0]), s0);
+#pragma unroll
+  for (int q = 1; q <= RAD; ++q) {
+    uint32_t sp[K], sm[K], t[K];
+    ix_block_get<W>(row, gstride, j + RAD + q, sp);
+    ix_block_get<W>(row, gstride, j + RAD - q, sm);
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = sp[k];
+    L::add_to(t, sm);
+    if (d2[q] > 0) L::mac(pos, (uint32_t)d2[q], t);
+    else L::mac(neg, (uint32_t)(-d2[q]), t);
+    if (d1[q] > 0) {
+      L::sub_from(sp, sm);
+      L::mac(dd1, (uint32_t)d1[q], sp);
+    } else {
+      L::sub_from(sm, sp);
+      L::mac(dd1, (uint32_t)(-d1[q]), sm);
+    }
+  }
+  L::sub_from(pos, neg);
+  typename T::Acc acc;
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc.a[k] = pos[k];
+  D2 = T::to_num(acc, row.E - 32);
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc.a[k] = dd1[k];
+  D1 = T::to_num(acc, row.E - 32);
+}
+template <int W>
+IXD void ix_stencil(const IxArgs& x, const IxRow& row, int gstride, int j, typename IxT<W>::Num& D2,
+                    typename IxT<W>::Num& D1) {
+  if (x.a.radius == 5) ix_stencil<W, 5>(row, gstride, j, D2, D1);
+  else ix_stencil<W, 1>(row, gstride, j, D2, D1);
 }
 
 // Eq. lw1, first phase: s_Phi = Phi_{h+1} + Phi_h of row h into the ghosted rows.
+// (the values as engine numbers at their own columns; eR, eI: the thread's largest exponents)
 template <int W>
-IXD void ix_half_prep(const IxArgs& x, int h, int tx, int TX, const IxRow& sR, const IxRow& sI, int gstride) {
+IXD void ix_half_prep(const IxArgs& x, int h, int tx, int TX, const IxRow& sR, const IxRow& sI, int gstride,
+                      int& eR, int& eI) {
   const StepArgs& a = x.a;
   const size_t ws = (size_t)a.g.n_r * a.g.pitch;
   for (int j = tx; j < a.g.n_th; j += TX) {
@@ -200,8 +441,21 @@ IXD void ix_half_prep(const IxArgs& x, int h, int tx, int TX, const IxRow& sR, c
     const auto vR = IxT<W>::add(IxT<W>::load(a.u_in + i1, ws, bad), IxT<W>::load(a.u_in + i0, ws, bad), 0u);
     const auto vI = IxT<W>::add(IxT<W>::load(a.u_in + W * ws + i1, ws, bad),
                                 IxT<W>::load(a.u_in + W * ws + i0, ws, bad), 0u);
-    ix_put_ghosted<W>(sR, gstride, a.g.n_th, a.radius, a.g.parity, j, vR);
-    ix_put_ghosted<W>(sI, gstride, a.g.n_th, a.radius, a.g.parity, j, vI);
+    ix_row_put<W>(sR, gstride, j + a.radius, vR, ix_en(vR));
+    ix_row_put<W>(sI, gstride, j + a.radius, vI, ix_en(vI));
+    eR = imax(eR, vR.e);
+    eI = imax(eI, vI.e);
+  }
+}
+
+// End of a row's first phase: each warp's largest exponents of the two rows into wmax
+// ([2][8] per row of the block; the warps of a row never straddle rows).
+IXD void ix_warp_max(int eR, int eI, int tx, int* wmax) {
+  eR = __reduce_max_sync(0xffffffffu, eR);
+  eI = __reduce_max_sync(0xffffffffu, eI);
+  if ((tx & 31) == 0) {
+    wmax[tx >> 5] = eR;
+    wmax[8 + (tx >> 5)] = eI;
   }
 }
 
@@ -215,6 +469,10 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   const int pitch = a.g.pitch, rad = a.radius;
   const size_t ws = (size_t)a.g.n_r * pitch, hs = (size_t)(a.g.n_r - 1) * pitch;
   const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
+  // the theta stencils first: only their four results stay live
+  Num D2R, D1R, D2I, D1I;
+  ix_stencil<W>(x, sR, gstride, j, D2R, D1R);
+  ix_stencil<W>(x, sI, gstride, j, D2I, D1I);
   uint32_t bad = 0;
   const double* u = a.u_in;
   const Num uPR0 = T::load(u + 0 * W * ws + i0, ws, bad), uPR1 = T::load(u + 0 * W * ws + i1, ws, bad);
@@ -227,11 +485,10 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   // four Pi values early
   const Num dQR = T::add(uQR1, uQR0, 1u), dQI = T::add(uQI1, uQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
-  const Num LR = ix_theta<W>(x, sR, gstride, j), LI = ix_theta<W>(x, sI, gstride, j);
   const size_t ci = (size_t)h * pitch + j;
-  int ce[8];
+  int ce[kIxPlanes];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) ce[q] = __ldg(x.che + q * hs + ci);
+  for (int q = 0; q < kIxPlanes; ++q) ce[q] = __ldg(x.che + q * hs + ci);
 #define TT(q, v, f) ix_tterm<W>(acc, x.chm, hs, q, ci, ce[q], v, f, mx)
 #define TE(q, v) ix_texp<W>(ce[q], v)
   typename T::Acc acc;
@@ -252,18 +509,19 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   ix_nterm<W>(acc, h4, sQI, 0u, mx);
   ix_store<W>(a.uh + 1 * W * hs + ci, hs, acc, T::base(mx), bad, w);
   // Pi_R = H3 s_PiR + H4 s_PiI + H0 (Pi_R,h+1 - Pi_R,h) + H1 d_PhiR + H2 d_PhiI + H5 L_R + H6 s_PhiR - H7 s_PhiI
-  mx = imax(imax(imax(TE(3, sQR), TE(4, sQI)), TE(0, dQR)),
-            imax(imax(TE(1, dPR), TE(2, dPI)), imax(TE(5, LR), imax(TE(6, sPR), TE(7, sPI)))));
+  // with H5 L_R = (H5 A2) D2_R + (H5 A1 cot) D1_R (planes 5 and 8)
+  mx = imax(imax(imax(TE(3, sQR), TE(4, sQI)), imax(TE(0, dQR), TE(8, D1R))),
+            imax(imax(TE(1, dPR), TE(2, dPI)), imax(TE(5, D2R), imax(TE(6, sPR), TE(7, sPI)))));
   T::zero(acc);
   TT(3, sQR, 0u); TT(4, sQI, 0u); TT(0, dQR, 0u); TT(1, dPR, 0u);
-  TT(2, dPI, 0u); TT(5, LR, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
+  TT(2, dPI, 0u); TT(5, D2R, 0u); TT(8, D1R, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
   ix_store<W>(a.uh + 2 * W * hs + ci, hs, acc, T::base(mx), bad, w);
   // Pi_I = H3 s_PiI - H4 s_PiR + H0 (Pi_I,h+1 - Pi_I,h) + H1 d_PhiI - H2 d_PhiR + H5 L_I + H6 s_PhiI + H7 s_PhiR
-  mx = imax(imax(imax(TE(3, sQI), TE(4, sQR)), TE(0, dQI)),
-            imax(imax(TE(1, dPI), TE(2, dPR)), imax(TE(5, LI), imax(TE(6, sPI), TE(7, sPR)))));
+  mx = imax(imax(imax(TE(3, sQI), TE(4, sQR)), imax(TE(0, dQI), TE(8, D1I))),
+            imax(imax(TE(1, dPI), TE(2, dPR)), imax(TE(5, D2I), imax(TE(6, sPI), TE(7, sPR)))));
   T::zero(acc);
   TT(3, sQI, 0u); TT(4, sQR, 1u); TT(0, dQI, 0u); TT(1, dPI, 0u);
-  TT(2, dPR, 1u); TT(5, LI, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
+  TT(2, dPR, 1u); TT(5, D2I, 0u); TT(8, D1I, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
   ix_store<W>(a.uh + 3 * W * hs + ci, hs, acc, T::base(mx), bad, w);
 #undef TT
 #undef TE
@@ -271,7 +529,8 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
 
 // Eq. lw2, first phase: s_Phi = Phi_{i+1/2} + Phi_{i-1/2} into the ghosted rows.
 template <int W>
-IXD void ix_full_prep(const IxArgs& x, int i, int tx, int TX, const IxRow& sR, const IxRow& sI, int gstride) {
+IXD void ix_full_prep(const IxArgs& x, int i, int tx, int TX, const IxRow& sR, const IxRow& sI, int gstride,
+                      int& eR, int& eI) {
   const StepArgs& a = x.a;
   const size_t hs = (size_t)(a.g.n_r - 1) * a.g.pitch;
   for (int j = tx; j < a.g.n_th; j += TX) {
@@ -279,8 +538,10 @@ IXD void ix_full_prep(const IxArgs& x, int i, int tx, int TX, const IxRow& sR, c
     uint32_t bad = 0;
     const auto vR = IxT<W>::add(IxT<W>::load(a.uh + p, hs, bad), IxT<W>::load(a.uh + m, hs, bad), 0u);
     const auto vI = IxT<W>::add(IxT<W>::load(a.uh + W * hs + p, hs, bad), IxT<W>::load(a.uh + W * hs + m, hs, bad), 0u);
-    ix_put_ghosted<W>(sR, gstride, a.g.n_th, a.radius, a.g.parity, j, vR);
-    ix_put_ghosted<W>(sI, gstride, a.g.n_th, a.radius, a.g.parity, j, vI);
+    ix_row_put<W>(sR, gstride, j + a.radius, vR, ix_en(vR));
+    ix_row_put<W>(sI, gstride, j + a.radius, vI, ix_en(vI));
+    eR = imax(eR, vR.e);
+    eI = imax(eI, vI.e);
   }
 }
 
@@ -294,6 +555,9 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   const int pitch = a.g.pitch, rad = a.radius, n_th = a.g.n_th;
   const size_t ws = (size_t)a.g.n_r * pitch, hs = (size_t)(a.g.n_r - 1) * pitch;
   const size_t p = (size_t)i * pitch + j, m = p - pitch;
+  Num D2R, D1R, D2I, D1I;
+  ix_stencil<W>(x, sR, gstride, j, D2R, D1R);
+  ix_stencil<W>(x, sI, gstride, j, D2I, D1I);
   uint32_t bad = 0;
   const double* uh = a.uh;
   const Num hPR1 = T::load(uh + 0 * W * hs + p, hs, bad), hPR0 = T::load(uh + 0 * W * hs + m, hs, bad);
@@ -304,13 +568,12 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   const Num sQR = T::add(hQR1, hQR0, 0u), sQI = T::add(hQI1, hQI0, 0u);
   const Num dQR = T::add(hQR1, hQR0, 1u), dQI = T::add(hQI1, hQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
-  const Num LR = ix_theta<W>(x, sR, gstride, j), LI = ix_theta<W>(x, sI, gstride, j);
   const size_t ci = (size_t)i * pitch + j;
   const Num PR = T::load(a.u_in + 0 * W * ws + ci, ws, bad), PI = T::load(a.u_in + 1 * W * ws + ci, ws, bad);
   const Num QR = T::load(a.u_in + 2 * W * ws + ci, ws, bad), QI = T::load(a.u_in + 3 * W * ws + ci, ws, bad);
-  int ce[8];
+  int ce[kIxPlanes];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) ce[q] = __ldg(x.cne + q * ws + ci);
+  for (int q = 0; q < kIxPlanes; ++q) ce[q] = __ldg(x.cne + q * ws + ci);
 #define TT(q, v, f) ix_tterm<W>(acc, x.cnm, ws, q, ci, ce[q], v, f, mx)
 #define TE(q, v) ix_texp<W>(ce[q], v)
   typename T::Acc acc;
@@ -331,23 +594,23 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   ix_nterm<W>(acc, h2, sQI, 0u, mx);
   ix_store<W>(a.u_out + 1 * W * ws + ci, ws, acc, T::base(mx), bad, o1);
   // Pi_R' = Pi_R + N0 (h_PiR,i+1/2 - h_PiR,i-1/2) + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L_R
-  //         + N6 s_PhiR - N7 s_PhiI
-  mx = imax(imax(T::pexp(one.e, QR.e), imax(TE(0, dQR), TE(1, dPR))),
-            imax(imax(TE(2, dPI), TE(3, sQR)), imax(imax(TE(4, sQI), TE(5, LR)), imax(TE(6, sPR), TE(7, sPI)))));
+  //         + N6 s_PhiR - N7 s_PhiI, with N5 L_R = (N5 A2) D2_R + (N5 A1 cot) D1_R (planes 5 and 8)
+  mx = imax(imax(imax(T::pexp(one.e, QR.e), TE(8, D1R)), imax(TE(0, dQR), TE(1, dPR))),
+            imax(imax(TE(2, dPI), TE(3, sQR)), imax(imax(TE(4, sQI), TE(5, D2R)), imax(TE(6, sPR), TE(7, sPI)))));
   T::zero(acc);
   ix_nterm<W>(acc, one, QR, 0u, mx);
   TT(0, dQR, 0u); TT(1, dPR, 0u); TT(2, dPI, 0u); TT(3, sQR, 0u);
-  TT(4, sQI, 0u); TT(5, LR, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
+  TT(4, sQI, 0u); TT(5, D2R, 0u); TT(8, D1R, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
   ix_store<W>(a.u_out + 2 * W * ws + ci, ws, acc, T::base(mx), bad, w);
   const bool bad2 = nonfinite(w[0]);
   // Pi_I' = Pi_I + N0 (h_PiI,i+1/2 - h_PiI,i-1/2) + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L_I
   //         + N6 s_PhiI + N7 s_PhiR
-  mx = imax(imax(T::pexp(one.e, QI.e), imax(TE(0, dQI), TE(1, dPI))),
-            imax(imax(TE(2, dPR), TE(3, sQI)), imax(imax(TE(4, sQR), TE(5, LI)), imax(TE(6, sPI), TE(7, sPR)))));
+  mx = imax(imax(imax(T::pexp(one.e, QI.e), TE(8, D1I)), imax(TE(0, dQI), TE(1, dPI))),
+            imax(imax(TE(2, dPR), TE(3, sQI)), imax(imax(TE(4, sQR), TE(5, D2I)), imax(TE(6, sPI), TE(7, sPR)))));
   T::zero(acc);
   ix_nterm<W>(acc, one, QI, 0u, mx);
   TT(0, dQI, 0u); TT(1, dPI, 0u); TT(2, dPR, 1u); TT(3, sQI, 0u);
-  TT(4, sQR, 1u); TT(5, LI, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
+  TT(4, sQR, 1u); TT(5, D2I, 0u); TT(8, D1I, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
   ix_store<W>(a.u_out + 3 * W * ws + ci, ws, acc, T::base(mx), bad, w);
 #undef TT
 #undef TE
@@ -363,27 +626,45 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
 }
 
 // Shared memory of the engine kernels, for blockDim.y rows: mantissas [rows][2][kU4][gstride]
-// (uint4) first, then the exponent-sign words [rows][2][gstride] (int).
+// (uint4) first, then the exponent-sign words [rows][2][gstride] (int), the block-floating
+// rows [rows][2][kBlk / 2][gstride] (uint2) and the per-warp exponent maxima [rows][16] (int).
 template <int W>
-IXD void ix_rows(int gstride, IxRow& sR, IxRow& sI) {
+IXD void ix_rows(int gstride, IxRow& sR, IxRow& sI, int*& wmax) {
   extern __shared__ uint4 ixsm[];
   const int rows = blockDim.y, y = threadIdx.y;
-  constexpr int U = IxT<W>::kU4;
+  constexpr int U = IxT<W>::kU4, KB = IxT<W>::kBlk / 2;
   int* ebase = reinterpret_cast<int*>(ixsm + (size_t)rows * 2 * U * gstride);
+  uint2* bbase = reinterpret_cast<uint2*>(ebase + (size_t)rows * 2 * gstride);
+  int* mbase = reinterpret_cast<int*>(bbase + (size_t)rows * 2 * KB * gstride);
   sR.m = ixsm + (size_t)y * 2 * U * gstride;
   sI.m = sR.m + (size_t)U * gstride;
   sR.e = ebase + (size_t)y * 2 * gstride;
   sI.e = sR.e + gstride;
+  sR.b = bbase + (size_t)y * 2 * KB * gstride;
+  sI.b = sR.b + (size_t)KB * gstride;
+  sR.E = sI.E = ix::kZeroE;
+  wmax = mbase + 16 * y;
+}
+// Bytes of shared memory for `rows` rows of gstride columns.
+template <int W>
+inline size_t ix_smem_bytes(int rows, int gstride) {
+  return (size_t)rows * 2 * gstride * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int) + IxT<W>::kBlk * sizeof(uint32_t)) +
+         (size_t)rows * 16 * sizeof(int);
 }
 
 template <int W, int V>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) half_ix_kernel(IxArgs x) {
   const int gstride = x.a.g.n_th + 2 * x.a.radius;
   IxRow sR, sI;
-  ix_rows<W>(gstride, sR, sI);
+  int* wmax;
+  ix_rows<W>(gstride, sR, sI, wmax);
   const int h = blockIdx.x * blockDim.y + threadIdx.y;
   const bool ok = h < x.a.g.n_r - 1;
-  if (ok) ix_half_prep<W>(x, h, threadIdx.x, blockDim.x, sR, sI, gstride);
+  int eR = ix::kZeroE, eI = ix::kZeroE;
+  if (ok) ix_half_prep<W>(x, h, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
+  ix_warp_max(eR, eI, threadIdx.x, wmax);
+  __syncthreads();
+  if (ok) ix_block_rows<W>(x, threadIdx.x, blockDim.x, sR, sI, gstride, wmax);
   __syncthreads();
   if (!ok) return;
   uint32_t bad = 0;
@@ -396,10 +677,15 @@ template <int W, int V>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) full_ix_kernel(IxArgs x) {
   const int gstride = x.a.g.n_th + 2 * x.a.radius;
   IxRow sR, sI;
-  ix_rows<W>(gstride, sR, sI);
+  int* wmax;
+  ix_rows<W>(gstride, sR, sI, wmax);
   const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
   const bool ok = i < x.a.g.n_r - 1;
-  if (ok) ix_full_prep<W>(x, i, threadIdx.x, blockDim.x, sR, sI, gstride);
+  int eR = ix::kZeroE, eI = ix::kZeroE;
+  if (ok) ix_full_prep<W>(x, i, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
+  ix_warp_max(eR, eI, threadIdx.x, wmax);
+  __syncthreads();
+  if (ok) ix_block_rows<W>(x, threadIdx.x, blockDim.x, sR, sI, gstride, wmax);
   __syncthreads();
   if (!ok) return;
   uint32_t bad = 0;

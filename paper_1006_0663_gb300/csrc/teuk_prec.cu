@@ -80,6 +80,7 @@ int setup_impl(teuk_s* h) {
   const R A1 = rad == 5 ? r_div(r_from<R>(1.0), r_mul_d(dth, 2520.0))
                         : r_div(r_from<R>(1.0), r_mul_d(dth, 2.0));
   std::vector<double> sn((size_t)W * n_th), cs((size_t)W * n_th), wt((size_t)nq * W * n_th);
+  std::vector<double> lf((size_t)2 * W * n_th);  // weight_q = A2 d2_q + (A1 cot) d1_q
   for (int j = 0; j < n_th; ++j) {
     const R th = r_mul_d(dth, double(j) + 0.5);
     R s, c;
@@ -87,6 +88,13 @@ int setup_impl(teuk_s* h) {
     store_plane(sn, n_th, j, s);
     store_plane(cs, n_th, j, c);
     const R cot = r_div(c, s);
+    {
+      double w[4];
+      to_words(A2, w);
+      for (int k = 0; k < W; ++k) lf[(size_t)k * n_th + j] = w[k];
+      to_words(r_mul(A1, cot), w);
+      for (int k = 0; k < W; ++k) lf[((size_t)W + k) * n_th + j] = w[k];
+    }
     for (int q = 0; q < nq; ++q) {
       const R wq = r_add(r_mul_d(A2, d2[q]), r_mul(r_mul_d(A1, d1[q]), cot));
       double w[4];
@@ -97,6 +105,7 @@ int setup_impl(teuk_s* h) {
   TEUK_CUDA(h, cudaMemcpyAsync(h->sin_th, sn.data(), sn.size() * 8, cudaMemcpyHostToDevice, h->stream));
   TEUK_CUDA(h, cudaMemcpyAsync(h->cos_th, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, h->stream));
   TEUK_CUDA(h, cudaMemcpyAsync(h->wts, wt.data(), wt.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  TEUK_CUDA(h, cudaMemcpyAsync(h->lfac, lf.data(), lf.size() * 8, cudaMemcpyHostToDevice, h->stream));
 
   SetupArgs sa{};
   sa.g = Geom{n_r, n_th, pitch, h->parity};
@@ -302,8 +311,9 @@ int dissipate_impl(teuk_s* h) {
 }
 
 // Arithmetic engine of the double-double step (0: FP64 error-free transforms, 1: integer
-// engine). The integer engine keeps the coefficient tables and stencil weights in its own
-// format, converted here once from the double-double tables.
+// engine). The integer engine keeps the coefficient tables in its own format, converted here
+// once from the multi-word tables, with the theta operator's factors folded into plane 5 and
+// a ninth plane (ix_fold_kernel).
 int engine_impl(teuk_s* h, int engine) {
   if (engine == 0) {
     h->engine = 0;
@@ -312,16 +322,18 @@ int engine_impl(teuk_s* h, int engine) {
 #if TEUK_WORDS != 1
   if (!h->ix_m) {
     constexpr int U = IxT<W>::kU4;
-    const size_t ncn = (size_t)8 * h->n_r * h->pitch, nch = (size_t)8 * (h->n_r - 1) * h->pitch;
-    const size_t nw = (size_t)(2 * h->radius + 1) * h->n_th, total = ncn + nch + nw;
+    const size_t ws = (size_t)h->n_r * h->pitch, hs = (size_t)(h->n_r - 1) * h->pitch;
+    const size_t ncn = (size_t)kIxPlanes * ws, nch = (size_t)kIxPlanes * hs, total = ncn + nch;
     TEUK_CUDA(h, cudaMalloc(&h->ix_m, total * U * sizeof(uint4)));
     TEUK_CUDA(h, cudaMalloc(&h->ix_e, total * sizeof(int)));
-    const size_t ws = (size_t)h->n_r * h->pitch, hs = (size_t)(h->n_r - 1) * h->pitch;
-    ix_table_kernel<W><<<(unsigned)((ncn + 255) / 256), 256, 0, h->stream>>>(h->cn, ws, ws, ncn, h->ix_m, h->ix_e);
-    ix_table_kernel<W><<<(unsigned)((nch + 255) / 256), 256, 0, h->stream>>>(h->ch, hs, hs, nch, h->ix_m + U * ncn,
-                                                                             h->ix_e + ncn);
-    ix_table_kernel<W><<<(unsigned)((nw + 255) / 256), 256, 0, h->stream>>>(
-        h->wts, h->n_th, h->n_th, nw, h->ix_m + U * (ncn + nch), h->ix_e + ncn + nch);
+    // planes 0..7 from the folded tables, then plane 5 -> (5, 8)
+    ix_table_kernel<W><<<(unsigned)((8 * ws + 255) / 256), 256, 0, h->stream>>>(h->cn, ws, ws, 8 * ws, h->ix_m, h->ix_e);
+    ix_table_kernel<W><<<(unsigned)((8 * hs + 255) / 256), 256, 0, h->stream>>>(h->ch, hs, hs, 8 * hs,
+                                                                               h->ix_m + U * ncn, h->ix_e + ncn);
+    ix_fold_kernel<W><<<(unsigned)((ws + 255) / 256), 256, 0, h->stream>>>(h->ix_m, h->ix_e, ws, h->pitch, h->n_th,
+                                                                          h->lfac);
+    ix_fold_kernel<W><<<(unsigned)((hs + 255) / 256), 256, 0, h->stream>>>(h->ix_m + U * ncn, h->ix_e + ncn, hs,
+                                                                          h->pitch, h->n_th, h->lfac);
     TEUK_CUDA(h, cudaGetLastError());
     TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   }
@@ -384,9 +396,9 @@ int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
   if (h->engine == 1) {
     // integer engine: the row family's block shape, shared rows in the engine's format
     constexpr int U = IxT<W>::kU4;
-    const size_t ncn = (size_t)8 * h->n_r * h->pitch, nch = (size_t)8 * (h->n_r - 1) * h->pitch;
-    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, h->ix_m + U * (ncn + nch), h->ix_e + ncn + nch};
-    const size_t ism = (size_t)blk.y * 2 * (h->n_th + 2 * h->radius) * (U * sizeof(uint4) + sizeof(int));
+    const size_t ncn = (size_t)kIxPlanes * h->n_r * h->pitch;
+    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn};
+    const size_t ism = ix_smem_bytes<W>((int)blk.y, h->n_th + 2 * h->radius);
     if (ism > 48 * 1024) {
       TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
       TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
