@@ -83,9 +83,10 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
 
 /* Arithmetic engine of a double-double or quad-double handle (the paper's "quadruple" and
  * "octal" precisions, Sec. 3.D): 0 = FP64 error-free transforms (the default), 1 = integer
- * engine: every dot product of the step is formed exactly in fixed-point mantissas (128-bit
- * for dd, 256-bit for qd) on the integer pipe and rounded once (error about 2^-105 / 2^-208
- * of the result plus 2^-150 / 2^-270 of the largest term; subnormal operands count as zero).
+ * engine: every dot product of the step is formed in fixed-point mantissas (128-bit for dd,
+ * 256-bit for qd) on the integer pipe and rounded once (error about 2^-105 / 2^-208 of the
+ * result plus N 2^-122 / N 2^-249 of the largest of its N terms; subnormal operands count as
+ * zero).
  * GB300 issues far more integer than FP64 operations per cycle. Results of the two engines
  * agree to the precision's rounding, not bit for bit. Engine 1 converts the coefficient tables
  * once (about 1.25x their size of extra device memory) and runs the rows-per-block kernels
@@ -117,7 +118,9 @@ int teuk_step(teuk_t h, int64_t n_outer_steps);
 int teuk_use_graphs(teuk_t h, int enable);
 /* Advances n single Lax-Wendroff iterations of dt/substeps (no observer samples). */
 int teuk_substep(teuk_t h, int64_t n_iterations);
-/* Waits for the handle's stream; returns TEUK_ERR_NONFINITE if any Inf/NaN was produced. */
+/* Waits for the handle's stream; returns TEUK_ERR_NONFINITE if any Inf/NaN was produced, and
+ * TEUK_ERR_CUDA if a step kernel's wait for its own copies into shared memory reached its
+ * iteration limit (the kernel then skipped its rows). */
 int teuk_sync(teuk_t h);
 
 /* Phi at the node nearest rstar_obs (ties toward the lower index): out[2][w][n_theta]. */

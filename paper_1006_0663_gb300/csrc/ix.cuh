@@ -3,16 +3,18 @@
 // GB300 executes 2 FP64 operations per SM per cycle but about 60-80 integer instructions, so
 // the multi-word arithmetic of the Lax-Wendroff step (Sec. 3.D, Sec. 4: "quadruple" precision)
 // runs here on the integer pipe: every operand becomes a 128-bit fixed-point mantissa with an
-// exponent, products are formed exactly from 32-bit limbs (multiply-add with carry chains), and
-// the terms of a dot product are added, aligned to the largest, in a 192-bit two's-complement
+// exponent, products are formed from 32-bit limbs (multiply-add with carry chains), and the
+// terms of a dot product are added, aligned to the largest, in a 192-bit two's-complement
 // accumulator. Only the final split into two doubles uses three FP64 operations (Fast2Sum).
 //
-// Accuracy (worst case, relative to the largest term of a dot product): the product keeps all
-// partial products of weight >= 2^96 of the 256-bit product (error < 2^-156 of it), terms
-// below the accumulator's last bit (2^-185 of the largest) are truncated, and the result is
-// cut to 106 bits before the final rounding: the result is within about 2^-105 of its own
-// magnitude plus 2^-150 of the largest term, tighter than the FP64 error-free-transform
-// accumulator it replaces. Subnormal inputs are treated as zero; Inf/NaN inputs set `bad`.
+// Accuracy (worst case): a product keeps the partial products of weight >= 2^96 of the
+// 256-bit product; the dropped ones (columns 0-2 of 32-bit limbs) sum to less than 3 * 2^128,
+// i.e. less than 2^-122.4 of a product of two mantissas >= 2^126. Terms below the
+// accumulator's last bit (2^-185 of the largest) are truncated, and the result is cut to 106
+// bits before the final rounding: an N-term dot product is within about 2^-105 of its own
+// magnitude plus N 2^-122.4 of its largest term (2^-118.8 for 12 terms), tighter than the
+// FP64 error-free-transform accumulator it replaces (2^-104 of the sum of |terms|). Subnormal
+// inputs are treated as zero; Inf/NaN inputs set `bad`.
 //
 // The same code runs on the host (tests) and the device; integer arithmetic makes them agree
 // bit for bit.

@@ -3,10 +3,12 @@
 //
 // A quad-double (x0, x1, x2, x3) becomes an 8-limb (256-bit) fixed-point mantissa with the
 // leading bit of x0 at position 254 and an exponent; products keep all partial products of
-// weight >= 2^224 of the 512-bit product (error < 2^-245 of it); the terms of a dot product
+// weight >= 2^224 of the 512-bit product (the dropped columns 0-6 sum to less than 7.2 *
+// 2^256, i.e. 2^-249.1 of a product of two mantissas >= 2^254); the terms of a dot product
 // are added, aligned to the largest, in a 320-bit two's-complement accumulator; the result's
-// top 212 bits are cut into four doubles and renormalised (HLB01 renormalisation, FP64). The
-// result is within about 2^-208 of its own magnitude plus 2^-270 of the largest term.
+// top 212 bits are cut into four doubles and renormalised (HLB01 renormalisation, FP64). An
+// N-term dot product is within about 2^-208 of its own magnitude plus N 2^-249.1 of its
+// largest term (2^-245.6 for 12 terms).
 // Subnormal words are treated as zero; Inf/NaN words set `bad`.
 #pragma once
 

@@ -448,6 +448,10 @@ int teuk_sync(teuk_t h) {
     h->last_error = "non-finite value produced by the Lax-Wendroff step";
     return TEUK_ERR_NONFINITE;
   }
+  if (st & 2u) {
+    h->last_error = "a copy into shared memory did not complete within its wait limit";
+    return TEUK_ERR_CUDA;
+  }
   return TEUK_OK;
 }
 

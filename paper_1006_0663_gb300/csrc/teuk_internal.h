@@ -75,6 +75,8 @@ struct teuk_s {
                                        // 1 integer engine (ix.cuh)
   uint4* ix_m = nullptr;               // integer-engine tables: node coefficients, half-node
   int* ix_e = nullptr;                 // coefficients, stencil weights (mantissas, exponent-sign)
+  long long ix_stage_key = -1;         // launch shape the staging choice below was made for
+  int ix_stage = 0;                    // integer-engine kernels copy their table rows to shared memory
   std::string last_error;
 };
 

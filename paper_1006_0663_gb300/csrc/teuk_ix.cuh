@@ -1,7 +1,8 @@
 // Double-double and quad-double step kernels on the integer engine (ix.cuh, ixq.cuh): the
 // same two kernels per Lax-Wendroff iteration as teuk_kernels.cuh (Eqs. lw1, lw2 with the
 // folded coefficient tables and the 10th/2nd-order theta stencil, Sec. 3.B-3.D), with every
-// dot product formed exactly on the integer pipe and rounded once to the handle's precision.
+// dot product formed in fixed point on the integer pipe (each product cut below 2^-122 (dd) /
+// 2^-249 (qd) of itself, the sum of the terms exact) and rounded once to the handle's precision.
 // The state and the half-step rows stay multi-word doubles in HBM; the coefficient tables are
 // kept in the engine's format: the mantissa as 1 (dd) or 2 (qd) uint4 per value in planes of
 // their own, the exponent and sign as one int (e * 2 + neg).
@@ -93,6 +94,46 @@ struct IxArgs {
   const int* cne;       //   exponent-sign words [kIxPlanes][n_r][pitch]
   const uint4* chm;     // half-node coefficients [kIxPlanes][kU4][n_r - 1][pitch]
   const int* che;
+  int stage;            // 1: each block copies its rows of the tables into shared memory first
+};
+
+// Asynchronous bulk copies global -> shared completing on an mbarrier (sm_90+ PTX).
+IXD uint32_t ix_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+IXD void ix_bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ix_saddr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+IXD void ix_bar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ix_saddr(bar)), "r"(bytes) : "memory");
+}
+// bytes: a multiple of 16; both addresses 16-byte aligned
+IXD void ix_bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   ix_saddr(dst)),
+               "l"(src), "r"(bytes), "r"(ix_saddr(bar))
+               : "memory");
+}
+// Waits for phase 0 of bar with an iteration limit; false if the limit was reached.
+IXD bool ix_bar_wait(uint64_t* bar) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(ix_saddr(bar))
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Where a point reads its coefficients: plane q of value index ci at m[(q kU4 + u) pp + ci],
+// e[q pp + ci] (the global tables, or the block's rows of them in shared memory).
+struct IxTab {
+  const uint4* m;
+  const int* e;
+  size_t pp;
 };
 
 template <class N>
@@ -103,7 +144,7 @@ template <int W>
 IXD void ix_ldm(const uint4* base, size_t per_plane, size_t c, size_t r, uint32_t* m) {
 #pragma unroll
   for (int u = 0; u < IxT<W>::kU4; ++u) {
-    const uint4 v = __ldg(base + (c * IxT<W>::kU4 + u) * per_plane + r);
+    const uint4 v = base[(c * IxT<W>::kU4 + u) * per_plane + r];  // global or shared
     m[4 * u] = v.x; m[4 * u + 1] = v.y; m[4 * u + 2] = v.z; m[4 * u + 3] = v.w;
   }
 }
@@ -462,7 +503,8 @@ IXD void ix_warp_max(int eR, int eI, int tx, int* wmax) {
 // Eq. lw1 at half node h, column j (same terms as half_point in teuk_kernels.cuh).
 template <int W>
 IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxRow& sI, int gstride,
-                       const typename IxT<W>::Num& half, const typename IxT<W>::Num& h4) {
+                       const typename IxT<W>::Num& half, const typename IxT<W>::Num& h4, const IxTab& tb,
+                       size_t ci) {
   using T = IxT<W>;
   using Num = typename T::Num;
   const StepArgs& a = x.a;
@@ -485,11 +527,11 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   // four Pi values early
   const Num dQR = T::add(uQR1, uQR0, 1u), dQI = T::add(uQI1, uQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
-  const size_t ci = (size_t)h * pitch + j;
+  const size_t oi = (size_t)h * pitch + j;  // output index
   int ce[kIxPlanes];
 #pragma unroll
-  for (int q = 0; q < kIxPlanes; ++q) ce[q] = __ldg(x.che + q * hs + ci);
-#define TT(q, v, f) ix_tterm<W>(acc, x.chm, hs, q, ci, ce[q], v, f, mx)
+  for (int q = 0; q < kIxPlanes; ++q) ce[q] = tb.e[q * tb.pp + ci];
+#define TT(q, v, f) ix_tterm<W>(acc, tb.m, tb.pp, q, ci, ce[q], v, f, mx)
 #define TE(q, v) ix_texp<W>(ce[q], v)
   typename T::Acc acc;
   int mx;
@@ -500,14 +542,14 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   ix_nterm<W>(acc, half, sPR, 0u, mx);
   TT(0, dPR, 1u);
   ix_nterm<W>(acc, h4, sQR, 0u, mx);
-  ix_store<W>(a.uh + 0 * W * hs + ci, hs, acc, T::base(mx), bad, w);
+  ix_store<W>(a.uh + 0 * W * hs + oi, hs, acc, T::base(mx), bad, w);
   // Phi_I
   mx = imax(imax(T::pexp(half.e, sPI.e), TE(0, dPI)), T::pexp(h4.e, sQI.e));
   T::zero(acc);
   ix_nterm<W>(acc, half, sPI, 0u, mx);
   TT(0, dPI, 1u);
   ix_nterm<W>(acc, h4, sQI, 0u, mx);
-  ix_store<W>(a.uh + 1 * W * hs + ci, hs, acc, T::base(mx), bad, w);
+  ix_store<W>(a.uh + 1 * W * hs + oi, hs, acc, T::base(mx), bad, w);
   // Pi_R = H3 s_PiR + H4 s_PiI + H0 (Pi_R,h+1 - Pi_R,h) + H1 d_PhiR + H2 d_PhiI + H5 L_R + H6 s_PhiR - H7 s_PhiI
   // with H5 L_R = (H5 A2) D2_R + (H5 A1 cot) D1_R (planes 5 and 8)
   mx = imax(imax(imax(TE(3, sQR), TE(4, sQI)), imax(TE(0, dQR), TE(8, D1R))),
@@ -515,14 +557,14 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   T::zero(acc);
   TT(3, sQR, 0u); TT(4, sQI, 0u); TT(0, dQR, 0u); TT(1, dPR, 0u);
   TT(2, dPI, 0u); TT(5, D2R, 0u); TT(8, D1R, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
-  ix_store<W>(a.uh + 2 * W * hs + ci, hs, acc, T::base(mx), bad, w);
+  ix_store<W>(a.uh + 2 * W * hs + oi, hs, acc, T::base(mx), bad, w);
   // Pi_I = H3 s_PiI - H4 s_PiR + H0 (Pi_I,h+1 - Pi_I,h) + H1 d_PhiI - H2 d_PhiR + H5 L_I + H6 s_PhiI + H7 s_PhiR
   mx = imax(imax(imax(TE(3, sQI), TE(4, sQR)), imax(TE(0, dQI), TE(8, D1I))),
             imax(imax(TE(1, dPI), TE(2, dPR)), imax(TE(5, D2I), imax(TE(6, sPI), TE(7, sPR)))));
   T::zero(acc);
   TT(3, sQI, 0u); TT(4, sQR, 1u); TT(0, dQI, 0u); TT(1, dPI, 0u);
   TT(2, dPR, 1u); TT(5, D2I, 0u); TT(8, D1I, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
-  ix_store<W>(a.uh + 3 * W * hs + ci, hs, acc, T::base(mx), bad, w);
+  ix_store<W>(a.uh + 3 * W * hs + oi, hs, acc, T::base(mx), bad, w);
 #undef TT
 #undef TE
 }
@@ -548,7 +590,8 @@ IXD void ix_full_prep(const IxArgs& x, int i, int tx, int TX, const IxRow& sR, c
 // Eq. lw2 at node i, column j (same terms as full_point); returns true for a non-finite value.
 template <int W>
 IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxRow& sI, int gstride,
-                       const typename IxT<W>::Num& one, const typename IxT<W>::Num& h2, long long slot) {
+                       const typename IxT<W>::Num& one, const typename IxT<W>::Num& h2, long long slot,
+                       const IxTab& tb, size_t cti) {
   using T = IxT<W>;
   using Num = typename T::Num;
   const StepArgs& a = x.a;
@@ -573,8 +616,8 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   const Num QR = T::load(a.u_in + 2 * W * ws + ci, ws, bad), QI = T::load(a.u_in + 3 * W * ws + ci, ws, bad);
   int ce[kIxPlanes];
 #pragma unroll
-  for (int q = 0; q < kIxPlanes; ++q) ce[q] = __ldg(x.cne + q * ws + ci);
-#define TT(q, v, f) ix_tterm<W>(acc, x.cnm, ws, q, ci, ce[q], v, f, mx)
+  for (int q = 0; q < kIxPlanes; ++q) ce[q] = tb.e[q * tb.pp + cti];
+#define TT(q, v, f) ix_tterm<W>(acc, tb.m, tb.pp, q, cti, ce[q], v, f, mx)
 #define TE(q, v) ix_texp<W>(ce[q], v)
   typename T::Acc acc;
   int mx;
@@ -625,69 +668,130 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   return bad || bad2 || nonfinite(o0[0]) || nonfinite(o1[0]) || nonfinite(w[0]);
 }
 
-// Shared memory of the engine kernels, for blockDim.y rows: mantissas [rows][2][kU4][gstride]
-// (uint4) first, then the exponent-sign words [rows][2][gstride] (int), the block-floating
-// rows [rows][2][kBlk / 2][gstride] (uint2) and the per-warp exponent maxima [rows][16] (int).
+// Shared memory of the engine kernels, for blockDim.y rows: with staging, the block's rows of
+// the coefficient tables first (mantissas [kIxPlanes][kU4][rows][pitch] uint4, exponent-sign
+// words [kIxPlanes][rows][pitch] int); then the value mantissas [rows][2][kU4][gstride]
+// (uint4), their exponent-sign words [rows][2][gstride] (int), the block-floating rows
+// [rows][2][kBlk / 2][gstride] (uint2), the per-warp exponent maxima [rows][16] (int) and the
+// copies' mbarrier.
+struct IxSmem {
+  uint4* tm;
+  int* te;
+  int* wmax;
+  uint64_t* bar;
+};
 template <int W>
-IXD void ix_rows(int gstride, IxRow& sR, IxRow& sI, int*& wmax) {
+IXD IxSmem ix_rows(int gstride, int pitch, int stage, IxRow& sR, IxRow& sI) {
   extern __shared__ uint4 ixsm[];
   const int rows = blockDim.y, y = threadIdx.y;
   constexpr int U = IxT<W>::kU4, KB = IxT<W>::kBlk / 2;
-  int* ebase = reinterpret_cast<int*>(ixsm + (size_t)rows * 2 * U * gstride);
+  IxSmem sm;
+  sm.tm = ixsm;
+  sm.te = reinterpret_cast<int*>(ixsm + (size_t)kIxPlanes * U * rows * pitch);
+  uint4* rbase = stage ? reinterpret_cast<uint4*>(sm.te + (size_t)kIxPlanes * rows * pitch) : ixsm;
+  int* ebase = reinterpret_cast<int*>(rbase + (size_t)rows * 2 * U * gstride);
   uint2* bbase = reinterpret_cast<uint2*>(ebase + (size_t)rows * 2 * gstride);
   int* mbase = reinterpret_cast<int*>(bbase + (size_t)rows * 2 * KB * gstride);
-  sR.m = ixsm + (size_t)y * 2 * U * gstride;
+  sR.m = rbase + (size_t)y * 2 * U * gstride;
   sI.m = sR.m + (size_t)U * gstride;
   sR.e = ebase + (size_t)y * 2 * gstride;
   sI.e = sR.e + gstride;
   sR.b = bbase + (size_t)y * 2 * KB * gstride;
   sI.b = sR.b + (size_t)KB * gstride;
   sR.E = sI.E = ix::kZeroE;
-  wmax = mbase + 16 * y;
+  sm.wmax = mbase + 16 * y;
+  sm.bar = reinterpret_cast<uint64_t*>(mbase + 16 * rows);
+  return sm;
 }
-// Bytes of shared memory for `rows` rows of gstride columns.
+// Bytes of shared memory for `rows` rows of gstride columns (with the table rows if stage).
 template <int W>
-inline size_t ix_smem_bytes(int rows, int gstride) {
-  return (size_t)rows * 2 * gstride * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int) + IxT<W>::kBlk * sizeof(uint32_t)) +
-         (size_t)rows * 16 * sizeof(int);
+inline size_t ix_smem_bytes(int rows, int gstride, int pitch, int stage) {
+  const size_t tab = stage ? (size_t)kIxPlanes * rows * pitch * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int)) : 0;
+  return tab +
+         (size_t)rows * 2 * gstride * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int) + IxT<W>::kBlk * sizeof(uint32_t)) +
+         (size_t)rows * 16 * sizeof(int) + sizeof(uint64_t);
+}
+
+// One thread of the block starts the copies of the block's table rows r0 .. r0 + nv - 1
+// (planes of per_plane values at row pitch `pitch`; 16-byte aligned since pitch is a multiple
+// of 16) into shared memory.
+template <int W>
+IXD void ix_stage_tables(const IxSmem& sm, const uint4* gm, const int* ge, size_t per_plane, int pitch, int r0,
+                         int nv) {
+  constexpr int U = IxT<W>::kU4;
+  const int rows = blockDim.y;
+  const uint32_t mb = (uint32_t)nv * pitch * sizeof(uint4), eb = (uint32_t)nv * pitch * sizeof(int);
+  ix_bar_init(sm.bar);
+  ix_bar_expect(sm.bar, kIxPlanes * (U * mb + eb));
+  for (int q = 0; q < kIxPlanes; ++q) {
+    for (int u = 0; u < U; ++u)
+      ix_bulk_copy(sm.tm + ((size_t)(q * U + u) * rows) * pitch, gm + (q * U + u) * per_plane + (size_t)r0 * pitch,
+                   mb, sm.bar);
+    ix_bulk_copy(sm.te + (size_t)q * rows * pitch, ge + q * per_plane + (size_t)r0 * pitch, eb, sm.bar);
+  }
 }
 
 template <int W, int V>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) half_ix_kernel(IxArgs x) {
-  const int gstride = x.a.g.n_th + 2 * x.a.radius;
+  const int gstride = x.a.g.n_th + 2 * x.a.radius, pitch = x.a.g.pitch, nh = x.a.g.n_r - 1;
+  const size_t hs = (size_t)nh * pitch;
   IxRow sR, sI;
-  int* wmax;
-  ix_rows<W>(gstride, sR, sI, wmax);
-  const int h = blockIdx.x * blockDim.y + threadIdx.y;
-  const bool ok = h < x.a.g.n_r - 1;
+  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI);
+  const int h0 = blockIdx.x * blockDim.y, h = h0 + threadIdx.y;
+  if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
+    ix_stage_tables<W>(sm, x.chm, x.che, hs, pitch, h0, min((int)blockDim.y, nh - h0));
+  const bool ok = h < nh;
   int eR = ix::kZeroE, eI = ix::kZeroE;
   if (ok) ix_half_prep<W>(x, h, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
-  ix_warp_max(eR, eI, threadIdx.x, wmax);
+  ix_warp_max(eR, eI, threadIdx.x, sm.wmax);
   __syncthreads();
-  if (ok) ix_block_rows<W>(x, threadIdx.x, blockDim.x, sR, sI, gstride, wmax);
+  if (ok) ix_block_rows<W>(x, threadIdx.x, blockDim.x, sR, sI, gstride, sm.wmax);
   __syncthreads();
   if (!ok) return;
+  IxTab tb{x.chm, x.che, hs};
+  size_t base = (size_t)h * pitch;
+  if (x.stage) {
+    if (!ix_bar_wait(sm.bar)) {
+      atomicOr(x.a.status, 2u);
+      return;
+    }
+    tb = IxTab{sm.tm, sm.te, (size_t)blockDim.y * pitch};
+    base = (size_t)threadIdx.y * pitch;
+  }
   uint32_t bad = 0;
   const auto half = ix_pow2<W>(-1);
   const auto h4 = IxT<W>::load(x.a.h4, 1, bad);
-  for (int j = threadIdx.x; j < x.a.g.n_th; j += blockDim.x) ix_half_point<W>(x, h, j, sR, sI, gstride, half, h4);
+  for (int j = threadIdx.x; j < x.a.g.n_th; j += blockDim.x)
+    ix_half_point<W>(x, h, j, sR, sI, gstride, half, h4, tb, base + j);
 }
 
 template <int W, int V>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) full_ix_kernel(IxArgs x) {
-  const int gstride = x.a.g.n_th + 2 * x.a.radius;
+  const int gstride = x.a.g.n_th + 2 * x.a.radius, pitch = x.a.g.pitch, n_r = x.a.g.n_r;
+  const size_t ws = (size_t)n_r * pitch;
   IxRow sR, sI;
-  int* wmax;
-  ix_rows<W>(gstride, sR, sI, wmax);
-  const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
-  const bool ok = i < x.a.g.n_r - 1;
+  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI);
+  const int i0 = 1 + blockIdx.x * blockDim.y, i = i0 + threadIdx.y;
+  if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
+    ix_stage_tables<W>(sm, x.cnm, x.cne, ws, pitch, i0, min((int)blockDim.y, n_r - 1 - i0));
+  const bool ok = i < n_r - 1;
   int eR = ix::kZeroE, eI = ix::kZeroE;
   if (ok) ix_full_prep<W>(x, i, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
-  ix_warp_max(eR, eI, threadIdx.x, wmax);
+  ix_warp_max(eR, eI, threadIdx.x, sm.wmax);
   __syncthreads();
-  if (ok) ix_block_rows<W>(x, threadIdx.x, blockDim.x, sR, sI, gstride, wmax);
+  if (ok) ix_block_rows<W>(x, threadIdx.x, blockDim.x, sR, sI, gstride, sm.wmax);
   __syncthreads();
   if (!ok) return;
+  IxTab tb{x.cnm, x.cne, ws};
+  size_t base = (size_t)i * pitch;
+  if (x.stage) {
+    if (!ix_bar_wait(sm.bar)) {
+      atomicOr(x.a.status, 2u);
+      return;
+    }
+    tb = IxTab{sm.tm, sm.te, (size_t)blockDim.y * pitch};
+    base = (size_t)threadIdx.y * pitch;
+  }
   uint32_t bad = 0;
   const auto one = ix_pow2<W>(0);
   const auto h2 = IxT<W>::load(x.a.h2, 1, bad);
@@ -695,7 +799,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   if (x.a.record) slot = x.a.ring_slot >= 0 ? x.a.ring_slot : (*x.a.ring_counter) % x.a.ring_cap;
   bool anybad = false;
   for (int j = threadIdx.x; j < x.a.g.n_th; j += blockDim.x)
-    anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot);
+    anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot, tb, base + j);
   if (anybad) atomicOr(x.a.status, 1u);
 }
 

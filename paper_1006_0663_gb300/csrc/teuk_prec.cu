@@ -397,12 +397,30 @@ int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
     // integer engine: the row family's block shape, shared rows in the engine's format
     constexpr int U = IxT<W>::kU4;
     const size_t ncn = (size_t)kIxPlanes * h->n_r * h->pitch;
-    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn};
-    const size_t ism = ix_smem_bytes<W>((int)blk.y, h->n_th + 2 * h->radius);
-    if (ism > 48 * 1024) {
-      TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
-      TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+    const int gs = h->n_th + 2 * h->radius;
+    const long long key = ((long long)V << 40) | ((long long)blk.x << 20) | blk.y;
+    if (h->ix_stage_key != key) {
+      // stage the table rows in shared memory when that keeps as many blocks per SM resident
+      int occ[2] = {0, 0}, dev = 0, optin = 0;
+      TEUK_CUDA(h, cudaGetDevice(&dev));
+      TEUK_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      for (int st = 0; st < 2; ++st) {
+        const size_t b = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, st);
+        if (b > (size_t)optin) continue;
+        TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[st], full_ix_kernel<W, V>, (int)(blk.x * blk.y), b) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          occ[st] = 0;
+        }
+      }
+      h->ix_stage = occ[1] > 0 && occ[1] >= occ[0] ? 1 : 0;
+      h->ix_stage_key = key;
     }
+    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, h->ix_stage};
+    const size_t ism = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage);
+    TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+    TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
     cudaEvent_t ev = nullptr;
     time_begin(h, &ev);
     half_ix_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
@@ -559,8 +577,8 @@ __host__ __device__ R dot11(const double* a, const double* b, const double* out,
 }
 
 // op 9 (double-double and quad-double): the same sum through the integer engine (ix.cuh,
-// ixq.cuh): the 11 products and the initial value as terms of one exact dot product, rounded
-// once. ops 10 / 11: a + b / a - b through the engine's sum of two numbers, then rounded.
+// ixq.cuh): the 11 products and the initial value as terms of one fixed-point dot product,
+// rounded once. ops 10 / 11: a + b / a - b through the engine's sum of two numbers, then rounded.
 #if TEUK_WORDS != 1
 __host__ __device__ R ix_dot11(const double* a, const double* b, const double* out, int64_t n, int64_t t) {
   using T = IxT<W>;

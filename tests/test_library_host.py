@@ -162,7 +162,9 @@ def test_dot11_accumulator_with_cancellation_host(words):
     assert worst < BOUND[words], worst
 
 
-ENGINE_BOUNDS = {2: (-104, -150, -125), 4: (-208, -270, -253)}  # result, largest term, larger operand
+# result, largest term (12 terms x the cut of the product window: 2^-122.4 / 2^-249.1 per
+# term), larger operand
+ENGINE_BOUNDS = {2: (-104, -118, -125), 4: (-208, -245, -253)}
 
 
 def _rand_expansion(rng, words, e):
@@ -184,7 +186,7 @@ def _val(x, t):
 def test_integer_engine_dot_host(words):
     """The integer engine's dot product (op 9: out + 11 products, operands with exponents spread
     over +-200 binades, zeros, repeated terms that cancel) against mpmath: the error stays within
-    2^-104 (dd) / 2^-208 (qd) of the exact result plus 2^-150 / 2^-270 of the largest term."""
+    2^-104 (dd) / 2^-208 (qd) of the exact result plus 2^-118 / 2^-245 of the largest term."""
     mpm.mp.prec = 900
     rng = np.random.default_rng(11 + words)
     n = 160
@@ -209,6 +211,51 @@ def test_integer_engine_dot_host(words):
         assert abs(r[1, t]) <= np.spacing(abs(r[0, t])) / 2, t
     with pytest.raises(teuk.TeukError):
         teuk.mw_eval(9, 1, np.zeros((1, 3)), np.zeros((1, 3)), device=False)
+
+
+def _words_of(v, words):
+    out = []
+    for _ in range(words):
+        out.append(float(v))
+        v -= mpm.mpf(out[-1])
+    return out
+
+
+@pytest.mark.parametrize("words", [2, 4])
+def test_integer_engine_dot_cancellation_host(words):
+    """Dot products whose exact value is far below their largest term (x y - x (y + eps) plus
+    small terms, eps = 2^-80 / 2^-170 of y): the error is then governed by the bound relative
+    to the largest term, N 2^-122.4 / N 2^-249.1 for N terms (the partial products a product
+    window drops), and is not far below it: a window that kept fewer columns, or a bound
+    claimed tighter than the window allows, fails here."""
+    mpm.mp.prec = 900
+    rng = np.random.default_rng(40 + words)
+    n = 11  # every output sums the same 11 products (op 9 windows are circular)
+    sh = 80 if words == 2 else 170
+    _, eb, _ = ENGINE_BOUNDS[words]
+    worst = mpm.mpf(0)
+    for trial in range(40):
+        a = np.zeros((words, n)); b = np.zeros((words, n)); o = np.zeros((words, n))
+        x = _rand_expansion(rng, words, 0)
+        y = _rand_expansion(rng, words, 0)
+        eps = mpm.mpf(rng.uniform(0.5, 1.0)) * mpm.mpf(2) ** (-sh) * _val(np.array(y)[:, None], 0)
+        a[:, 0] = x; b[:, 0] = y
+        a[:, 1] = x; b[:, 1] = _words_of(-(_val(np.array(y)[:, None], 0) + eps), words)
+        for q in range(2, n):
+            a[:, q] = _rand_expansion(rng, words, -sh - 10 - int(rng.integers(0, 20)))
+            b[:, q] = _rand_expansion(rng, words, 0)
+        r = teuk.mw_eval(9, words, a, b, out=o, device=False)
+        terms = [_val(a, q) * _val(b, q) for q in range(n)]
+        exact = mpm.fsum(terms)
+        big = max(abs(t) for t in terms)
+        assert abs(exact) < big * mpm.mpf(2) ** (-sh + 2)
+        for t in range(n):
+            err = abs(_val(r, t) - exact)
+            assert err <= abs(exact) * mpm.mpf(2) ** (-104 if words == 2 else -208) + big * mpm.mpf(2) ** eb, (trial, t)
+            worst = max(worst, err / big)
+    # the cut of the windows is visible: the error relative to the largest term is within a few
+    # binades of the bound, far above the final rounding's 2^-105 |exact| share
+    assert worst > mpm.mpf(2) ** (eb - 12), float(mpm.log(worst, 2))
 
 
 @pytest.mark.parametrize("words", [2, 4])
