@@ -233,13 +233,16 @@ def run_batch1(prob, words, steps, torch, teuk):
     return prob.n_r * prob.n_theta * prob.substeps * steps / dt, dt / steps * 1e3
 
 
-def run_c4(torch, teuk, workloads):
+def run_c4(torch, teuk, workloads, engine=1):
     """The 64-member double-double batch: one cooperative launch per outer step against the
-    same members stepped one at a time (CUDA graphs on), equal arithmetic (bit-identical)."""
+    same members stepped one at a time (CUDA graphs on), equal arithmetic (bit-identical), on
+    the given multi-word engine."""
     members = []
     for i in range(workloads.BATCH_SIZE):
         p = workloads.batch_member(i)
         g = teuk.Teuk.from_problem(p)
+        if engine:
+            g.set_engine(engine)
         ar, ai = p.amps
         g.set_initial_pulse(p.center, p.width, ar, ai, p.ell)
         g.set_observer(p.rstar_obs, capacity=8)
@@ -269,7 +272,8 @@ def run_c4(torch, teuk, workloads):
             "updates_per_outer_step": pts,
             "batched_updates_per_s": pts / t_bat, "one_at_a_time_updates_per_s": pts / t_seq,
             "speedup": t_seq / t_bat, "batched_ms_per_step": t_bat * 1e3,
-            "one_at_a_time_ms_per_step": t_seq * 1e3, "grid_blocks": info["grid"]}
+            "one_at_a_time_ms_per_step": t_seq * 1e3, "grid_blocks": info["grid"],
+            "arithmetic": ENGINE_NAME[engine]}
 
 
 def run_e2e(prob, words, steps, torch, teuk, engine=0):
@@ -636,7 +640,10 @@ def main():
                 variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} {ENGINE_NAME[other]}"] = {
                     "updates_per_s": r0["points"] * r0["substeps"] * max(2, args.steps // 2) / (r0["ms_total"] * 1e-3),
                     "roofline": roofline_for(r0, prob, W, other, clocks, sms, teuk.fp64_peak(), args.workload)}
-        batched = None if args.no_batch else run_c4(torch, teuk, workloads)
+        batched = None
+        if not args.no_batch:
+            batched = run_c4(torch, teuk, workloads, engine=1)
+            batched["other_engine"] = run_c4(torch, teuk, workloads, engine=0)
         cpu = None if args.no_cpu else cpu_baseline(prob, W)
         if cpu is not None:
             cpu["cpu_model"] = cpu_model()

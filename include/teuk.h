@@ -178,10 +178,12 @@ int64_t teuk_kernel_launches(teuk_t h);
  * every member with more than q Lax-Wendroff iterations per step does one iteration; work
  * items of equal size (rows x theta columns) from all active members share the GPU, with a
  * grid-wide barrier between the half-step and full-step phases. Results are bit-identical to
- * stepping each member alone with teuk_step. Members must use the same precision and device,
- * stay alive while the batch exists, and not be stepped by other calls meanwhile; the batch
- * runs on the first member's stream. Observer rings of members receive one sample per outer
- * step, as with teuk_step. */
+ * stepping each member alone with teuk_step. Members must use the same precision, arithmetic
+ * engine (teuk_set_engine, chosen before the batch is made: a later change makes
+ * teuk_batch_step fail with TEUK_ERR_INVALID_ARG) and device, have no r* dissipation, stay
+ * alive while the batch exists, and not be stepped by other calls meanwhile; the batch runs on
+ * the first member's stream. Observer rings of members receive one sample per outer step, as
+ * with teuk_step. */
 typedef struct teuk_batch_s* teuk_batch_t;
 int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members);
 int teuk_batch_step(teuk_batch_t b, int64_t n_outer_steps);
@@ -209,8 +211,10 @@ int teuk_tune(teuk_t h, int* rows_per_block);
 int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant);
 /* Sets the launch shape explicitly (same meaning as above; threads_theta a multiple of 32,
  * threads_theta * rows_per_block <= 256; both ignored for variants 3..5, rows_per_block
- * ignored for 6..8; with variants 2 and 8 the block is cut to 128 threads). Results do not
- * depend on the shape. */
+ * ignored for 6..8; with variants 2 and 8 the block is cut to 128 threads; on the integer
+ * engine only variants 0..2, and rows_per_block rows must fit one block's shared memory,
+ * else TEUK_ERR_INVALID_ARG; the autotuner skips such shapes). Results do not depend on the
+ * shape. */
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant);
 
 /* Lax-Wendroff iterations that allocate nothing, for callers that cannot let a library

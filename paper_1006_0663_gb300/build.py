@@ -32,12 +32,14 @@ def _sources():
              ("teuk_batch", "teuk_batch.cu", [])]
     for w in (1, 2, 4):
         units.append((f"teuk_w{w}", "teuk_prec.cu", [f"-DTEUK_WORDS={w}"]))
+    for w in (2, 4):
+        units.append((f"teuk_ixk_w{w}", "teuk_ixk.cu", [f"-DTEUK_WORDS={w}"]))
     return units
 
 
 def _inputs_mtime() -> float:
     files = [os.path.join(CSRC, f) for f in HEADERS + ["teuk_capi.cu", "teuk_prec.cu", "teuk_noalloc.cu",
-                                                          "teuk_batch.cu"]]
+                                                          "teuk_batch.cu", "teuk_ixk.cu"]]
     files.append(os.path.join(ROOT, "include", "teuk.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)

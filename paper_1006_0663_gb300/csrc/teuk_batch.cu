@@ -1,6 +1,7 @@
 // Batched execution of many teuk problems in one cooperative launch (include/teuk.h,
 // teuk_batch_*): members of uneven size, theta resolution and substep count advance their
-// outer steps together; see batch_kernel in teuk_kernels.cuh.
+// outer steps together; see batch_kernel in teuk_kernels.cuh, and batch_ix_kernel in
+// teuk_ix.cuh for members on the integer engine.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -17,6 +18,9 @@ struct teuk_batch_s {
   std::vector<teuk_s*> members;               // sorted by k, descending
   std::vector<teuk::BatchMember> host_members;
   teuk::BatchMember* d_members = nullptr;
+  int engine = 0;                             // the members' arithmetic engine (all the same)
+  std::vector<teuk::IxArgs> host_ix;          // engine 1: the members' engine arguments
+  teuk::IxArgs* d_ix = nullptr;
   int* d_item_member = nullptr;
   int* d_active = nullptr;
   int k_max = 0;
@@ -63,7 +67,15 @@ const void* kernel_for(int W) {
   }
 }
 
+teuk::IxArgs member_ix_args(const teuk_s* h) {
+  const int U = h->W / 2;  // uint4 per engine mantissa: 1 (dd), 2 (qd)
+  const size_t ncn = (size_t)teuk::kIxPlanes * h->n_r * h->pitch;
+  return teuk::IxArgs{member_args(h), h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, 0};
+}
+
 void free_batch(teuk_batch_s* b) {
+  if (b->d_ix) cudaFree(b->d_ix);
+  b->d_ix = nullptr;
   if (b->d_members) cudaFree(b->d_members);
   if (b->d_item_member) cudaFree(b->d_item_member);
   if (b->d_active) cudaFree(b->d_active);
@@ -88,8 +100,13 @@ int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members) {
   b->W = b->members[0]->W;
   b->device = b->members[0]->device;
   b->stream = b->members[0]->stream;
+  b->engine = b->members[0]->engine;
   for (teuk_s* h : b->members)
-    if (h->W != b->W || h->device != b->device || h->ko_sigma > 0) { delete b; return TEUK_ERR_INVALID_ARG; }
+    if (h->W != b->W || h->device != b->device || h->ko_sigma > 0 || h->engine != b->engine ||
+        (h->engine == 1 && !h->ix_m)) {
+      delete b;
+      return TEUK_ERR_INVALID_ARG;
+    }
   // members with more iterations per outer step first: the active items of round q are a prefix
   std::stable_sort(b->members.begin(), b->members.end(), [](const teuk_s* x, const teuk_s* y) { return x->k > y->k; });
   std::vector<int> item_member;
@@ -105,7 +122,13 @@ int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members) {
     const int n_items = (h->n_r - 1 + M.rows - 1) / M.rows;
     for (int t = 0; t < n_items; ++t) item_member.push_back((int)idx);
     b->host_members.push_back(M);
-    smem = std::max(smem, (size_t)M.rows * 2 * b->W * (h->n_th + 2 * h->radius) * sizeof(double));
+    const int gs = h->n_th + 2 * h->radius;
+    if (b->engine == 1) {
+      smem = std::max(smem, b->W == 2 ? teuk::ix_row_smem_w2(M.rows, gs) : teuk::ix_row_smem_w4(M.rows, gs));
+      b->host_ix.push_back(member_ix_args(h));
+    } else {
+      smem = std::max(smem, (size_t)M.rows * 2 * b->W * gs * sizeof(double));
+    }
     b->k_max = std::max(b->k_max, h->k);
     b->points_per_outer += (int64_t)h->k * h->n_r * h->n_th;
   }
@@ -127,13 +150,20 @@ int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members) {
   if ((e = cudaMalloc(&b->d_active, active.size() * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc");
   cudaMemcpy(b->d_item_member, item_member.data(), item_member.size() * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_active, active.data(), active.size() * sizeof(int), cudaMemcpyHostToDevice);
-  const void* fn = kernel_for(b->W);
-  if (smem > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return fail(e, "cudaFuncSetAttribute");
   int per_sm = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess)
-    return fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (b->engine == 1) {
+    if ((e = cudaMalloc(&b->d_ix, b->host_ix.size() * sizeof(teuk::IxArgs))) != cudaSuccess)
+      return fail(e, "cudaMalloc");
+    e = b->W == 2 ? teuk::batch_ix_occupancy_w2(&per_sm, smem) : teuk::batch_ix_occupancy_w4(&per_sm, smem);
+    if (e != cudaSuccess) return fail(e, "batch kernel occupancy");
+  } else {
+    const void* fn = kernel_for(b->W);
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess)
+      return fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   b->grid = per_sm * sms;
   if (b->grid < 1) return fail(cudaErrorInvalidConfiguration, "batch kernel does not fit on an SM");
@@ -143,9 +173,14 @@ int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members) {
 
 int teuk_batch_step(teuk_batch_t b, int64_t n_outer_steps) {
   if (!b || n_outer_steps < 0) return TEUK_ERR_INVALID_ARG;
-  // the members' own streams must have finished their earlier work
-  for (teuk_s* h : b->members)
+  // the members' own streams must have finished their earlier work; their engine is the batch's
+  for (teuk_s* h : b->members) {
+    if (h->engine != b->engine) {
+      b->last_error = "a member's arithmetic engine changed after the batch was made";
+      return TEUK_ERR_INVALID_ARG;
+    }
     if (h->stream != b->stream) cudaStreamSynchronize(h->stream);
+  }
   int64_t done = 0;
   while (done < n_outer_steps) {
     const int64_t chunk = std::min(kStepsPerLaunch, n_outer_steps - done);
@@ -161,8 +196,17 @@ int teuk_batch_step(teuk_batch_t b, int64_t n_outer_steps) {
                                     b->stream);
     if (e != cudaSuccess) { b->last_error = cudaGetErrorString(e); return TEUK_ERR_CUDA; }
     teuk::BatchArgs args{b->d_members, b->d_item_member, b->d_active, b->k_max, (int)chunk};
-    void* params[] = {&args};
-    e = cudaLaunchCooperativeKernel(kernel_for(b->W), dim3(b->grid), dim3(kThreads), params, b->smem, b->stream);
+    if (b->engine == 1) {
+      for (size_t idx = 0; idx < b->members.size(); ++idx) b->host_ix[idx] = member_ix_args(b->members[idx]);
+      e = cudaMemcpyAsync(b->d_ix, b->host_ix.data(), b->host_ix.size() * sizeof(teuk::IxArgs),
+                          cudaMemcpyHostToDevice, b->stream);
+      if (e == cudaSuccess)
+        e = b->W == 2 ? teuk::batch_ix_launch_w2(args, b->d_ix, b->grid, b->smem, b->stream)
+                      : teuk::batch_ix_launch_w4(args, b->d_ix, b->grid, b->smem, b->stream);
+    } else {
+      void* params[] = {&args};
+      e = cudaLaunchCooperativeKernel(kernel_for(b->W), dim3(b->grid), dim3(kThreads), params, b->smem, b->stream);
+    }
     if (e != cudaSuccess) { b->last_error = std::string("cooperative launch: ") + cudaGetErrorString(e); return TEUK_ERR_CUDA; }
     ++b->launches;
     for (teuk_s* h : b->members) {

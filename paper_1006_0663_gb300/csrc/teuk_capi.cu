@@ -554,6 +554,18 @@ int teuk_get_tortoise(teuk_t h, int which, double* x_out) {
   return TEUK_OK;
 }
 
+// Whether ty rows of the integer engine's kernels fit the shared memory of one block.
+bool ix_shape_fits(const teuk_s* h, int ty) {
+  if (h->W == 1) return true;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  const int gs = h->n_th + 2 * h->radius;
+  const size_t b = h->W == 2 ? teuk::ix_row_smem_w2(ty, gs) : teuk::ix_row_smem_w4(ty, gs);
+  return b <= (size_t)optin;
+}
+
 int teuk_tune(teuk_t h, int* rows_per_block) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   const size_t n = (size_t)4 * h->W * h->n_r * h->pitch;
@@ -577,6 +589,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   // row width itself) x rows per block, at most 256 threads
   int best_v = 0, best_f = 0;
   auto trial = [&](int f, int v, int tx, int ty) {
+    if (h->engine == 1 && !ix_shape_fits(h, ty)) return;  // rows too wide for one block
     h->kernel_family = f;
     h->kernel_variant = v;
     h->threads_theta = tx;
@@ -663,6 +676,8 @@ int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int v
     if (threads_theta < 32 || threads_theta % 32 != 0 || rows_per_block < 1 ||
         threads_theta * rows_per_block > 256)
       return invalid(h, "launch shape: threads_theta a multiple of 32, threads_theta * rows <= 256");
+    if (h->engine == 1 && !ix_shape_fits(h, rows_per_block))
+      return invalid(h, "launch shape: the integer engine's rows need more shared memory than a block can have");
     h->kernel_family = 0;
     h->kernel_variant = variant;
     h->threads_theta = threads_theta;

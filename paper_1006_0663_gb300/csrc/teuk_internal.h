@@ -98,6 +98,22 @@ int substep_buffers_w4(teuk_s* h, const double* u_in, double* u_out, double* scr
 int prepare_w1(teuk_s* h);
 int prepare_w2(teuk_s* h);
 int prepare_w4(teuk_s* h);
+// Integer-engine kernels (double-double and quad-double; teuk_ixk.cu): the engine's tables,
+// the step's kernel pair of register-budget variant 0..2, and the batched executor.
+struct StepArgs;
+struct BatchArgs;
+struct IxArgs;
+int ix_tables_w2(teuk_s* h);
+int ix_tables_w4(teuk_s* h);
+int ix_launch_pair_w2(teuk_s* h, const StepArgs& sa, dim3 blk, int variant);
+int ix_launch_pair_w4(teuk_s* h, const StepArgs& sa, dim3 blk, int variant);
+// (shared memory of `rows` engine rows of gstride columns without the staged tables)
+size_t ix_row_smem_w2(int rows, int gstride);
+size_t ix_row_smem_w4(int rows, int gstride);
+cudaError_t batch_ix_occupancy_w2(int* per_sm, size_t smem);
+cudaError_t batch_ix_occupancy_w4(int* per_sm, size_t smem);
+cudaError_t batch_ix_launch_w2(const BatchArgs& args, const IxArgs* d_ix, int grid, size_t smem, cudaStream_t st);
+cudaError_t batch_ix_launch_w4(const BatchArgs& args, const IxArgs* d_ix, int grid, size_t smem, cudaStream_t st);
 int engine_w1(teuk_s* h, int engine);
 int engine_w2(teuk_s* h, int engine);
 int engine_w4(teuk_s* h, int engine);

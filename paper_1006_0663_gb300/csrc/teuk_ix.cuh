@@ -83,19 +83,6 @@ IXHD typename IxT<W>::Num ix_pow2(int k) {
   return r;
 }
 
-// Planes of the engine's coefficient tables: the eight folded coefficients of the step, with
-// plane 5 (H5 / N5, the factor of the theta operator) replaced by H5 A2 and plane 8 holding
-// H5 A1 cot theta_j.
-constexpr int kIxPlanes = 9;
-
-struct IxArgs {
-  StepArgs a;           // geometry, state, half-step rows, ring, status
-  const uint4* cnm;     // node coefficients [kIxPlanes][kU4][n_r][pitch]: mantissas
-  const int* cne;       //   exponent-sign words [kIxPlanes][n_r][pitch]
-  const uint4* chm;     // half-node coefficients [kIxPlanes][kU4][n_r - 1][pitch]
-  const int* che;
-  int stage;            // 1: each block copies its rows of the tables into shared memory first
-};
 
 // Asynchronous bulk copies global -> shared completing on an mbarrier (sm_90+ PTX).
 IXD uint32_t ix_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -491,10 +478,10 @@ IXD void ix_half_prep(const IxArgs& x, int h, int tx, int TX, const IxRow& sR, c
 
 // End of a row's first phase: each warp's largest exponents of the two rows into wmax
 // ([2][8] per row of the block; the warps of a row never straddle rows).
-IXD void ix_warp_max(int eR, int eI, int tx, int* wmax) {
+IXD void ix_warp_max(int eR, int eI, int tx, int* wmax, bool write = true) {
   eR = __reduce_max_sync(0xffffffffu, eR);
   eI = __reduce_max_sync(0xffffffffu, eI);
-  if ((tx & 31) == 0) {
+  if (write && (tx & 31) == 0) {
     wmax[tx >> 5] = eR;
     wmax[8 + (tx >> 5)] = eI;
   }
@@ -681,9 +668,8 @@ struct IxSmem {
   uint64_t* bar;
 };
 template <int W>
-IXD IxSmem ix_rows(int gstride, int pitch, int stage, IxRow& sR, IxRow& sI) {
+IXD IxSmem ix_rows(int gstride, int pitch, int stage, IxRow& sR, IxRow& sI, int rows, int y) {
   extern __shared__ uint4 ixsm[];
-  const int rows = blockDim.y, y = threadIdx.y;
   constexpr int U = IxT<W>::kU4, KB = IxT<W>::kBlk / 2;
   IxSmem sm;
   sm.tm = ixsm;
@@ -736,7 +722,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) h
   const int gstride = x.a.g.n_th + 2 * x.a.radius, pitch = x.a.g.pitch, nh = x.a.g.n_r - 1;
   const size_t hs = (size_t)nh * pitch;
   IxRow sR, sI;
-  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI);
+  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI, blockDim.y, threadIdx.y);
   const int h0 = blockIdx.x * blockDim.y, h = h0 + threadIdx.y;
   if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
     ix_stage_tables<W>(sm, x.chm, x.che, hs, pitch, h0, min((int)blockDim.y, nh - h0));
@@ -770,7 +756,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   const int gstride = x.a.g.n_th + 2 * x.a.radius, pitch = x.a.g.pitch, n_r = x.a.g.n_r;
   const size_t ws = (size_t)n_r * pitch;
   IxRow sR, sI;
-  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI);
+  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI, blockDim.y, threadIdx.y);
   const int i0 = 1 + blockIdx.x * blockDim.y, i = i0 + threadIdx.y;
   if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
     ix_stage_tables<W>(sm, x.cnm, x.cne, ws, pitch, i0, min((int)blockDim.y, n_r - 1 - i0));
@@ -801,6 +787,80 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   for (int j = threadIdx.x; j < x.a.g.n_th; j += blockDim.x)
     anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot, tb, base + j);
   if (anybad) atomicOr(x.a.status, 1u);
+}
+
+// Batched execution on the integer engine: batch_kernel's rounds (every member with k > q
+// performs iteration q; half-step phase, grid barrier, full-step phase, grid barrier) with the
+// engine's row set-up and point functions per work item (rows x theta threads of the block;
+// tables read from global memory). ix: the members' engine arguments, indexed like b.m.
+template <int W>
+__global__ void __launch_bounds__(256, 2) batch_ix_kernel(BatchArgs b, const IxArgs* ix) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  for (int s = 0; s < b.n_outer; ++s) {
+    for (int q = 0; q < b.k_max; ++q) {
+      const int n_act = b.active_items[q];
+      for (int it = blockIdx.x; it < n_act; it += gridDim.x) {
+        const int mi = b.item_member[it];
+        const BatchMember& M = b.m[mi];
+        const IxArgs& x = ix[mi];
+        const int tx = threadIdx.x % M.tx, ty = threadIdx.x / M.tx;
+        const bool row = ty < M.rows;
+        const int h = (it - M.item_begin) * M.rows + ty, nh = M.a.g.n_r - 1, pitch = M.a.g.pitch;
+        const bool ok = row && h < nh;
+        const int gstride = M.a.g.n_th + 2 * M.a.radius;
+        IxRow sR, sI;
+        const IxSmem sm = ix_rows<W>(gstride, pitch, 0, sR, sI, M.rows, row ? ty : 0);
+        int eR = ix::kZeroE, eI = ix::kZeroE;
+        if (ok) ix_half_prep<W>(x, h, tx, M.tx, sR, sI, gstride, eR, eI);
+        ix_warp_max(eR, eI, tx, sm.wmax, row);
+        __syncthreads();
+        if (ok) ix_block_rows<W>(x, tx, M.tx, sR, sI, gstride, sm.wmax);
+        __syncthreads();
+        if (ok) {
+          uint32_t bad = 0;
+          const auto half = ix_pow2<W>(-1);
+          const auto h4 = IxT<W>::load(M.a.h4, 1, bad);
+          const IxTab tb{x.chm, x.che, (size_t)nh * pitch};
+          for (int j = tx; j < M.a.g.n_th; j += M.tx)
+            ix_half_point<W>(x, h, j, sR, sI, gstride, half, h4, tb, (size_t)h * pitch + j);
+        }
+        __syncthreads();
+      }
+      grid.sync();
+      for (int it = blockIdx.x; it < n_act; it += gridDim.x) {
+        const int mi = b.item_member[it];
+        const BatchMember& M = b.m[mi];
+        const IxArgs& x = ix[mi];
+        const int tx = threadIdx.x % M.tx, ty = threadIdx.x / M.tx;
+        const bool row = ty < M.rows;
+        const int i = 1 + (it - M.item_begin) * M.rows + ty, n_r = M.a.g.n_r, pitch = M.a.g.pitch;
+        const bool ok = row && i < n_r - 1;
+        const int gstride = M.a.g.n_th + 2 * M.a.radius;
+        IxRow sR, sI;
+        const IxSmem sm = ix_rows<W>(gstride, pitch, 0, sR, sI, M.rows, row ? ty : 0);
+        int eR = ix::kZeroE, eI = ix::kZeroE;
+        if (ok) ix_full_prep<W>(x, i, tx, M.tx, sR, sI, gstride, eR, eI);
+        ix_warp_max(eR, eI, tx, sm.wmax, row);
+        __syncthreads();
+        if (ok) ix_block_rows<W>(x, tx, M.tx, sR, sI, gstride, sm.wmax);
+        __syncthreads();
+        if (ok) {
+          uint32_t bad = 0;
+          const auto one = ix_pow2<W>(0);
+          const auto h2 = IxT<W>::load(M.a.h2, 1, bad);
+          const long long slot = (q == M.k - 1 && M.ring_cap > 0) ? (M.ring_base + s) % M.ring_cap : -1;
+          const IxTab tb{x.cnm, x.cne, (size_t)n_r * pitch};
+          bool anybad = false;
+          for (int j = tx; j < M.a.g.n_th; j += M.tx)
+            anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot, tb, (size_t)i * pitch + j);
+          if (anybad) atomicOr(M.a.status, 1u);
+        }
+        __syncthreads();
+      }
+      grid.sync();
+    }
+  }
 }
 
 #undef IXD

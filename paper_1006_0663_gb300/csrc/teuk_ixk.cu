@@ -1,0 +1,123 @@
+// Integer-engine kernels of one precision (built once for double-double, once for
+// quad-double: TEUK_WORDS = 2 or 4), in a unit of their own so that they compile in parallel
+// with the FP64-transform kernels of teuk_prec.cu: conversion of the coefficient tables, the
+// step's two kernels per Lax-Wendroff iteration (Eqs. lw1, lw2) and the batched executor.
+#include <cstring>
+
+#include "teuk_internal.h"
+#include "teuk_kernels.cuh"
+#include "teuk_ix.cuh"
+
+#if TEUK_WORDS != 2 && TEUK_WORDS != 4
+#error "teuk_ixk.cu is built for TEUK_WORDS = 2 or 4"
+#endif
+
+#define TEUK_CAT2(a, b) a##b
+#define TEUK_CAT(a, b) TEUK_CAT2(a, b)
+#define TEUK_SUFFIX(name) TEUK_CAT(name, TEUK_WORDS)
+
+namespace teuk {
+namespace TEUK_SUFFIX(ixk_w) {
+
+constexpr int W = TEUK_WORDS;
+constexpr int U = IxT<W>::kU4;
+
+// The engine's coefficient tables, converted once from the folded multi-word tables (planes
+// 0..7), then plane 5 -> (H5 A2, H5 A1 cot theta_j) as planes 5 and 8 (ix_fold_kernel).
+int tables(teuk_s* h) {
+  const size_t ws = (size_t)h->n_r * h->pitch, hs = (size_t)(h->n_r - 1) * h->pitch;
+  const size_t ncn = (size_t)kIxPlanes * ws, nch = (size_t)kIxPlanes * hs, total = ncn + nch;
+  TEUK_CUDA(h, cudaMalloc(&h->ix_m, total * U * sizeof(uint4)));
+  TEUK_CUDA(h, cudaMalloc(&h->ix_e, total * sizeof(int)));
+  ix_table_kernel<W><<<(unsigned)((8 * ws + 255) / 256), 256, 0, h->stream>>>(h->cn, ws, ws, 8 * ws, h->ix_m, h->ix_e);
+  ix_table_kernel<W><<<(unsigned)((8 * hs + 255) / 256), 256, 0, h->stream>>>(h->ch, hs, hs, 8 * hs,
+                                                                             h->ix_m + U * ncn, h->ix_e + ncn);
+  ix_fold_kernel<W><<<(unsigned)((ws + 255) / 256), 256, 0, h->stream>>>(h->ix_m, h->ix_e, ws, h->pitch, h->n_th,
+                                                                        h->lfac);
+  ix_fold_kernel<W><<<(unsigned)((hs + 255) / 256), 256, 0, h->stream>>>(h->ix_m + U * ncn, h->ix_e + ncn, hs,
+                                                                        h->pitch, h->n_th, h->lfac);
+  TEUK_CUDA(h, cudaGetLastError());
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
+// The half and full kernels of register-budget variant V for the block shape blk: rows of
+// the row family, shared rows in the engine's format.
+template <int V>
+int launch_pair(teuk_s* h, const StepArgs& sa, dim3 blk) {
+  const int nh = h->n_r - 1, nf = h->n_r - 2;
+  const size_t ncn = (size_t)kIxPlanes * h->n_r * h->pitch;
+  const int gs = h->n_th + 2 * h->radius;
+  const long long key = ((long long)V << 40) | ((long long)blk.x << 20) | blk.y;
+  if (h->ix_stage_key != key) {
+    // stage the table rows in shared memory when that keeps as many blocks per SM resident
+    int occ[2] = {0, 0}, dev = 0, optin = 0;
+    TEUK_CUDA(h, cudaGetDevice(&dev));
+    TEUK_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (int st = 0; st < 2; ++st) {
+      const size_t b = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, st);
+      if (b > (size_t)optin) continue;
+      TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[st], full_ix_kernel<W, V>, (int)(blk.x * blk.y), b) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        occ[st] = 0;
+      }
+    }
+    h->ix_stage = occ[1] > 0 && occ[1] >= occ[0] ? 1 : 0;
+    h->ix_stage_key = key;
+  }
+  IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, h->ix_stage};
+  const size_t ism = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage);
+  {
+    int dev = 0, optin = 0;
+    TEUK_CUDA(h, cudaGetDevice(&dev));
+    TEUK_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (ism > (size_t)optin) {
+      h->last_error = "launch shape: the engine's rows need more shared memory than a block can have";
+      return TEUK_ERR_INVALID_ARG;
+    }
+  }
+  TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+  TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+  cudaEvent_t ev = nullptr;
+  time_begin(h, &ev);
+  half_ix_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+  time_end(h, 0, ev);
+  time_begin(h, &ev);
+  full_ix_kernel<W, V><<<(nf + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+  time_end(h, 1, ev);
+  h->launches += 2;
+  TEUK_CUDA(h, cudaGetLastError());
+  return TEUK_OK;
+}
+
+}  // namespace ixk_wN
+using namespace TEUK_SUFFIX(ixk_w);
+
+int TEUK_SUFFIX(ix_tables_w)(teuk_s* h) { return tables(h); }
+int TEUK_SUFFIX(ix_launch_pair_w)(teuk_s* h, const StepArgs& sa, dim3 blk, int variant) {
+  switch (variant) {
+    case 1: return launch_pair<1>(h, sa, blk);
+    case 2: return launch_pair<2>(h, sa, blk);
+    default: return launch_pair<0>(h, sa, blk);
+  }
+}
+
+// Shared memory of `rows` engine rows without staged tables (launch-shape checks, batches);
+// resident blocks per SM and the cooperative launch of batch_ix_kernel (teuk_batch.cu).
+size_t TEUK_SUFFIX(ix_row_smem_w)(int rows, int gstride) { return ix_smem_bytes<W>(rows, gstride, 0, 0); }
+cudaError_t TEUK_SUFFIX(batch_ix_occupancy_w)(int* per_sm, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(batch_ix_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_ix_kernel<W>, 256, smem);
+  return e;
+}
+cudaError_t TEUK_SUFFIX(batch_ix_launch_w)(const BatchArgs& args, const IxArgs* d_ix, int grid, size_t smem,
+                                           cudaStream_t st) {
+  BatchArgs a = args;
+  const IxArgs* p = d_ix;
+  void* params[] = {&a, &p};
+  return cudaLaunchCooperativeKernel((const void*)batch_ix_kernel<W>, dim3(grid), dim3(256), params, smem, st);
+}
+
+}  // namespace teuk

@@ -826,6 +826,20 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   if (bad) atomicOr(a.status, 1u);
 }
 
+// Arguments of the integer-engine step kernels (teuk_ix.cuh). Planes of the engine's
+// coefficient tables: the eight folded coefficients of the step, with plane 5 (H5 / N5, the
+// factor of the theta operator) replaced by H5 A2 and plane 8 holding H5 A1 cot theta_j.
+constexpr int kIxPlanes = 9;
+
+struct IxArgs {
+  StepArgs a;           // geometry, state, half-step rows, ring, status
+  const uint4* cnm;     // node coefficients [kIxPlanes][kU4][n_r][pitch]: mantissas
+  const int* cne;       //   exponent-sign words [kIxPlanes][n_r][pitch]
+  const uint4* chm;     // half-node coefficients [kIxPlanes][kU4][n_r - 1][pitch]
+  const int* che;
+  int stage;            // 1: each block copies its rows of the tables into shared memory first
+};
+
 // ---- batched execution: many problems of uneven size in one cooperative launch ------------
 struct BatchMember {
   StepArgs a;            // the member's buffers (state updated in place, scratch, tables)

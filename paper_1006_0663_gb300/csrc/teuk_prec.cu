@@ -321,21 +321,8 @@ int engine_impl(teuk_s* h, int engine) {
   }
 #if TEUK_WORDS != 1
   if (!h->ix_m) {
-    constexpr int U = IxT<W>::kU4;
-    const size_t ws = (size_t)h->n_r * h->pitch, hs = (size_t)(h->n_r - 1) * h->pitch;
-    const size_t ncn = (size_t)kIxPlanes * ws, nch = (size_t)kIxPlanes * hs, total = ncn + nch;
-    TEUK_CUDA(h, cudaMalloc(&h->ix_m, total * U * sizeof(uint4)));
-    TEUK_CUDA(h, cudaMalloc(&h->ix_e, total * sizeof(int)));
-    // planes 0..7 from the folded tables, then plane 5 -> (5, 8)
-    ix_table_kernel<W><<<(unsigned)((8 * ws + 255) / 256), 256, 0, h->stream>>>(h->cn, ws, ws, 8 * ws, h->ix_m, h->ix_e);
-    ix_table_kernel<W><<<(unsigned)((8 * hs + 255) / 256), 256, 0, h->stream>>>(h->ch, hs, hs, 8 * hs,
-                                                                               h->ix_m + U * ncn, h->ix_e + ncn);
-    ix_fold_kernel<W><<<(unsigned)((ws + 255) / 256), 256, 0, h->stream>>>(h->ix_m, h->ix_e, ws, h->pitch, h->n_th,
-                                                                          h->lfac);
-    ix_fold_kernel<W><<<(unsigned)((hs + 255) / 256), 256, 0, h->stream>>>(h->ix_m + U * ncn, h->ix_e + ncn, hs,
-                                                                          h->pitch, h->n_th, h->lfac);
-    TEUK_CUDA(h, cudaGetLastError());
-    TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int rc = W == 2 ? ix_tables_w2(h) : ix_tables_w4(h);
+    if (rc != TEUK_OK) return rc;
   }
   h->engine = 1;
   return TEUK_OK;
@@ -393,45 +380,8 @@ template <int V>
 int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
   const int nh = h->n_r - 1, nf = h->n_r - 2;
 #if TEUK_WORDS != 1
-  if (h->engine == 1) {
-    // integer engine: the row family's block shape, shared rows in the engine's format
-    constexpr int U = IxT<W>::kU4;
-    const size_t ncn = (size_t)kIxPlanes * h->n_r * h->pitch;
-    const int gs = h->n_th + 2 * h->radius;
-    const long long key = ((long long)V << 40) | ((long long)blk.x << 20) | blk.y;
-    if (h->ix_stage_key != key) {
-      // stage the table rows in shared memory when that keeps as many blocks per SM resident
-      int occ[2] = {0, 0}, dev = 0, optin = 0;
-      TEUK_CUDA(h, cudaGetDevice(&dev));
-      TEUK_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      for (int st = 0; st < 2; ++st) {
-        const size_t b = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, st);
-        if (b > (size_t)optin) continue;
-        TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[st], full_ix_kernel<W, V>, (int)(blk.x * blk.y), b) !=
-            cudaSuccess) {
-          cudaGetLastError();
-          occ[st] = 0;
-        }
-      }
-      h->ix_stage = occ[1] > 0 && occ[1] >= occ[0] ? 1 : 0;
-      h->ix_stage_key = key;
-    }
-    IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, h->ix_stage};
-    const size_t ism = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage);
-    TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
-    TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
-    cudaEvent_t ev = nullptr;
-    time_begin(h, &ev);
-    half_ix_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
-    time_end(h, 0, ev);
-    time_begin(h, &ev);
-    full_ix_kernel<W, V><<<(nf + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
-    time_end(h, 1, ev);
-    h->launches += 2;
-    TEUK_CUDA(h, cudaGetLastError());
-    return TEUK_OK;
-  }
+  if (h->engine == 1)  // integer engine (teuk_ixk.cu)
+    return W == 2 ? ix_launch_pair_w2(h, sa, blk, V) : ix_launch_pair_w4(h, sa, blk, V);
 #endif
   if (h->kernel_family == 1) {
     const int nseg = (h->n_th + 31) / 32;

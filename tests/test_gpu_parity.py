@@ -309,6 +309,61 @@ def test_batch_matches_individual_bitwise(W):
     b.close()
 
 
+@pytest.mark.parametrize("W", [2, 4])
+def test_batch_engine_matches_individual_bitwise(W):
+    """Members on the integer engine advanced in one cooperative launch (batch_ix_kernel) give
+    exactly the states and waveforms of advancing each alone on the engine; a batch refuses to
+    step once a member changed engine, and members of different engines make no batch."""
+    alone = [_member(W, kw) for kw in BATCH_MEMBERS]
+    batched = [_member(W, kw) for kw in BATCH_MEMBERS]
+    for g in alone + batched:
+        g.set_engine(1)
+    n = 5
+    for g in alone:
+        g.step(n)
+        g.sync()
+    b = teuk.Batch(batched)
+    b.step(n)
+    b.sync()
+    assert b.info()["launches"] == 1
+    for ga, gb in zip(alone, batched):
+        np.testing.assert_array_equal(ga.get_state(), gb.get_state())
+        np.testing.assert_array_equal(ga.read_waveform(), gb.read_waveform())
+    batched[0].set_engine(0)
+    with pytest.raises(teuk.TeukError):
+        b.step(1)
+    b.close()
+    other = _member(W, BATCH_MEMBERS[1])
+    with pytest.raises(teuk.TeukError):
+        teuk.Batch([alone[0], other])
+    for g in alone + batched + [other]:
+        g.close()
+
+
+def test_engine_wide_rows_shapes():
+    """Integer-engine rows of 512 theta cells: shapes whose rows exceed one block's shared
+    memory are refused by teuk_set_launch_shape and skipped by the autotuner, and the tuned
+    handle steps to the same bits as the default shape."""
+    p = small(n_r=41, n_theta=512, substeps=2)
+    g1 = teuk.Teuk(precision=2, **p)
+    g2 = teuk.Teuk(precision=2, **p)
+    for g in (g1, g2):
+        g.set_engine(1)
+        g.set_initial_pulse(8.0, 4.0, 0.8, 0.6, max(abs(p["m"]), abs(p["s"])))
+    with pytest.raises(teuk.TeukError):
+        g1.set_launch_shape(32, 8, 0)
+    g1.tune()
+    sh = g1.launch_shape()
+    assert sh["variant"] in (0, 1, 2) and sh["threads_theta"] * sh["rows_per_block"] <= 256
+    g1.step(3)
+    g2.step(3)
+    g1.sync()
+    g2.sync()
+    np.testing.assert_array_equal(g1.get_state(), g2.get_state())
+    g1.close()
+    g2.close()
+
+
 def test_batch_chunks_of_200_steps():
     alone = [_member(1, kw) for kw in BATCH_MEMBERS[:2]]
     batched = [_member(1, kw) for kw in BATCH_MEMBERS[:2]]
