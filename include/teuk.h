@@ -254,7 +254,8 @@ const char* teuk_last_error(teuk_t h);
 /* Multi-word arithmetic self-test: applies op (0 add, 1 sub, 2 mul, 3 div, 4 sqrt, 5 exp,
  * 6 log, 7 dot-accumulate a*b + out, 8 out[t] + sum_{q<11} a[t+q] b[t+q] (indices mod n) through
  * one accumulator, 9 the same sum through the integer engine, 10 / 11 a + b / a - b through
- * the integer engine; 9..11 for double-double and quad-double)
+ * the integer engine, 12 a / 2 + b through the engine's products by powers of two (a shift
+ * of the other mantissa); 9..12 for double-double and quad-double)
  * elementwise to n values of precision w, on the host (device = 0) or the current CUDA
  * device (device = 1). a, b, out: [w][n] host arrays. */
 int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out,

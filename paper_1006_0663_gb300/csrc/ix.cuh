@@ -319,6 +319,18 @@ MW_HD void acc_prod(Acc& acc, const uint32_t* cm, const uint32_t* vm, uint32_t n
   mul_window(cm, vm, p);
   acc_add(acc, p, neg, r < 0 ? 0 : r);
 }
+// acc += (-1)^neg c v for c a power of two (mantissa 2^126, as made by a constant 2^k): the
+// product window is v's mantissa shifted left by 30, the same bits mul_window gives.
+MW_HD void acc_prod_pow2(Acc& acc, const uint32_t* vm, uint32_t neg, int ep, int maxE) {
+  const int r = maxE + 6 - ep;
+  if (r >= 192) return;
+  uint32_t p[5];
+  p[0] = vm[0] << 30;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) p[k] = fshl(vm[k - 1], vm[k], 30);
+  p[4] = vm[3] >> 2;
+  acc_add(acc, p, neg, r < 0 ? 0 : r);
+}
 // Exponent of the accumulator's bit 0 for the largest product exponent maxE.
 MW_HD int acc_base(int maxE) { return maxE - 26; }
 

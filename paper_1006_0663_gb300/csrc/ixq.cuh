@@ -151,6 +151,18 @@ MW_HD void acc_prod10(Acc10& acc, const uint32_t* cm, const uint32_t* vm, uint32
   mul_window8(cm, vm, p);
   acc_add10(acc, p, neg, r < 0 ? 0 : r);
 }
+// acc += (-1)^neg c v for c a power of two (mantissa 2^254): v's mantissa shifted left by 30,
+// the same bits mul_window8 gives.
+MW_HD void acc_prod_pow2_10(Acc10& acc, const uint32_t* vm, uint32_t neg, int ep, int maxE) {
+  const int r = maxE + 6 - ep;
+  if (r >= 320) return;
+  uint32_t p[9];
+  p[0] = vm[0] << 30;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) p[k] = fshl(vm[k - 1], vm[k], 30);
+  p[8] = vm[7] >> 2;
+  acc_add10(acc, p, neg, r < 0 ? 0 : r);
+}
 // exponent of the accumulator's bit 0 (the largest window's top lands at bit 312)
 MW_HD int acc_base10(int maxE) { return maxE - 26; }
 

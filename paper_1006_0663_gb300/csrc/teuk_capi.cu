@@ -742,7 +742,7 @@ int teuk_fp64_peak(double* ops_per_second) {
 }
 
 int teuk_mw_eval(int op, int words, int device, const double* a, const double* b, double* out, int64_t n) {
-  if (!a || !b || !out || n < 0 || op < 0 || op > 11) return TEUK_ERR_INVALID_ARG;
+  if (!a || !b || !out || n < 0 || op < 0 || op > 12) return TEUK_ERR_INVALID_ARG;
   switch (words) {
     case 1: return teuk::mw_eval_w1(op, device, a, b, out, n);
     case 2: return teuk::mw_eval_w2(op, device, a, b, out, n);

@@ -40,6 +40,9 @@ template <> struct IxT<2> {
   static IXHD void prod(Acc& acc, const uint32_t* cm, const uint32_t* vm, uint32_t neg, int ep, int mx) {
     ix::acc_prod(acc, cm, vm, neg, ep, mx);
   }
+  static IXHD void prod_pow2(Acc& acc, const uint32_t* vm, uint32_t neg, int ep, int mx) {
+    ix::acc_prod_pow2(acc, vm, neg, ep, mx);
+  }
   static IXHD int base(int mx) { return ix::acc_base(mx); }
   static IXHD Num to_num(const Acc& acc, int B) { return ix::to_num(acc, B); }
   static IXHD void to_words(const Acc& acc, int B, double* w) {
@@ -63,6 +66,9 @@ template <> struct IxT<4> {
   static IXHD void zero(Acc& acc) { ix::acc_zero10(acc); }
   static IXHD void prod(Acc& acc, const uint32_t* cm, const uint32_t* vm, uint32_t neg, int ep, int mx) {
     ix::acc_prod10(acc, cm, vm, neg, ep, mx);
+  }
+  static IXHD void prod_pow2(Acc& acc, const uint32_t* vm, uint32_t neg, int ep, int mx) {
+    ix::acc_prod_pow2_10(acc, vm, neg, ep, mx);
   }
   static IXHD int base(int mx) { return ix::acc_base10(mx); }
   static IXHD Num to_num(const Acc& acc, int B) { return ix::to_num8(acc, B); }
@@ -295,8 +301,11 @@ struct IxRow {
   uint4* m;
   int* e;
   uint2* b;
-  int E;  // largest exponent of the row (kZeroE for a row of zeros)
+  int E;     // largest exponent of the row (kZeroE for a row of zeros)
+  uint4* dm; // the differences of the same two rows (Phi_{h+1} - Phi_h), engine numbers at the
+  int* de;   //   row's own columns; exponent word kIxBadEn where an operand was Inf / NaN
 };
+constexpr int kIxBadEn = (int)0x80000000;  // never an exponent-sign word (those are >= -2^25)
 template <int W>
 IXD typename IxT<W>::Num ix_row_get(const IxRow& row, int gstride, int idx) {
   typename IxT<W>::Num r;
@@ -317,6 +326,31 @@ IXD void ix_row_put(const IxRow& row, int gstride, int idx, const typename IxT<W
     row.m[u * gstride + idx] = make_uint4(v.m[4 * u], v.m[4 * u + 1], v.m[4 * u + 2], v.m[4 * u + 3]);
   row.e[idx] = en;
 }
+// Difference at column idx; sets bad where the prep phase met a non-finite operand.
+template <int W>
+IXD typename IxT<W>::Num ix_diff_get(const IxRow& row, int gstride, int idx, uint32_t& bad) {
+  const int en = row.de[idx];
+  if (en == kIxBadEn) {
+    bad = 1;
+    return IxT<W>::zero_num();
+  }
+  typename IxT<W>::Num r;
+#pragma unroll
+  for (int u = 0; u < IxT<W>::kU4; ++u) {
+    const uint4 v = row.dm[u * gstride + idx];
+    r.m[4 * u] = v.x; r.m[4 * u + 1] = v.y; r.m[4 * u + 2] = v.z; r.m[4 * u + 3] = v.w;
+  }
+  r.e = en >> 1;
+  r.neg = (uint32_t)en & 1u;
+  return r;
+}
+template <int W>
+IXD void ix_diff_put(const IxRow& row, int gstride, int idx, const typename IxT<W>::Num& v, uint32_t bad) {
+#pragma unroll
+  for (int u = 0; u < IxT<W>::kU4; ++u)
+    row.dm[u * gstride + idx] = make_uint4(v.m[4 * u], v.m[4 * u + 1], v.m[4 * u + 2], v.m[4 * u + 3]);
+  row.de[idx] = bad ? kIxBadEn : v.e * 2 + (int)v.neg;
+}
 IXHD int imax(int a, int b) { return a > b ? a : b; }
 
 // One term c * v with c from a coefficient table (plane q, index ci), sign flipped if flip.
@@ -334,6 +368,12 @@ IXD void ix_nterm(typename IxT<W>::Acc& acc, const typename IxT<W>::Num& c, cons
 }
 template <int W>
 IXD int ix_texp(int ce, const typename IxT<W>::Num& v) { return IxT<W>::pexp(ce >> 1, v.e); }
+// One term c v with c = 2^k made by ix_pow2 (no multiply: a shift of v's mantissa).
+template <int W>
+IXD void ix_p2term(typename IxT<W>::Acc& acc, const typename IxT<W>::Num& c, const typename IxT<W>::Num& v,
+                   uint32_t flip, int mx) {
+  IxT<W>::prod_pow2(acc, v.m, c.neg ^ v.neg ^ flip, IxT<W>::pexp(c.e, v.e), mx);
+}
 
 template <int W>
 IXD void ix_store(double* p, size_t ws, const typename IxT<W>::Acc& acc, int B, uint32_t bad, double* w) {
@@ -466,11 +506,13 @@ IXD void ix_half_prep(const IxArgs& x, int h, int tx, int TX, const IxRow& sR, c
   for (int j = tx; j < a.g.n_th; j += TX) {
     const size_t i0 = (size_t)h * a.g.pitch + j, i1 = i0 + a.g.pitch;
     uint32_t bad = 0;
-    const auto vR = IxT<W>::add(IxT<W>::load(a.u_in + i1, ws, bad), IxT<W>::load(a.u_in + i0, ws, bad), 0u);
-    const auto vI = IxT<W>::add(IxT<W>::load(a.u_in + W * ws + i1, ws, bad),
-                                IxT<W>::load(a.u_in + W * ws + i0, ws, bad), 0u);
+    const auto r1 = IxT<W>::load(a.u_in + i1, ws, bad), r0 = IxT<W>::load(a.u_in + i0, ws, bad);
+    const auto q1 = IxT<W>::load(a.u_in + W * ws + i1, ws, bad), q0 = IxT<W>::load(a.u_in + W * ws + i0, ws, bad);
+    const auto vR = IxT<W>::add(r1, r0, 0u), vI = IxT<W>::add(q1, q0, 0u);
     ix_row_put<W>(sR, gstride, j + a.radius, vR, ix_en(vR));
     ix_row_put<W>(sI, gstride, j + a.radius, vI, ix_en(vI));
+    ix_diff_put<W>(sR, gstride, j + a.radius, IxT<W>::add(r1, r0, 1u), bad);
+    ix_diff_put<W>(sI, gstride, j + a.radius, IxT<W>::add(q1, q0, 1u), bad);
     eR = imax(eR, vR.e);
     eI = imax(eI, vI.e);
   }
@@ -504,11 +546,10 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   ix_stencil<W>(x, sI, gstride, j, D2I, D1I);
   uint32_t bad = 0;
   const double* u = a.u_in;
-  const Num uPR0 = T::load(u + 0 * W * ws + i0, ws, bad), uPR1 = T::load(u + 0 * W * ws + i1, ws, bad);
-  const Num uPI0 = T::load(u + 1 * W * ws + i0, ws, bad), uPI1 = T::load(u + 1 * W * ws + i1, ws, bad);
   const Num uQR0 = T::load(u + 2 * W * ws + i0, ws, bad), uQR1 = T::load(u + 2 * W * ws + i1, ws, bad);
   const Num uQI0 = T::load(u + 3 * W * ws + i0, ws, bad), uQI1 = T::load(u + 3 * W * ws + i1, ws, bad);
-  const Num dPR = T::add(uPR1, uPR0, 1u), dPI = T::add(uPI1, uPI0, 1u);
+  // Phi_{h+1} - Phi_h from the prep phase
+  const Num dPR = ix_diff_get<W>(sR, gstride, j + rad, bad), dPI = ix_diff_get<W>(sI, gstride, j + rad, bad);
   const Num sQR = T::add(uQR1, uQR0, 0u), sQI = T::add(uQI1, uQI0, 0u);
   // one exact difference and one product are cheaper here than two products, and free the
   // four Pi values early
@@ -526,14 +567,14 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   // Phi_R = s_PhiR/2 - H0 d_PhiR + (h/4) s_PiR
   mx = imax(imax(T::pexp(half.e, sPR.e), TE(0, dPR)), T::pexp(h4.e, sQR.e));
   T::zero(acc);
-  ix_nterm<W>(acc, half, sPR, 0u, mx);
+  ix_p2term<W>(acc, half, sPR, 0u, mx);
   TT(0, dPR, 1u);
   ix_nterm<W>(acc, h4, sQR, 0u, mx);
   ix_store<W>(a.uh + 0 * W * hs + oi, hs, acc, T::base(mx), bad, w);
   // Phi_I
   mx = imax(imax(T::pexp(half.e, sPI.e), TE(0, dPI)), T::pexp(h4.e, sQI.e));
   T::zero(acc);
-  ix_nterm<W>(acc, half, sPI, 0u, mx);
+  ix_p2term<W>(acc, half, sPI, 0u, mx);
   TT(0, dPI, 1u);
   ix_nterm<W>(acc, h4, sQI, 0u, mx);
   ix_store<W>(a.uh + 1 * W * hs + oi, hs, acc, T::base(mx), bad, w);
@@ -565,10 +606,13 @@ IXD void ix_full_prep(const IxArgs& x, int i, int tx, int TX, const IxRow& sR, c
   for (int j = tx; j < a.g.n_th; j += TX) {
     const size_t p = (size_t)i * a.g.pitch + j, m = p - a.g.pitch;
     uint32_t bad = 0;
-    const auto vR = IxT<W>::add(IxT<W>::load(a.uh + p, hs, bad), IxT<W>::load(a.uh + m, hs, bad), 0u);
-    const auto vI = IxT<W>::add(IxT<W>::load(a.uh + W * hs + p, hs, bad), IxT<W>::load(a.uh + W * hs + m, hs, bad), 0u);
+    const auto r1 = IxT<W>::load(a.uh + p, hs, bad), r0 = IxT<W>::load(a.uh + m, hs, bad);
+    const auto q1 = IxT<W>::load(a.uh + W * hs + p, hs, bad), q0 = IxT<W>::load(a.uh + W * hs + m, hs, bad);
+    const auto vR = IxT<W>::add(r1, r0, 0u), vI = IxT<W>::add(q1, q0, 0u);
     ix_row_put<W>(sR, gstride, j + a.radius, vR, ix_en(vR));
     ix_row_put<W>(sI, gstride, j + a.radius, vI, ix_en(vI));
+    ix_diff_put<W>(sR, gstride, j + a.radius, IxT<W>::add(r1, r0, 1u), bad);
+    ix_diff_put<W>(sI, gstride, j + a.radius, IxT<W>::add(q1, q0, 1u), bad);
     eR = imax(eR, vR.e);
     eI = imax(eI, vI.e);
   }
@@ -590,11 +634,10 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   ix_stencil<W>(x, sI, gstride, j, D2I, D1I);
   uint32_t bad = 0;
   const double* uh = a.uh;
-  const Num hPR1 = T::load(uh + 0 * W * hs + p, hs, bad), hPR0 = T::load(uh + 0 * W * hs + m, hs, bad);
-  const Num hPI1 = T::load(uh + 1 * W * hs + p, hs, bad), hPI0 = T::load(uh + 1 * W * hs + m, hs, bad);
   const Num hQR1 = T::load(uh + 2 * W * hs + p, hs, bad), hQR0 = T::load(uh + 2 * W * hs + m, hs, bad);
   const Num hQI1 = T::load(uh + 3 * W * hs + p, hs, bad), hQI0 = T::load(uh + 3 * W * hs + m, hs, bad);
-  const Num dPR = T::add(hPR1, hPR0, 1u), dPI = T::add(hPI1, hPI0, 1u);
+  // h_Phi,i+1/2 - h_Phi,i-1/2 from the prep phase
+  const Num dPR = ix_diff_get<W>(sR, gstride, j + rad, bad), dPI = ix_diff_get<W>(sI, gstride, j + rad, bad);
   const Num sQR = T::add(hQR1, hQR0, 0u), sQI = T::add(hQI1, hQI0, 0u);
   const Num dQR = T::add(hQR1, hQR0, 1u), dQI = T::add(hQI1, hQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
@@ -612,14 +655,14 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   // Phi_R' = Phi_R - N0 d_PhiR + (h/2) s_PiR
   mx = imax(imax(T::pexp(one.e, PR.e), TE(0, dPR)), T::pexp(h2.e, sQR.e));
   T::zero(acc);
-  ix_nterm<W>(acc, one, PR, 0u, mx);
+  ix_p2term<W>(acc, one, PR, 0u, mx);
   TT(0, dPR, 1u);
   ix_nterm<W>(acc, h2, sQR, 0u, mx);
   ix_store<W>(a.u_out + 0 * W * ws + ci, ws, acc, T::base(mx), bad, o0);
   // Phi_I'
   mx = imax(imax(T::pexp(one.e, PI.e), TE(0, dPI)), T::pexp(h2.e, sQI.e));
   T::zero(acc);
-  ix_nterm<W>(acc, one, PI, 0u, mx);
+  ix_p2term<W>(acc, one, PI, 0u, mx);
   TT(0, dPI, 1u);
   ix_nterm<W>(acc, h2, sQI, 0u, mx);
   ix_store<W>(a.u_out + 1 * W * ws + ci, ws, acc, T::base(mx), bad, o1);
@@ -628,7 +671,7 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   mx = imax(imax(imax(T::pexp(one.e, QR.e), TE(8, D1R)), imax(TE(0, dQR), TE(1, dPR))),
             imax(imax(TE(2, dPI), TE(3, sQR)), imax(imax(TE(4, sQI), TE(5, D2R)), imax(TE(6, sPR), TE(7, sPI)))));
   T::zero(acc);
-  ix_nterm<W>(acc, one, QR, 0u, mx);
+  ix_p2term<W>(acc, one, QR, 0u, mx);
   TT(0, dQR, 0u); TT(1, dPR, 0u); TT(2, dPI, 0u); TT(3, sQR, 0u);
   TT(4, sQI, 0u); TT(5, D2R, 0u); TT(8, D1R, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
   ix_store<W>(a.u_out + 2 * W * ws + ci, ws, acc, T::base(mx), bad, w);
@@ -638,7 +681,7 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   mx = imax(imax(imax(T::pexp(one.e, QI.e), TE(8, D1I)), imax(TE(0, dQI), TE(1, dPI))),
             imax(imax(TE(2, dPR), TE(3, sQI)), imax(imax(TE(4, sQR), TE(5, D2I)), imax(TE(6, sPI), TE(7, sPR)))));
   T::zero(acc);
-  ix_nterm<W>(acc, one, QI, 0u, mx);
+  ix_p2term<W>(acc, one, QI, 0u, mx);
   TT(0, dQI, 0u); TT(1, dPI, 0u); TT(2, dPR, 1u); TT(3, sQI, 0u);
   TT(4, sQR, 1u); TT(5, D2I, 0u); TT(8, D1I, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
   ix_store<W>(a.u_out + 3 * W * ws + ci, ws, acc, T::base(mx), bad, w);
@@ -658,7 +701,8 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
 // Shared memory of the engine kernels, for blockDim.y rows: with staging, the block's rows of
 // the coefficient tables first (mantissas [kIxPlanes][kU4][rows][pitch] uint4, exponent-sign
 // words [kIxPlanes][rows][pitch] int); then the value mantissas [rows][2][kU4][gstride]
-// (uint4), their exponent-sign words [rows][2][gstride] (int), the block-floating rows
+// (uint4), the difference mantissas (same shape), the values' and the differences'
+// exponent-sign words [rows][2][gstride] (int) each, the block-floating rows
 // [rows][2][kBlk / 2][gstride] (uint2), the per-warp exponent maxima [rows][16] (int) and the
 // copies' mbarrier.
 struct IxSmem {
@@ -675,13 +719,18 @@ IXD IxSmem ix_rows(int gstride, int pitch, int stage, IxRow& sR, IxRow& sI, int 
   sm.tm = ixsm;
   sm.te = reinterpret_cast<int*>(ixsm + (size_t)kIxPlanes * U * rows * pitch);
   uint4* rbase = stage ? reinterpret_cast<uint4*>(sm.te + (size_t)kIxPlanes * rows * pitch) : ixsm;
-  int* ebase = reinterpret_cast<int*>(rbase + (size_t)rows * 2 * U * gstride);
-  uint2* bbase = reinterpret_cast<uint2*>(ebase + (size_t)rows * 2 * gstride);
+  // values, then differences: mantissas, then exponent-sign words
+  int* ebase = reinterpret_cast<int*>(rbase + (size_t)rows * 2 * U * gstride * 2);
+  uint2* bbase = reinterpret_cast<uint2*>(ebase + (size_t)rows * 2 * gstride * 2);
   int* mbase = reinterpret_cast<int*>(bbase + (size_t)rows * 2 * KB * gstride);
   sR.m = rbase + (size_t)y * 2 * U * gstride;
   sI.m = sR.m + (size_t)U * gstride;
   sR.e = ebase + (size_t)y * 2 * gstride;
   sI.e = sR.e + gstride;
+  sR.dm = rbase + (size_t)rows * 2 * U * gstride + (size_t)y * 2 * U * gstride;
+  sI.dm = sR.dm + (size_t)U * gstride;
+  sR.de = ebase + (size_t)rows * 2 * gstride + (size_t)y * 2 * gstride;
+  sI.de = sR.de + gstride;
   sR.b = bbase + (size_t)y * 2 * KB * gstride;
   sI.b = sR.b + (size_t)KB * gstride;
   sR.E = sI.E = ix::kZeroE;
@@ -694,7 +743,8 @@ template <int W>
 inline size_t ix_smem_bytes(int rows, int gstride, int pitch, int stage) {
   const size_t tab = stage ? (size_t)kIxPlanes * rows * pitch * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int)) : 0;
   return tab +
-         (size_t)rows * 2 * gstride * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int) + IxT<W>::kBlk * sizeof(uint32_t)) +
+         (size_t)rows * 2 * gstride *
+             (2 * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int)) + IxT<W>::kBlk * sizeof(uint32_t)) +
          (size_t)rows * 16 * sizeof(int) + sizeof(uint64_t);
 }
 

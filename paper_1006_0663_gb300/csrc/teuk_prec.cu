@@ -528,7 +528,8 @@ __host__ __device__ R dot11(const double* a, const double* b, const double* out,
 
 // op 9 (double-double and quad-double): the same sum through the integer engine (ix.cuh,
 // ixq.cuh): the 11 products and the initial value as terms of one fixed-point dot product,
-// rounded once. ops 10 / 11: a + b / a - b through the engine's sum of two numbers, then rounded.
+// rounded once. ops 10 / 11: a + b / a - b through the engine's sum of two numbers, then rounded;
+// op 12: a / 2 + b as two products by powers of two.
 #if TEUK_WORDS != 1
 __host__ __device__ R ix_dot11(const double* a, const double* b, const double* out, int64_t n, int64_t t) {
   using T = IxT<W>;
@@ -554,6 +555,17 @@ __host__ __device__ R ix_addsub(int op, const double* a, const double* b, int64_
   using T = IxT<W>;
   uint32_t bad = 0;
   const typename T::Num one = ix_pow2<W>(0);
+  if (op == 12) {  // a / 2 + b: both terms through the power-of-two products
+    const typename T::Num half = ix_pow2<W>(-1), x = T::load(a + t, n, bad), y = T::load(b + t, n, bad);
+    const int ex = T::pexp(half.e, x.e), ey = T::pexp(one.e, y.e), mx = ex > ey ? ex : ey;
+    typename T::Acc acc;
+    T::zero(acc);
+    T::prod_pow2(acc, x.m, x.neg, ex, mx);
+    T::prod_pow2(acc, y.m, y.neg, ey, mx);
+    double w[4] = {0, 0, 0, 0};
+    T::to_words(acc, T::base(mx), w);
+    return from_words<R>(w);
+  }
   const typename T::Num v = T::add(T::load(a + t, n, bad), T::load(b + t, n, bad), op == 11 ? 1u : 0u);
   const int mx = T::pexp(one.e, v.e);
   typename T::Acc acc;

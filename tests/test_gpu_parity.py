@@ -587,7 +587,7 @@ def test_integer_engine_ops_device_matches_host(W):
             x[k] = x[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -54
     a[:, ::17] = 0.0
     b[:, 5::13] = a[:, 5::13]
-    for op in (9, 10, 11):
+    for op in (9, 10, 11, 12):
         h = teuk.mw_eval(op, W, a, b, out=o, device=False)
         d = teuk.mw_eval(op, W, a, b, out=o, device=True)
         np.testing.assert_array_equal(h, d, err_msg=f"op {op}")
@@ -596,8 +596,8 @@ def test_integer_engine_ops_device_matches_host(W):
 @pytest.mark.parametrize("W", [2, 4])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_integer_engine_evolution_parity(oracle_mod, W, case):
-    """Double-double and quad-double through the integer engine (every dot product exact on the
-    integer pipe, rounded once) against the 256-bit oracle, the same cases as the FP64-transform
+    """Double-double and quad-double through the integer engine (every dot product in fixed
+    point on the integer pipe, rounded once) against the 256-bit oracle, the same cases as the FP64-transform
     engine."""
     p = small(**CASES[case])
     g, o = make_pair(oracle_mod, p, W)

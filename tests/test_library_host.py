@@ -259,6 +259,34 @@ def test_integer_engine_dot_cancellation_host(words):
 
 
 @pytest.mark.parametrize("words", [2, 4])
+def test_integer_engine_pow2_products_host(words):
+    """a / 2 + b through the engine's products by powers of two (op 12: the window of 2^k v is
+    v's mantissa shifted, no partial products dropped): the exact value rounded once (to the
+    top 106 / 212 bits); with b = 0 or a = 0 the leading word is exactly a[0] / 2 or b[0]."""
+    mpm.mp.prec = 900
+    rng = np.random.default_rng(70 + words)
+    n = 200
+    a = np.zeros((words, n)); b = np.zeros((words, n))
+    for t in range(n):
+        ea = int(rng.integers(-300, 300))
+        a[:, t] = _rand_expansion(rng, words, ea)
+        b[:, t] = _rand_expansion(rng, words, ea + int(rng.integers(-150, 150)))
+    b[:, :20] = 0.0
+    a[:, 20:40] = 0.0
+    r = teuk.mw_eval(12, words, a, b, device=False)
+    er = -104 if words == 2 else -208
+    for t in range(n):
+        exact = _val(a, t) / 2 + _val(b, t)
+        big = max(abs(_val(a, t)) / 2, abs(_val(b, t)))
+        assert abs(_val(r, t) - exact) <= abs(exact) * mpm.mpf(2) ** er + big * mpm.mpf(2) ** -180, t
+    # the leading word of a single power-of-two term is the operand's, scaled
+    np.testing.assert_array_equal(r[0, :20], a[0, :20] / 2)
+    np.testing.assert_array_equal(r[0, 20:40], b[0, 20:40])
+    with pytest.raises(teuk.TeukError):
+        teuk.mw_eval(12, 1, np.zeros((1, 3)), np.zeros((1, 3)), device=False)
+
+
+@pytest.mark.parametrize("words", [2, 4])
 @pytest.mark.parametrize("op", [10, 11])
 def test_integer_engine_sum_host(op, words):
     """a + b and a - b through the integer engine (the smaller operand cut below the larger's
