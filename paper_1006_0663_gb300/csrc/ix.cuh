@@ -204,7 +204,7 @@ MW_HD void acc_add(Acc& acc, const uint32_t* p, uint32_t neg, int r) {
   // add t or its two's complement (~t + 1)
   const uint32_t mask = 0u - neg;
 #if defined(__CUDA_ARCH__)
-  uint32_t junk;  // only the carry of this first addition is used
+  uint32_t junk;  // only the carry of this first addition is used (the sum itself is dropped)
   asm("add.cc.u32 %6, %7, 0xffffffff;\n\t"
       "addc.cc.u32 %0, %0, %8;\n\taddc.cc.u32 %1, %1, %9;\n\taddc.cc.u32 %2, %2, %10;\n\t"
       "addc.cc.u32 %3, %3, %11;\n\taddc.cc.u32 %4, %4, %12;\n\taddc.u32 %5, %5, %13;"

@@ -530,6 +530,14 @@ IXD void ix_warp_max(int eR, int eI, int tx, int* wmax, bool write = true) {
 }
 
 // Eq. lw1 at half node h, column j (same terms as half_point in teuk_kernels.cuh).
+// The two components share one loop body (own = this component, other = the other one; the
+// signs of the cross terms follow the component): unrolled for double-double, kept as a loop
+// for quad-double, whose unrolled kernels outgrow the instruction caches.
+template <int W>
+struct IxUnroll {
+  static constexpr int n = W == 4 ? 1 : 2;
+};
+
 template <int W>
 IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxRow& sI, int gstride,
                        const typename IxT<W>::Num& half, const typename IxT<W>::Num& h4, const IxTab& tb,
@@ -540,10 +548,6 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   const int pitch = a.g.pitch, rad = a.radius;
   const size_t ws = (size_t)a.g.n_r * pitch, hs = (size_t)(a.g.n_r - 1) * pitch;
   const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
-  // the theta stencils first: only their four results stay live
-  Num D2R, D1R, D2I, D1I;
-  ix_stencil<W>(x, sR, gstride, j, D2R, D1R);
-  ix_stencil<W>(x, sI, gstride, j, D2I, D1I);
   uint32_t bad = 0;
   const double* u = a.u_in;
   const Num uQR0 = T::load(u + 2 * W * ws + i0, ws, bad), uQR1 = T::load(u + 2 * W * ws + i1, ws, bad);
@@ -551,8 +555,7 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   // Phi_{h+1} - Phi_h from the prep phase
   const Num dPR = ix_diff_get<W>(sR, gstride, j + rad, bad), dPI = ix_diff_get<W>(sI, gstride, j + rad, bad);
   const Num sQR = T::add(uQR1, uQR0, 0u), sQI = T::add(uQI1, uQI0, 0u);
-  // one exact difference and one product are cheaper here than two products, and free the
-  // four Pi values early
+  // one exact difference and one product are cheaper here than two products
   const Num dQR = T::add(uQR1, uQR0, 1u), dQI = T::add(uQI1, uQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
   const size_t oi = (size_t)h * pitch + j;  // output index
@@ -561,38 +564,34 @@ IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxR
   for (int q = 0; q < kIxPlanes; ++q) ce[q] = tb.e[q * tb.pp + ci];
 #define TT(q, v, f) ix_tterm<W>(acc, tb.m, tb.pp, q, ci, ce[q], v, f, mx)
 #define TE(q, v) ix_texp<W>(ce[q], v)
-  typename T::Acc acc;
-  int mx;
-  double w[4];
-  // Phi_R = s_PhiR/2 - H0 d_PhiR + (h/4) s_PiR
-  mx = imax(imax(T::pexp(half.e, sPR.e), TE(0, dPR)), T::pexp(h4.e, sQR.e));
-  T::zero(acc);
-  ix_p2term<W>(acc, half, sPR, 0u, mx);
-  TT(0, dPR, 1u);
-  ix_nterm<W>(acc, h4, sQR, 0u, mx);
-  ix_store<W>(a.uh + 0 * W * hs + oi, hs, acc, T::base(mx), bad, w);
-  // Phi_I
-  mx = imax(imax(T::pexp(half.e, sPI.e), TE(0, dPI)), T::pexp(h4.e, sQI.e));
-  T::zero(acc);
-  ix_p2term<W>(acc, half, sPI, 0u, mx);
-  TT(0, dPI, 1u);
-  ix_nterm<W>(acc, h4, sQI, 0u, mx);
-  ix_store<W>(a.uh + 1 * W * hs + oi, hs, acc, T::base(mx), bad, w);
-  // Pi_R = H3 s_PiR + H4 s_PiI + H0 (Pi_R,h+1 - Pi_R,h) + H1 d_PhiR + H2 d_PhiI + H5 L_R + H6 s_PhiR - H7 s_PhiI
-  // with H5 L_R = (H5 A2) D2_R + (H5 A1 cot) D1_R (planes 5 and 8)
-  mx = imax(imax(imax(TE(3, sQR), TE(4, sQI)), imax(TE(0, dQR), TE(8, D1R))),
-            imax(imax(TE(1, dPR), TE(2, dPI)), imax(TE(5, D2R), imax(TE(6, sPR), TE(7, sPI)))));
-  T::zero(acc);
-  TT(3, sQR, 0u); TT(4, sQI, 0u); TT(0, dQR, 0u); TT(1, dPR, 0u);
-  TT(2, dPI, 0u); TT(5, D2R, 0u); TT(8, D1R, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
-  ix_store<W>(a.uh + 2 * W * hs + oi, hs, acc, T::base(mx), bad, w);
-  // Pi_I = H3 s_PiI - H4 s_PiR + H0 (Pi_I,h+1 - Pi_I,h) + H1 d_PhiI - H2 d_PhiR + H5 L_I + H6 s_PhiI + H7 s_PhiR
-  mx = imax(imax(imax(TE(3, sQI), TE(4, sQR)), imax(TE(0, dQI), TE(8, D1I))),
-            imax(imax(TE(1, dPI), TE(2, dPR)), imax(TE(5, D2I), imax(TE(6, sPI), TE(7, sPR)))));
-  T::zero(acc);
-  TT(3, sQI, 0u); TT(4, sQR, 1u); TT(0, dQI, 0u); TT(1, dPI, 0u);
-  TT(2, dPR, 1u); TT(5, D2I, 0u); TT(8, D1I, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
-  ix_store<W>(a.uh + 3 * W * hs + oi, hs, acc, T::base(mx), bad, w);
+#pragma unroll(IxUnroll<W>::n)
+  for (int c = 0; c < 2; ++c) {
+    const bool im = c != 0;
+    const uint32_t fc = (uint32_t)c;
+    Num D2, D1;
+    ix_stencil<W>(x, im ? sI : sR, gstride, j, D2, D1);
+    const Num sPo = im ? sPI : sPR, sPx = im ? sPR : sPI, dPo = im ? dPI : dPR, dPx = im ? dPR : dPI;
+    const Num sQo = im ? sQI : sQR, sQx = im ? sQR : sQI, dQo = im ? dQI : dQR;
+    typename T::Acc acc;
+    int mx;
+    double w[4];
+    // Phi_c = s_Phi_c/2 - H0 d_Phi_c + (h/4) s_Pi_c
+    mx = imax(imax(T::pexp(half.e, sPo.e), TE(0, dPo)), T::pexp(h4.e, sQo.e));
+    T::zero(acc);
+    ix_p2term<W>(acc, half, sPo, 0u, mx);
+    TT(0, dPo, 1u);
+    ix_nterm<W>(acc, h4, sQo, 0u, mx);
+    ix_store<W>(a.uh + c * W * hs + oi, hs, acc, T::base(mx), bad, w);
+    // Pi_R = H3 s_PiR + H4 s_PiI + H0 (Pi_R,h+1 - Pi_R,h) + H1 d_PhiR + H2 d_PhiI + H5 L_R + H6 s_PhiR - H7 s_PhiI
+    // Pi_I = H3 s_PiI - H4 s_PiR + H0 (Pi_I,h+1 - Pi_I,h) + H1 d_PhiI - H2 d_PhiR + H5 L_I + H6 s_PhiI + H7 s_PhiR
+    // with H5 L = (H5 A2) D2 + (H5 A1 cot) D1 (planes 5 and 8)
+    mx = imax(imax(imax(TE(3, sQo), TE(4, sQx)), imax(TE(0, dQo), TE(8, D1))),
+              imax(imax(TE(1, dPo), TE(2, dPx)), imax(TE(5, D2), imax(TE(6, sPo), TE(7, sPx)))));
+    T::zero(acc);
+    TT(3, sQo, 0u); TT(4, sQx, fc); TT(0, dQo, 0u); TT(1, dPo, 0u);
+    TT(2, dPx, fc); TT(5, D2, 0u); TT(8, D1, 0u); TT(6, sPo, 0u); TT(7, sPx, 1u - fc);
+    ix_store<W>(a.uh + (2 + c) * W * hs + oi, hs, acc, T::base(mx), bad, w);
+  }
 #undef TT
 #undef TE
 }
@@ -629,9 +628,6 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   const int pitch = a.g.pitch, rad = a.radius, n_th = a.g.n_th;
   const size_t ws = (size_t)a.g.n_r * pitch, hs = (size_t)(a.g.n_r - 1) * pitch;
   const size_t p = (size_t)i * pitch + j, m = p - pitch;
-  Num D2R, D1R, D2I, D1I;
-  ix_stencil<W>(x, sR, gstride, j, D2R, D1R);
-  ix_stencil<W>(x, sI, gstride, j, D2I, D1I);
   uint32_t bad = 0;
   const double* uh = a.uh;
   const Num hQR1 = T::load(uh + 2 * W * hs + p, hs, bad), hQR0 = T::load(uh + 2 * W * hs + m, hs, bad);
@@ -649,53 +645,47 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
   for (int q = 0; q < kIxPlanes; ++q) ce[q] = tb.e[q * tb.pp + cti];
 #define TT(q, v, f) ix_tterm<W>(acc, tb.m, tb.pp, q, cti, ce[q], v, f, mx)
 #define TE(q, v) ix_texp<W>(ce[q], v)
-  typename T::Acc acc;
-  int mx;
-  double o0[4], o1[4], w[4];
-  // Phi_R' = Phi_R - N0 d_PhiR + (h/2) s_PiR
-  mx = imax(imax(T::pexp(one.e, PR.e), TE(0, dPR)), T::pexp(h2.e, sQR.e));
-  T::zero(acc);
-  ix_p2term<W>(acc, one, PR, 0u, mx);
-  TT(0, dPR, 1u);
-  ix_nterm<W>(acc, h2, sQR, 0u, mx);
-  ix_store<W>(a.u_out + 0 * W * ws + ci, ws, acc, T::base(mx), bad, o0);
-  // Phi_I'
-  mx = imax(imax(T::pexp(one.e, PI.e), TE(0, dPI)), T::pexp(h2.e, sQI.e));
-  T::zero(acc);
-  ix_p2term<W>(acc, one, PI, 0u, mx);
-  TT(0, dPI, 1u);
-  ix_nterm<W>(acc, h2, sQI, 0u, mx);
-  ix_store<W>(a.u_out + 1 * W * ws + ci, ws, acc, T::base(mx), bad, o1);
-  // Pi_R' = Pi_R + N0 (h_PiR,i+1/2 - h_PiR,i-1/2) + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L_R
-  //         + N6 s_PhiR - N7 s_PhiI, with N5 L_R = (N5 A2) D2_R + (N5 A1 cot) D1_R (planes 5 and 8)
-  mx = imax(imax(imax(T::pexp(one.e, QR.e), TE(8, D1R)), imax(TE(0, dQR), TE(1, dPR))),
-            imax(imax(TE(2, dPI), TE(3, sQR)), imax(imax(TE(4, sQI), TE(5, D2R)), imax(TE(6, sPR), TE(7, sPI)))));
-  T::zero(acc);
-  ix_p2term<W>(acc, one, QR, 0u, mx);
-  TT(0, dQR, 0u); TT(1, dPR, 0u); TT(2, dPI, 0u); TT(3, sQR, 0u);
-  TT(4, sQI, 0u); TT(5, D2R, 0u); TT(8, D1R, 0u); TT(6, sPR, 0u); TT(7, sPI, 1u);
-  ix_store<W>(a.u_out + 2 * W * ws + ci, ws, acc, T::base(mx), bad, w);
-  const bool bad2 = nonfinite(w[0]);
-  // Pi_I' = Pi_I + N0 (h_PiI,i+1/2 - h_PiI,i-1/2) + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L_I
-  //         + N6 s_PhiI + N7 s_PhiR
-  mx = imax(imax(imax(T::pexp(one.e, QI.e), TE(8, D1I)), imax(TE(0, dQI), TE(1, dPI))),
-            imax(imax(TE(2, dPR), TE(3, sQI)), imax(imax(TE(4, sQR), TE(5, D2I)), imax(TE(6, sPI), TE(7, sPR)))));
-  T::zero(acc);
-  ix_p2term<W>(acc, one, QI, 0u, mx);
-  TT(0, dQI, 0u); TT(1, dPI, 0u); TT(2, dPR, 1u); TT(3, sQI, 0u);
-  TT(4, sQR, 1u); TT(5, D2I, 0u); TT(8, D1I, 0u); TT(6, sPI, 0u); TT(7, sPR, 0u);
-  ix_store<W>(a.u_out + 3 * W * ws + ci, ws, acc, T::base(mx), bad, w);
+  bool nf = false;
+#pragma unroll(IxUnroll<W>::n)
+  for (int c = 0; c < 2; ++c) {
+    const bool im = c != 0;
+    const uint32_t fc = (uint32_t)c;
+    Num D2, D1;
+    ix_stencil<W>(x, im ? sI : sR, gstride, j, D2, D1);
+    const Num sPo = im ? sPI : sPR, sPx = im ? sPR : sPI, dPo = im ? dPI : dPR, dPx = im ? dPR : dPI;
+    const Num sQo = im ? sQI : sQR, sQx = im ? sQR : sQI, dQo = im ? dQI : dQR;
+    const Num Po = im ? PI : PR, Qo = im ? QI : QR;
+    typename T::Acc acc;
+    int mx;
+    double o[4], w[4];
+    // Phi_c' = Phi_c - N0 d_Phi_c + (h/2) s_Pi_c
+    mx = imax(imax(T::pexp(one.e, Po.e), TE(0, dPo)), T::pexp(h2.e, sQo.e));
+    T::zero(acc);
+    ix_p2term<W>(acc, one, Po, 0u, mx);
+    TT(0, dPo, 1u);
+    ix_nterm<W>(acc, h2, sQo, 0u, mx);
+    ix_store<W>(a.u_out + c * W * ws + ci, ws, acc, T::base(mx), bad, o);
+    if (slot >= 0 && i == a.i_obs && !bad) {  // the observer's sample of Phi_c
+      double* dst = a.ring + (size_t)slot * 2 * W * n_th;
+#pragma unroll
+      for (int k = 0; k < W; ++k) dst[(c * W + k) * n_th + j] = o[k];
+    }
+    // Pi_R' = Pi_R + N0 (h_PiR,i+1/2 - h_PiR,i-1/2) + N1 d_PhiR + N2 d_PhiI + N3 s_PiR + N4 s_PiI + N5 L_R
+    //         + N6 s_PhiR - N7 s_PhiI
+    // Pi_I' = Pi_I + N0 (h_PiI,i+1/2 - h_PiI,i-1/2) + N1 d_PhiI - N2 d_PhiR + N3 s_PiI - N4 s_PiR + N5 L_I
+    //         + N6 s_PhiI + N7 s_PhiR, with N5 L = (N5 A2) D2 + (N5 A1 cot) D1 (planes 5 and 8)
+    mx = imax(imax(imax(T::pexp(one.e, Qo.e), TE(8, D1)), imax(TE(0, dQo), TE(1, dPo))),
+              imax(imax(TE(2, dPx), TE(3, sQo)), imax(imax(TE(4, sQx), TE(5, D2)), imax(TE(6, sPo), TE(7, sPx)))));
+    T::zero(acc);
+    ix_p2term<W>(acc, one, Qo, 0u, mx);
+    TT(0, dQo, 0u); TT(1, dPo, 0u); TT(2, dPx, fc); TT(3, sQo, 0u);
+    TT(4, sQx, fc); TT(5, D2, 0u); TT(8, D1, 0u); TT(6, sPo, 0u); TT(7, sPx, 1u - fc);
+    ix_store<W>(a.u_out + (2 + c) * W * ws + ci, ws, acc, T::base(mx), bad, w);
+    nf = nf || nonfinite(o[0]) || nonfinite(w[0]);
+  }
 #undef TT
 #undef TE
-  if (slot >= 0 && i == a.i_obs && !bad) {
-    double* dst = a.ring + (size_t)slot * 2 * W * n_th;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      dst[k * n_th + j] = o0[k];
-      dst[(W + k) * n_th + j] = o1[k];
-    }
-  }
-  return bad || bad2 || nonfinite(o0[0]) || nonfinite(o1[0]) || nonfinite(w[0]);
+  return bad || nf;
 }
 
 // Shared memory of the engine kernels, for blockDim.y rows: with staging, the block's rows of
