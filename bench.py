@@ -48,18 +48,18 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
            ("c5", "full_kernel<1, 0>"): (1085.83e6 + 247.52e6, "64 x 1", "profiles/step_kernels_f64_c5.txt"),
            ("c3", "half_kernel<4, 0>"): (25.95e6, "32 x 1", "profiles/step_kernels_qd_c3.txt"),
            ("c3", "full_kernel<4, 0>"): (34.35e6, "32 x 1", "profiles/step_kernels_qd_c3.txt"),
-           ("c2", "half_ix_kernel<2, 2>"): (64.06e6 + 3.90e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
-           ("c2", "full_ix_kernel<2, 2>"): (81.18e6 + 6.04e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
-           ("c3", "half_ix_kernel<4, 1>"): (27.08e6 + 0.17e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt"),
-           ("c3", "full_ix_kernel<4, 1>"): (34.83e6 + 1.48e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt")}
+           ("c2", "half_ix_kernel<2, 2>"): (64.05e6 + 2.98e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c2", "full_ix_kernel<2, 2>"): (81.18e6 + 4.11e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c3", "half_ix_kernel<4, 1>"): (27.01e6 + 0.08e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt"),
+           ("c3", "full_ix_kernel<4, 1>"): (34.74e6 + 1.12e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt")}
 
 
 # Integer-engine kernels (double-double): executed thread instructions per grid point for one
 # launch (ncu smsp__inst_executed.sum x smsp__thread_inst_executed_per_inst_executed / points).
-IX_INST = {2: {"half": (4825, "profiles/step_kernels_ix_dd_c2.txt"),
-               "full": (5213, "profiles/step_kernels_ix_dd_c2.txt")},
-           4: {"half": (9683, "profiles/step_kernels_ix_qd_c3.txt"),
-               "full": (10536, "profiles/step_kernels_ix_qd_c3.txt")}}
+IX_INST = {2: {"half": (4898, "profiles/step_kernels_ix_dd_c2.txt"),
+               "full": (5263, "profiles/step_kernels_ix_dd_c2.txt")},
+           4: {"half": (9890, "profiles/step_kernels_ix_qd_c3.txt"),
+               "full": (10922, "profiles/step_kernels_ix_qd_c3.txt")}}
 
 
 def kernel_name(dom, W, shape, engine=0):
