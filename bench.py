@@ -50,16 +50,21 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
            ("c3", "full_kernel<4, 0>"): (34.35e6, "32 x 1", "profiles/step_kernels_qd_c3.txt"),
            ("c2", "half_ix_kernel<2, 2>"): (64.05e6 + 2.98e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
            ("c2", "full_ix_kernel<2, 2>"): (81.18e6 + 4.11e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c2", "half_ix_kernel<2, 1>"): (64.05e6 + 1.56e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c2", "full_ix_kernel<2, 1>"): (81.11e6 + 2.45e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
            ("c3", "half_ix_kernel<4, 1>"): (27.01e6 + 0.08e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt"),
            ("c3", "full_ix_kernel<4, 1>"): (34.74e6 + 1.12e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt")}
 
 
-# Integer-engine kernels (double-double): executed thread instructions per grid point for one
-# launch (ncu smsp__inst_executed.sum x smsp__thread_inst_executed_per_inst_executed / points).
-IX_INST = {2: {"half": (4898, "profiles/step_kernels_ix_dd_c2.txt"),
-               "full": (5263, "profiles/step_kernels_ix_dd_c2.txt")},
-           4: {"half": (9890, "profiles/step_kernels_ix_qd_c3.txt"),
-               "full": (10922, "profiles/step_kernels_ix_qd_c3.txt")}}
+# Integer-engine kernels: executed thread instructions per grid point for one launch (ncu
+# thread_inst_executed / points), per kernel function (the register budgets differ in spill
+# code) from one capture of the kernel as it stands.
+IX_INST = {"half_ix_kernel<2, 2>": (4898, "profiles/step_kernels_ix_dd_c2.txt"),
+           "full_ix_kernel<2, 2>": (5263, "profiles/step_kernels_ix_dd_c2.txt"),
+           "half_ix_kernel<2, 1>": (4736, "profiles/step_kernels_ix_dd_c2.txt"),
+           "full_ix_kernel<2, 1>": (5140, "profiles/step_kernels_ix_dd_c2.txt"),
+           "half_ix_kernel<4, 1>": (9890, "profiles/step_kernels_ix_qd_c3.txt"),
+           "full_ix_kernel<4, 1>": (10922, "profiles/step_kernels_ix_qd_c3.txt")}
 
 
 def kernel_name(dom, W, shape, engine=0):
@@ -361,7 +366,7 @@ def roofline_for(res, prob, W, engine, clocks, sms, probe, workload):
     kname = kernel_name(dom, W, res["rows_per_block"], engine)
     tr = TRAFFIC.get((workload, kname))
     if engine == 1:
-        ops_pt, ops_src = IX_INST[W].get(dom, (None, "not captured"))
+        ops_pt, ops_src = IX_INST.get(kname, (None, "not captured"))
         peak = 128.0 * sms * mhz * 1e6
         peak_source = f"4 warp instructions/SM/cycle x 32 threads x {sms} SMs x {mhz:.0f} MHz (issue limit)"
         op_unit = f"executed thread instructions per point, ncu capture ({ops_src})"
