@@ -212,6 +212,7 @@ MW_HD void acc_add(Acc& acc, const uint32_t* p, uint32_t neg, int r) {
         "=r"(junk)
       : "r"(neg), "r"(t[0] ^ mask), "r"(t[1] ^ mask), "r"(t[2] ^ mask), "r"(t[3] ^ mask), "r"(t[4] ^ mask),
         "r"(t[5] ^ mask));
+  (void)junk;
 #else
   uint64_t c = neg;
   for (int k = 0; k < 6; ++k) {

@@ -128,6 +128,16 @@ struct IxTab {
   const int* e;
   size_t pp;
 };
+// Where a point reads the state: q = Pi_R (component 2), word 0, at the lower of its two rows
+// and the point's column (components W * qw apart, words qw, rows pitch); u (full step only)
+// = component 0, word 0 of the state at the point's node (components W * uw apart). Global
+// memory, or the block's copies of those rows in shared memory.
+struct IxSt {
+  const double* q;
+  size_t qw;
+  const double* u;
+  size_t uw;
+};
 
 template <class N>
 __host__ __device__ __forceinline__ int ix_en(const N& x) { return x.e * 2 + (int)x.neg; }
@@ -541,17 +551,15 @@ struct IxUnroll {
 template <int W>
 IXD void ix_half_point(const IxArgs& x, int h, int j, const IxRow& sR, const IxRow& sI, int gstride,
                        const typename IxT<W>::Num& half, const typename IxT<W>::Num& h4, const IxTab& tb,
-                       size_t ci) {
+                       size_t ci, const IxSt& st) {
   using T = IxT<W>;
   using Num = typename T::Num;
   const StepArgs& a = x.a;
   const int pitch = a.g.pitch, rad = a.radius;
-  const size_t ws = (size_t)a.g.n_r * pitch, hs = (size_t)(a.g.n_r - 1) * pitch;
-  const size_t i0 = (size_t)h * pitch + j, i1 = i0 + pitch;
+  const size_t hs = (size_t)(a.g.n_r - 1) * pitch;
   uint32_t bad = 0;
-  const double* u = a.u_in;
-  const Num uQR0 = T::load(u + 2 * W * ws + i0, ws, bad), uQR1 = T::load(u + 2 * W * ws + i1, ws, bad);
-  const Num uQI0 = T::load(u + 3 * W * ws + i0, ws, bad), uQI1 = T::load(u + 3 * W * ws + i1, ws, bad);
+  const Num uQR0 = T::load(st.q, st.qw, bad), uQR1 = T::load(st.q + pitch, st.qw, bad);
+  const Num uQI0 = T::load(st.q + W * st.qw, st.qw, bad), uQI1 = T::load(st.q + W * st.qw + pitch, st.qw, bad);
   // Phi_{h+1} - Phi_h from the prep phase
   const Num dPR = ix_diff_get<W>(sR, gstride, j + rad, bad), dPI = ix_diff_get<W>(sI, gstride, j + rad, bad);
   const Num sQR = T::add(uQR1, uQR0, 0u), sQI = T::add(uQI1, uQI0, 0u);
@@ -621,25 +629,24 @@ IXD void ix_full_prep(const IxArgs& x, int i, int tx, int TX, const IxRow& sR, c
 template <int W>
 IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxRow& sI, int gstride,
                        const typename IxT<W>::Num& one, const typename IxT<W>::Num& h2, long long slot,
-                       const IxTab& tb, size_t cti) {
+                       const IxTab& tb, size_t cti, const IxSt& st) {
   using T = IxT<W>;
   using Num = typename T::Num;
   const StepArgs& a = x.a;
   const int pitch = a.g.pitch, rad = a.radius, n_th = a.g.n_th;
-  const size_t ws = (size_t)a.g.n_r * pitch, hs = (size_t)(a.g.n_r - 1) * pitch;
-  const size_t p = (size_t)i * pitch + j, m = p - pitch;
+  const size_t ws = (size_t)a.g.n_r * pitch;
   uint32_t bad = 0;
-  const double* uh = a.uh;
-  const Num hQR1 = T::load(uh + 2 * W * hs + p, hs, bad), hQR0 = T::load(uh + 2 * W * hs + m, hs, bad);
-  const Num hQI1 = T::load(uh + 3 * W * hs + p, hs, bad), hQI0 = T::load(uh + 3 * W * hs + m, hs, bad);
+  // half-step Pi rows i - 1/2 (q) and i + 1/2 (q + pitch)
+  const Num hQR0 = T::load(st.q, st.qw, bad), hQR1 = T::load(st.q + pitch, st.qw, bad);
+  const Num hQI0 = T::load(st.q + W * st.qw, st.qw, bad), hQI1 = T::load(st.q + W * st.qw + pitch, st.qw, bad);
   // h_Phi,i+1/2 - h_Phi,i-1/2 from the prep phase
   const Num dPR = ix_diff_get<W>(sR, gstride, j + rad, bad), dPI = ix_diff_get<W>(sI, gstride, j + rad, bad);
   const Num sQR = T::add(hQR1, hQR0, 0u), sQI = T::add(hQI1, hQI0, 0u);
   const Num dQR = T::add(hQR1, hQR0, 1u), dQI = T::add(hQI1, hQI0, 1u);
   const Num sPR = ix_row_get<W>(sR, gstride, j + rad), sPI = ix_row_get<W>(sI, gstride, j + rad);
   const size_t ci = (size_t)i * pitch + j;
-  const Num PR = T::load(a.u_in + 0 * W * ws + ci, ws, bad), PI = T::load(a.u_in + 1 * W * ws + ci, ws, bad);
-  const Num QR = T::load(a.u_in + 2 * W * ws + ci, ws, bad), QI = T::load(a.u_in + 3 * W * ws + ci, ws, bad);
+  const Num PR = T::load(st.u, st.uw, bad), PI = T::load(st.u + W * st.uw, st.uw, bad);
+  const Num QR = T::load(st.u + 2 * W * st.uw, st.uw, bad), QI = T::load(st.u + 3 * W * st.uw, st.uw, bad);
   int ce[kIxPlanes];
 #pragma unroll
   for (int q = 0; q < kIxPlanes; ++q) ce[q] = tb.e[q * tb.pp + cti];
@@ -698,17 +705,28 @@ IXD bool ix_full_point(const IxArgs& x, int i, int j, const IxRow& sR, const IxR
 struct IxSmem {
   uint4* tm;
   int* te;
+  double* st;  // staged state rows (stage bit 2)
   int* wmax;
   uint64_t* bar;
 };
+// Doubles of staged state rows for `rows` rows: the half step's Pi rows h0 .. h0 + rows
+// ([2][W][rows + 1][pitch]); the full step's half-step Pi rows i0 - 1 .. i0 + rows - 1 (same
+// shape) and its state rows i0 .. i0 + rows - 1 ([4][W][rows][pitch]).
 template <int W>
-IXD IxSmem ix_rows(int gstride, int pitch, int stage, IxRow& sR, IxRow& sI, int rows, int y) {
+IXHD size_t ix_state_doubles(int rows, int pitch, bool full) {
+  return (size_t)2 * W * (rows + 1) * pitch + (full ? (size_t)4 * W * rows * pitch : 0);
+}
+template <int W>
+IXD IxSmem ix_rows(int gstride, int pitch, int stage, IxRow& sR, IxRow& sI, int rows, int y, bool full) {
   extern __shared__ uint4 ixsm[];
   constexpr int U = IxT<W>::kU4, KB = IxT<W>::kBlk / 2;
   IxSmem sm;
   sm.tm = ixsm;
   sm.te = reinterpret_cast<int*>(ixsm + (size_t)kIxPlanes * U * rows * pitch);
-  uint4* rbase = stage ? reinterpret_cast<uint4*>(sm.te + (size_t)kIxPlanes * rows * pitch) : ixsm;
+  sm.st = reinterpret_cast<double*>(sm.te + (size_t)kIxPlanes * rows * pitch);
+  uint4* rbase = (stage & 2) ? reinterpret_cast<uint4*>(sm.st + ix_state_doubles<W>(rows, pitch, full))
+                 : (stage & 1) ? reinterpret_cast<uint4*>(sm.st)
+                               : ixsm;
   // values, then differences: mantissas, then exponent-sign words
   int* ebase = reinterpret_cast<int*>(rbase + (size_t)rows * 2 * U * gstride * 2);
   uint2* bbase = reinterpret_cast<uint2*>(ebase + (size_t)rows * 2 * gstride * 2);
@@ -728,11 +746,13 @@ IXD IxSmem ix_rows(int gstride, int pitch, int stage, IxRow& sR, IxRow& sI, int 
   sm.bar = reinterpret_cast<uint64_t*>(mbase + 16 * rows);
   return sm;
 }
-// Bytes of shared memory for `rows` rows of gstride columns (with the table rows if stage).
+// Bytes of shared memory for `rows` rows of gstride columns (stage bit 1: with the table
+// rows; bit 2: also the state rows, which only go with the table rows).
 template <int W>
-inline size_t ix_smem_bytes(int rows, int gstride, int pitch, int stage) {
+inline size_t ix_smem_bytes(int rows, int gstride, int pitch, int stage, bool full) {
   const size_t tab = stage ? (size_t)kIxPlanes * rows * pitch * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int)) : 0;
-  return tab +
+  const size_t sta = (stage & 2) ? ix_state_doubles<W>(rows, pitch, full) * sizeof(double) : 0;
+  return tab + sta +
          (size_t)rows * 2 * gstride *
              (2 * (IxT<W>::kU4 * sizeof(uint4) + sizeof(int)) + IxT<W>::kBlk * sizeof(uint32_t)) +
          (size_t)rows * 16 * sizeof(int) + sizeof(uint64_t);
@@ -741,31 +761,46 @@ inline size_t ix_smem_bytes(int rows, int gstride, int pitch, int stage) {
 // One thread of the block starts the copies of the block's table rows r0 .. r0 + nv - 1
 // (planes of per_plane values at row pitch `pitch`; 16-byte aligned since pitch is a multiple
 // of 16) into shared memory.
+// With stage bit 2 also the state rows: Pi rows q0 .. q0 + nv of qsrc (planes qs doubles
+// apart) into [2][W][rows + 1][pitch], and (full step, usrc != null) rows r0 .. r0 + nv - 1
+// of all four components of usrc (planes us apart) into [4][W][rows][pitch] after them.
 template <int W>
-IXD void ix_stage_tables(const IxSmem& sm, const uint4* gm, const int* ge, size_t per_plane, int pitch, int r0,
-                         int nv) {
+IXD void ix_stage(const IxSmem& sm, int stage, const uint4* gm, const int* ge, size_t per_plane, int pitch, int r0,
+                  int nv, const double* qsrc, size_t qs, int q0, const double* usrc, size_t us) {
   constexpr int U = IxT<W>::kU4;
   const int rows = blockDim.y;
   const uint32_t mb = (uint32_t)nv * pitch * sizeof(uint4), eb = (uint32_t)nv * pitch * sizeof(int);
+  const uint32_t qb = (uint32_t)(nv + 1) * pitch * sizeof(double), ub = (uint32_t)nv * pitch * sizeof(double);
+  uint32_t bytes = kIxPlanes * (U * mb + eb);
+  if (stage & 2) bytes += 2 * W * qb + (usrc ? 4 * W * ub : 0);
   ix_bar_init(sm.bar);
-  ix_bar_expect(sm.bar, kIxPlanes * (U * mb + eb));
+  ix_bar_expect(sm.bar, bytes);
   for (int q = 0; q < kIxPlanes; ++q) {
     for (int u = 0; u < U; ++u)
       ix_bulk_copy(sm.tm + ((size_t)(q * U + u) * rows) * pitch, gm + (q * U + u) * per_plane + (size_t)r0 * pitch,
                    mb, sm.bar);
     ix_bulk_copy(sm.te + (size_t)q * rows * pitch, ge + q * per_plane + (size_t)r0 * pitch, eb, sm.bar);
   }
+  if (!(stage & 2)) return;
+  for (int k = 0; k < 2 * W; ++k)  // components 2, 3: planes 2 W .. 4 W - 1
+    ix_bulk_copy(sm.st + (size_t)k * (rows + 1) * pitch, qsrc + (size_t)(2 * W + k) * qs + (size_t)q0 * pitch, qb,
+                 sm.bar);
+  if (!usrc) return;
+  double* ud = sm.st + (size_t)2 * W * (rows + 1) * pitch;
+  for (int k = 0; k < 4 * W; ++k)
+    ix_bulk_copy(ud + (size_t)k * rows * pitch, usrc + (size_t)k * us + (size_t)r0 * pitch, ub, sm.bar);
 }
 
 template <int W, int V>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) half_ix_kernel(IxArgs x) {
   const int gstride = x.a.g.n_th + 2 * x.a.radius, pitch = x.a.g.pitch, nh = x.a.g.n_r - 1;
-  const size_t hs = (size_t)nh * pitch;
+  const size_t hs = (size_t)nh * pitch, ws = (size_t)x.a.g.n_r * pitch;
   IxRow sR, sI;
-  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI, blockDim.y, threadIdx.y);
+  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI, blockDim.y, threadIdx.y, false);
   const int h0 = blockIdx.x * blockDim.y, h = h0 + threadIdx.y;
   if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
-    ix_stage_tables<W>(sm, x.chm, x.che, hs, pitch, h0, min((int)blockDim.y, nh - h0));
+    ix_stage<W>(sm, x.stage, x.chm, x.che, hs, pitch, h0, min((int)blockDim.y, nh - h0), x.a.u_in, ws, h0, nullptr,
+                0);
   const bool ok = h < nh;
   int eR = ix::kZeroE, eI = ix::kZeroE;
   if (ok) ix_half_prep<W>(x, h, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
@@ -776,6 +811,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) h
   if (!ok) return;
   IxTab tb{x.chm, x.che, hs};
   size_t base = (size_t)h * pitch;
+  IxSt st{x.a.u_in + 2 * W * ws + (size_t)h * pitch, ws, nullptr, 0};
   if (x.stage) {
     if (!ix_bar_wait(sm.bar)) {
       atomicOr(x.a.status, 2u);
@@ -783,23 +819,25 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) h
     }
     tb = IxTab{sm.tm, sm.te, (size_t)blockDim.y * pitch};
     base = (size_t)threadIdx.y * pitch;
+    if (x.stage & 2) st = IxSt{sm.st + (size_t)threadIdx.y * pitch, (size_t)(blockDim.y + 1) * pitch, nullptr, 0};
   }
   uint32_t bad = 0;
   const auto half = ix_pow2<W>(-1);
   const auto h4 = IxT<W>::load(x.a.h4, 1, bad);
   for (int j = threadIdx.x; j < x.a.g.n_th; j += blockDim.x)
-    ix_half_point<W>(x, h, j, sR, sI, gstride, half, h4, tb, base + j);
+    ix_half_point<W>(x, h, j, sR, sI, gstride, half, h4, tb, base + j, IxSt{st.q + j, st.qw, nullptr, 0});
 }
 
 template <int W, int V>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) full_ix_kernel(IxArgs x) {
   const int gstride = x.a.g.n_th + 2 * x.a.radius, pitch = x.a.g.pitch, n_r = x.a.g.n_r;
-  const size_t ws = (size_t)n_r * pitch;
+  const size_t ws = (size_t)n_r * pitch, hs = (size_t)(n_r - 1) * pitch;
   IxRow sR, sI;
-  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI, blockDim.y, threadIdx.y);
+  const IxSmem sm = ix_rows<W>(gstride, pitch, x.stage, sR, sI, blockDim.y, threadIdx.y, true);
   const int i0 = 1 + blockIdx.x * blockDim.y, i = i0 + threadIdx.y;
   if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
-    ix_stage_tables<W>(sm, x.cnm, x.cne, ws, pitch, i0, min((int)blockDim.y, n_r - 1 - i0));
+    ix_stage<W>(sm, x.stage, x.cnm, x.cne, ws, pitch, i0, min((int)blockDim.y, n_r - 1 - i0), x.a.uh, hs, i0 - 1,
+                x.a.u_in, ws);
   const bool ok = i < n_r - 1;
   int eR = ix::kZeroE, eI = ix::kZeroE;
   if (ok) ix_full_prep<W>(x, i, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
@@ -810,6 +848,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   if (!ok) return;
   IxTab tb{x.cnm, x.cne, ws};
   size_t base = (size_t)i * pitch;
+  IxSt st{x.a.uh + 2 * W * hs + (size_t)(i - 1) * pitch, hs, x.a.u_in + (size_t)i * pitch, ws};
   if (x.stage) {
     if (!ix_bar_wait(sm.bar)) {
       atomicOr(x.a.status, 2u);
@@ -817,6 +856,11 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
     }
     tb = IxTab{sm.tm, sm.te, (size_t)blockDim.y * pitch};
     base = (size_t)threadIdx.y * pitch;
+    if (x.stage & 2) {
+      const size_t qw = (size_t)(blockDim.y + 1) * pitch;
+      st = IxSt{sm.st + (size_t)threadIdx.y * pitch, qw, sm.st + 2 * W * qw + (size_t)threadIdx.y * pitch,
+                (size_t)blockDim.y * pitch};
+    }
   }
   uint32_t bad = 0;
   const auto one = ix_pow2<W>(0);
@@ -825,7 +869,8 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   if (x.a.record) slot = x.a.ring_slot >= 0 ? x.a.ring_slot : (*x.a.ring_counter) % x.a.ring_cap;
   bool anybad = false;
   for (int j = threadIdx.x; j < x.a.g.n_th; j += blockDim.x)
-    anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot, tb, base + j);
+    anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot, tb, base + j,
+                               IxSt{st.q + j, st.qw, st.u + j, st.uw});
   if (anybad) atomicOr(x.a.status, 1u);
 }
 
@@ -847,10 +892,11 @@ __global__ void __launch_bounds__(256, 2) batch_ix_kernel(BatchArgs b, const IxA
         const int tx = threadIdx.x % M.tx, ty = threadIdx.x / M.tx;
         const bool row = ty < M.rows;
         const int h = (it - M.item_begin) * M.rows + ty, nh = M.a.g.n_r - 1, pitch = M.a.g.pitch;
+        const size_t ws = (size_t)M.a.g.n_r * pitch;
         const bool ok = row && h < nh;
         const int gstride = M.a.g.n_th + 2 * M.a.radius;
         IxRow sR, sI;
-        const IxSmem sm = ix_rows<W>(gstride, pitch, 0, sR, sI, M.rows, row ? ty : 0);
+        const IxSmem sm = ix_rows<W>(gstride, pitch, 0, sR, sI, M.rows, row ? ty : 0, false);
         int eR = ix::kZeroE, eI = ix::kZeroE;
         if (ok) ix_half_prep<W>(x, h, tx, M.tx, sR, sI, gstride, eR, eI);
         ix_warp_max(eR, eI, tx, sm.wmax, row);
@@ -863,7 +909,8 @@ __global__ void __launch_bounds__(256, 2) batch_ix_kernel(BatchArgs b, const IxA
           const auto h4 = IxT<W>::load(M.a.h4, 1, bad);
           const IxTab tb{x.chm, x.che, (size_t)nh * pitch};
           for (int j = tx; j < M.a.g.n_th; j += M.tx)
-            ix_half_point<W>(x, h, j, sR, sI, gstride, half, h4, tb, (size_t)h * pitch + j);
+            ix_half_point<W>(x, h, j, sR, sI, gstride, half, h4, tb, (size_t)h * pitch + j,
+                             IxSt{M.a.u_in + 2 * W * ws + (size_t)h * pitch + j, ws, nullptr, 0});
         }
         __syncthreads();
       }
@@ -875,10 +922,11 @@ __global__ void __launch_bounds__(256, 2) batch_ix_kernel(BatchArgs b, const IxA
         const int tx = threadIdx.x % M.tx, ty = threadIdx.x / M.tx;
         const bool row = ty < M.rows;
         const int i = 1 + (it - M.item_begin) * M.rows + ty, n_r = M.a.g.n_r, pitch = M.a.g.pitch;
+        const size_t ws = (size_t)n_r * pitch, hs = (size_t)(n_r - 1) * pitch;
         const bool ok = row && i < n_r - 1;
         const int gstride = M.a.g.n_th + 2 * M.a.radius;
         IxRow sR, sI;
-        const IxSmem sm = ix_rows<W>(gstride, pitch, 0, sR, sI, M.rows, row ? ty : 0);
+        const IxSmem sm = ix_rows<W>(gstride, pitch, 0, sR, sI, M.rows, row ? ty : 0, true);
         int eR = ix::kZeroE, eI = ix::kZeroE;
         if (ok) ix_full_prep<W>(x, i, tx, M.tx, sR, sI, gstride, eR, eI);
         ix_warp_max(eR, eI, tx, sm.wmax, row);
@@ -893,7 +941,9 @@ __global__ void __launch_bounds__(256, 2) batch_ix_kernel(BatchArgs b, const IxA
           const IxTab tb{x.cnm, x.cne, (size_t)n_r * pitch};
           bool anybad = false;
           for (int j = tx; j < M.a.g.n_th; j += M.tx)
-            anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot, tb, (size_t)i * pitch + j);
+            anybad |= ix_full_point<W>(x, i, j, sR, sI, gstride, one, h2, slot, tb, (size_t)i * pitch + j,
+                                       IxSt{M.a.uh + 2 * W * hs + (size_t)(i - 1) * pitch + j, hs,
+                                            M.a.u_in + (size_t)i * pitch + j, ws});
           if (anybad) atomicOr(M.a.status, 1u);
         }
         __syncthreads();

@@ -50,42 +50,47 @@ int launch_pair(teuk_s* h, const StepArgs& sa, dim3 blk) {
   const int gs = h->n_th + 2 * h->radius;
   const long long key = ((long long)V << 40) | ((long long)blk.x << 20) | blk.y;
   if (h->ix_stage_key != key) {
-    // stage the table rows in shared memory when that keeps as many blocks per SM resident
-    int occ[2] = {0, 0}, dev = 0, optin = 0;
+    // stage in shared memory as much as keeps as many blocks per SM resident: nothing (0), the
+    // table rows (1), the table and state rows (3); the full step's footprint is the larger
+    const int opts[3] = {0, 1, 3};
+    int occ[3] = {0, 0, 0}, dev = 0, optin = 0;
     TEUK_CUDA(h, cudaGetDevice(&dev));
     TEUK_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    for (int st = 0; st < 2; ++st) {
-      const size_t b = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, st);
+    for (int k = 0; k < 3; ++k) {
+      const size_t b = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, opts[k], true);
       if (b > (size_t)optin) continue;
       TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[st], full_ix_kernel<W, V>, (int)(blk.x * blk.y), b) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[k], full_ix_kernel<W, V>, (int)(blk.x * blk.y), b) !=
           cudaSuccess) {
         cudaGetLastError();
-        occ[st] = 0;
+        occ[k] = 0;
       }
     }
-    h->ix_stage = occ[1] > 0 && occ[1] >= occ[0] ? 1 : 0;
+    h->ix_stage = 0;
+    for (int k = 1; k < 3; ++k)
+      if (occ[k] > 0 && occ[k] >= occ[0]) h->ix_stage = opts[k];
     h->ix_stage_key = key;
   }
   IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, h->ix_stage};
-  const size_t ism = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage);
+  const size_t ism_h = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage, false);
+  const size_t ism_f = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage, true);
   {
     int dev = 0, optin = 0;
     TEUK_CUDA(h, cudaGetDevice(&dev));
     TEUK_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (ism > (size_t)optin) {
+    if (ism_f > (size_t)optin) {
       h->last_error = "launch shape: the engine's rows need more shared memory than a block can have";
       return TEUK_ERR_INVALID_ARG;
     }
   }
-  TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
-  TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+  TEUK_CUDA(h, cudaFuncSetAttribute(half_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism_h));
+  TEUK_CUDA(h, cudaFuncSetAttribute(full_ix_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism_f));
   cudaEvent_t ev = nullptr;
   time_begin(h, &ev);
-  half_ix_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+  half_ix_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, ism_h, h->stream>>>(x);
   time_end(h, 0, ev);
   time_begin(h, &ev);
-  full_ix_kernel<W, V><<<(nf + blk.y - 1) / blk.y, blk, ism, h->stream>>>(x);
+  full_ix_kernel<W, V><<<(nf + blk.y - 1) / blk.y, blk, ism_f, h->stream>>>(x);
   time_end(h, 1, ev);
   h->launches += 2;
   TEUK_CUDA(h, cudaGetLastError());
@@ -106,7 +111,7 @@ int TEUK_SUFFIX(ix_launch_pair_w)(teuk_s* h, const StepArgs& sa, dim3 blk, int v
 
 // Shared memory of `rows` engine rows without staged tables (launch-shape checks, batches);
 // resident blocks per SM and the cooperative launch of batch_ix_kernel (teuk_batch.cu).
-size_t TEUK_SUFFIX(ix_row_smem_w)(int rows, int gstride) { return ix_smem_bytes<W>(rows, gstride, 0, 0); }
+size_t TEUK_SUFFIX(ix_row_smem_w)(int rows, int gstride) { return ix_smem_bytes<W>(rows, gstride, 0, 0, true); }
 cudaError_t TEUK_SUFFIX(batch_ix_occupancy_w)(int* per_sm, size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(batch_ix_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_ix_kernel<W>, 256, smem);
