@@ -48,23 +48,23 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
            ("c5", "full_kernel<1, 0>"): (1085.83e6 + 247.52e6, "64 x 1", "profiles/step_kernels_f64_c5.txt"),
            ("c3", "half_kernel<4, 0>"): (25.95e6, "32 x 1", "profiles/step_kernels_qd_c3.txt"),
            ("c3", "full_kernel<4, 0>"): (34.35e6, "32 x 1", "profiles/step_kernels_qd_c3.txt"),
-           ("c2", "half_ix_kernel<2, 2>"): (64.05e6 + 2.98e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
-           ("c2", "full_ix_kernel<2, 2>"): (81.18e6 + 4.11e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
-           ("c2", "half_ix_kernel<2, 1>"): (64.05e6 + 1.56e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
-           ("c2", "full_ix_kernel<2, 1>"): (81.11e6 + 2.45e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
-           ("c3", "half_ix_kernel<4, 1>"): (27.01e6 + 0.08e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt"),
-           ("c3", "full_ix_kernel<4, 1>"): (34.74e6 + 1.12e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt")}
+           ("c2", "half_ix_kernel<2, 2>"): (64.06e6 + 3.03e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c2", "full_ix_kernel<2, 2>"): (81.19e6 + 4.94e6, "128 x 1", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c2", "half_ix_kernel<2, 1>"): (64.05e6 + 1.68e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c2", "full_ix_kernel<2, 1>"): (81.10e6 + 2.65e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
+           ("c3", "half_ix_kernel<4, 1>"): (27.01e6 + 0.12e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt"),
+           ("c3", "full_ix_kernel<4, 1>"): (34.75e6 + 1.38e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt")}
 
 
 # Integer-engine kernels: executed thread instructions per grid point for one launch (ncu
 # thread_inst_executed / points), per kernel function (the register budgets differ in spill
 # code) from one capture of the kernel as it stands.
-IX_INST = {"half_ix_kernel<2, 2>": (4898, "profiles/step_kernels_ix_dd_c2.txt"),
-           "full_ix_kernel<2, 2>": (5263, "profiles/step_kernels_ix_dd_c2.txt"),
-           "half_ix_kernel<2, 1>": (4736, "profiles/step_kernels_ix_dd_c2.txt"),
-           "full_ix_kernel<2, 1>": (5140, "profiles/step_kernels_ix_dd_c2.txt"),
-           "half_ix_kernel<4, 1>": (9890, "profiles/step_kernels_ix_qd_c3.txt"),
-           "full_ix_kernel<4, 1>": (10922, "profiles/step_kernels_ix_qd_c3.txt")}
+IX_INST = {"half_ix_kernel<2, 2>": (4904, "profiles/step_kernels_ix_dd_c2.txt"),
+           "full_ix_kernel<2, 2>": (5289, "profiles/step_kernels_ix_dd_c2.txt"),
+           "half_ix_kernel<2, 1>": (4665, "profiles/step_kernels_ix_dd_c2.txt"),
+           "full_ix_kernel<2, 1>": (5198, "profiles/step_kernels_ix_dd_c2.txt"),
+           "half_ix_kernel<4, 1>": (9883, "profiles/step_kernels_ix_qd_c3.txt"),
+           "full_ix_kernel<4, 1>": (10954, "profiles/step_kernels_ix_qd_c3.txt")}
 
 
 def kernel_name(dom, W, shape, engine=0):
