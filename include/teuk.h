@@ -88,9 +88,11 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
  * result plus N 2^-122 / N 2^-249 of the largest of its N terms; subnormal operands count as
  * zero).
  * GB300 issues far more integer than FP64 operations per cycle. Results of the two engines
- * agree to the precision's rounding, not bit for bit. Engine 1 converts the coefficient tables
- * once (about 1.25x their size of extra device memory) and runs the rows-per-block kernels
- * (launch-shape variants 0..2). FP64 handles accept 0 only. */
+ * agree to the precision's rounding, not bit for bit; engine 1 evaluates the theta operator in
+ * its factored form A2 D2 + (A1 cot theta) D1 with exact integer stencil sums. Engine 1
+ * converts the coefficient tables once (nine planes: about 1.4x (dd) / 1.3x (qd) their size of
+ * extra device memory) and runs the rows-per-block kernels (launch-shape variants 0..2).
+ * FP64 handles accept 0 only. */
 int teuk_set_engine(teuk_t h, int engine);
 int teuk_engine(teuk_t h);
 
