@@ -519,18 +519,20 @@ def _paper_parity(m):
     return 1 if abs(m) % 2 == 0 else -1
 
 
-@pytest.mark.parametrize("W", [1, 2, 4])
+@pytest.mark.parametrize("W,engine", [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1)])
 @pytest.mark.parametrize("order", [2, 10])
 @pytest.mark.parametrize("rule", ["regular", "paper"])
 @pytest.mark.parametrize("sm", [(-1, 2), (0, 1), (-2, 3)])
-def test_theta_order_and_parity_rule_matrix(oracle_mod, W, order, rule, sm):
+def test_theta_order_and_parity_rule_matrix(oracle_mod, W, engine, order, rule, sm):
     """Regression matrix of the angular options: 2nd-order (Sec. 3.B) and 10th-order (Sec. 3.D)
     theta differences x the regular (-1)^(m+s) reflection and the paper's |m| rule, which
-    differ for s = -1, m = 2 and agree for the other two modes."""
+    differ for s = -1, m = 2 and agree for the other two modes; both multi-word engines."""
     s, m = sm
     parity = workloads.parity_of(m, s) if rule == "regular" else _paper_parity(m)
     p = small(a=0.8, s=s, m=m, n_theta=26, n_r=37, substeps=3, theta_order=order, parity=parity)
     g, o = make_pair(oracle_mod, p, W)
+    if engine:
+        g.set_engine(1)
     ell = max(abs(m), abs(s))
     g.set_initial_pulse(8.0, 4.0, 0.75, 0.5, ell)
     o.pulse(8.0, 4.0, 0.75, 0.5, ell)
@@ -664,6 +666,33 @@ def test_integer_engine_launch_shapes_and_graphs_bitwise(W, n_theta):
             np.testing.assert_array_equal(st[0], ref[0], err_msg=str((tx, ty, v)))
             np.testing.assert_array_equal(st[1], ref[1], err_msg=str((tx, ty, v)))
         g.close()
+
+
+@pytest.mark.parametrize("W,engine", [(1, 0), (2, 0), (2, 1), (4, 0), (4, 1)])
+@pytest.mark.parametrize("scale", [-400, 400])
+def test_power_of_two_scale_covariance_bitwise(W, engine, scale):
+    """The scheme is linear in the state and both engines' arithmetic commutes with scaling by
+    a power of two (exponents shift, mantissas do not change, no value leaves the normal
+    range here): the evolved state and waveform of 2^scale u0 are 2^scale times those of u0,
+    bit for bit. Pins the exponent bookkeeping (block-floating rows, accumulator bases) far
+    from exponent 0."""
+    p = small(a=0.7, s=-1, m=1, n_theta=40, n_r=45, substeps=3)
+    runs = []
+    for k in (0, scale):
+        g = teuk.Teuk(precision=W, **p)
+        if engine:
+            g.set_engine(1)
+        g.set_initial_pulse(8.0, 4.0, 0.8, 0.6, 1)
+        g.set_state(g.get_state() * 2.0 ** k)
+        g.set_observer(12.0, capacity=4)
+        g.step(3)
+        g.sync()
+        runs.append((g.get_state(), g.read_waveform()))
+        g.close()
+    (s0, w0), (s1, w1) = runs
+    assert np.abs(s0).max() > 0
+    np.testing.assert_array_equal(s1, s0 * 2.0 ** scale)
+    np.testing.assert_array_equal(w1, w0 * 2.0 ** scale)
 
 
 @pytest.mark.parametrize("W", [2, 4])
