@@ -41,7 +41,8 @@ enum {
   TEUK_ERR_OOM = -3,           /* device or host allocation failed */
   TEUK_ERR_NONFINITE = -4,     /* the evolution produced Inf/NaN (instability) */
   TEUK_ERR_STATE_MISMATCH = -5,/* a state or observer request does not fit this handle */
-  TEUK_ERR_NO_DEVICE = -6      /* no CUDA device is available */
+  TEUK_ERR_NO_DEVICE = -6,     /* no CUDA device is available */
+  TEUK_ERR_TIMEOUT = -7        /* a bounded wait inside a step kernel reached its limit */
 };
 
 /* Grid and time stepping (Sec. 3.B: r* nodes r*_i = rstar_min + i dr*, i = 0..n_r-1,
@@ -121,7 +122,7 @@ int teuk_use_graphs(teuk_t h, int enable);
 /* Advances n single Lax-Wendroff iterations of dt/substeps (no observer samples). */
 int teuk_substep(teuk_t h, int64_t n_iterations);
 /* Waits for the handle's stream; returns TEUK_ERR_NONFINITE if any Inf/NaN was produced, and
- * TEUK_ERR_CUDA if a step kernel's wait for its own copies into shared memory reached its
+ * TEUK_ERR_TIMEOUT if a step kernel's wait for its own copies into shared memory reached its
  * iteration limit (the kernel then skipped its rows). */
 int teuk_sync(teuk_t h);
 

@@ -210,6 +210,7 @@ const char* teuk_strerror(int code) {
     case TEUK_ERR_NONFINITE: return "non-finite value in the evolution";
     case TEUK_ERR_STATE_MISMATCH: return "state does not match the handle";
     case TEUK_ERR_NO_DEVICE: return "no CUDA device";
+    case TEUK_ERR_TIMEOUT: return "a wait inside a step kernel reached its limit";
     default: return "unknown error";
   }
 }
@@ -450,7 +451,7 @@ int teuk_sync(teuk_t h) {
   }
   if (st & 2u) {
     h->last_error = "a copy into shared memory did not complete within its wait limit";
-    return TEUK_ERR_CUDA;
+    return TEUK_ERR_TIMEOUT;
   }
   return TEUK_OK;
 }

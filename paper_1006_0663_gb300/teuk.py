@@ -15,8 +15,8 @@ from . import build as _build
 
 _lib = None
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_STATE_MISMATCH, ERR_NO_DEVICE = (
-    0, -1, -2, -3, -4, -5, -6)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_STATE_MISMATCH, ERR_NO_DEVICE, ERR_TIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 FP64, DD, QD = 1, 2, 4
 
 SYMBOLS = [

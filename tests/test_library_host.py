@@ -32,6 +32,7 @@ def test_strerror_and_invalid_arguments():
     L = teuk.lib()
     assert L.teuk_strerror(0) == b"ok"
     assert b"invalid" in L.teuk_strerror(teuk.ERR_INVALID_ARG)
+    assert b"limit" in L.teuk_strerror(teuk.ERR_TIMEOUT)
     g = teuk.TeukGrid(-10.0, 10.0, 2, 16, 0.0, 1, 10, 0, 0)  # n_r < 3
     h = ctypes.c_void_p()
     rc = L.teuk_create(ctypes.byref(h), 1.0, 0.5, -2, 2, ctypes.byref(g), 1, None)
