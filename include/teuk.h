@@ -243,7 +243,10 @@ int teuk_substep_noalloc(teuk_t h, const double* u_in, double* u_out, int64_t n_
 
 /* Per-kernel timing with CUDA events on the handle's stream: enable = 1 starts recording
  * the duration of every half-step and full-step launch; teuk_kernel_times() waits for the
- * stream and returns (and clears) the summed milliseconds and launch counts. */
+ * stream and returns (and clears) the summed milliseconds and launch counts. Steps replayed
+ * as a CUDA graph keep running as a graph and time a sample: the two kernels of the last
+ * iteration of the outer step (event nodes of the graph), counted once per drain from the
+ * last replay before it (the counts say how many launches were timed). */
 int teuk_timing(teuk_t h, int enable);
 int teuk_kernel_times(teuk_t h, double* ms_half, double* ms_full, int64_t* n_half, int64_t* n_full);
 

@@ -111,14 +111,40 @@ __global__ void fp64_peak_kernel(double* out, double a, double b, int iters) {
 // outer step; the kernels read the slot from this counter).
 __global__ void advance_counter_kernel(long long* counter) { *counter += 1; }
 
+// Reads the timing events of the last replay of the outer-step graph into the totals.
+void read_graph_timing(teuk_s* h) {
+  if (!h->graph_events_fresh) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& p : h->graph_events) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      h->ms[p.kind] += t;
+      h->n_timed[p.kind] += 1;
+    } else {
+      cudaGetLastError();  // a pair without a time is skipped; keep the error from later checks
+    }
+  }
+  h->graph_events_fresh = false;
+}
+
 void drop_graph(teuk_s* h) {
+  read_graph_timing(h);
+  for (auto& p : h->graph_events) {
+    h->free_events.push_back(p.a);
+    h->free_events.push_back(p.b);
+  }
+  h->graph_events.clear();
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   h->graph_exec = nullptr;
 }
 
+// With timing on, the captured graph records an event pair around the two kernels of the
+// last iteration of the outer step (event record nodes: a node per kernel would cost about
+// what separate launches cost); the library reads the last replay's pairs when the timings
+// are drained.
 bool graphs_possible(const teuk_s* h) {
   const cudaStream_t legacy = (cudaStream_t)0x1;
-  return h->use_graphs && !h->timing && h->stream != nullptr && h->stream != legacy &&
+  return h->use_graphs && h->stream != nullptr && h->stream != legacy &&
          (h->ko_sigma == 0 || h->substeps_done % h->k == 0);
 }
 
@@ -135,12 +161,25 @@ int build_graph(teuk_s* h, bool record) {
   if (prc != TEUK_OK) return prc;
   const int64_t launches = h->launches;
   cudaGraph_t graph = nullptr;
+  if (h->timing) {  // events for the capture come from the pool, made before it starts
+    for (size_t n = h->free_events.size(); n < (size_t)(4 * h->k + 2); ++n) {
+      cudaEvent_t ev = nullptr;
+      TEUK_CUDA(h, cudaEventCreate(&ev));
+      h->free_events.push_back(ev);
+    }
+  }
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return teuk::cuda_fail(h, e, "cudaStreamBeginCapture");
+  h->capturing = true;
   int rc = h->ko_sigma > 0 ? dispatch_dissipate(h) : TEUK_OK;
-  for (int q = 0; q < h->k && rc == TEUK_OK; ++q) rc = dispatch_substep(h, record && q == h->k - 1, -1);
+  for (int q = 0; q < h->k && rc == TEUK_OK; ++q) {
+    h->time_this = q == h->k - 1;  // the graph times the last iteration of the outer step only
+    rc = dispatch_substep(h, record && q == h->k - 1, -1);
+  }
+  h->time_this = true;
   if (rc == TEUK_OK && record) advance_counter_kernel<<<1, 1, 0, h->stream>>>(h->d_ring_counter);
   e = cudaStreamEndCapture(h->stream, &graph);
+  h->capturing = false;
   h->launches = launches;
   if (rc != TEUK_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -158,6 +197,7 @@ int build_graph(teuk_s* h, bool record) {
 }
 
 void drain_timing(teuk_s* h) {
+  read_graph_timing(h);
   if (h->pending.empty()) return;
   cudaStreamSynchronize(h->stream);
   for (auto& p : h->pending) {
@@ -165,6 +205,8 @@ void drain_timing(teuk_s* h) {
     if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
       h->ms[p.kind] += t;
       h->n_timed[p.kind] += 1;
+    } else {
+      cudaGetLastError();  // a pair without a time is skipped; keep the error from later checks
     }
     h->free_events.push_back(p.a);
     h->free_events.push_back(p.b);
@@ -185,15 +227,25 @@ cudaEvent_t take_event(teuk_s* h) {
   cudaEventCreate(&e);
   return e;
 }
+// While the outer-step graph is captured, events are recorded as external event record
+// nodes (recorded when the graph runs), not as capture-internal dependencies.
+static void record_event(teuk_s* h, cudaEvent_t e) {
+  if (h->capturing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(e, h->stream);
+}
 void time_begin(teuk_s* h, cudaEvent_t* a) {
-  if (!h->timing) return;
+  if (!h->timing || !h->time_this) return;
   *a = take_event(h);
-  cudaEventRecord(*a, h->stream);
+  record_event(h, *a);
 }
 void time_end(teuk_s* h, int kind, cudaEvent_t a) {
   if (!h->timing || !a) return;
   cudaEvent_t b = take_event(h);
-  cudaEventRecord(b, h->stream);
+  record_event(h, b);
+  if (h->capturing) {  // recorded by every replay of the graph
+    h->graph_events.push_back(teuk_s::EvPair{kind, a, b});
+    return;
+  }
   h->pending.push_back(teuk_s::EvPair{kind, a, b});
   if (h->pending.size() > 4096) drain_timing(h);
 }
@@ -422,6 +474,7 @@ int teuk_step(teuk_t h, int64_t n) {
                                    h->stream));
     }
     for (int64_t t = 0; t < n; ++t) TEUK_CUDA(h, cudaGraphLaunch(h->graph_exec, h->stream));
+    if (!h->graph_events.empty()) h->graph_events_fresh = true;
     h->substeps_done += n * h->k;
     h->launches += n * (2 * h->k + (h->ko_sigma > 0 ? 1 : 0));
     if (record) h->n_recorded += n;
@@ -694,6 +747,7 @@ int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int v
 int teuk_timing(teuk_t h, int enable) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   drain_timing(h);
+  if (h->timing != (enable != 0)) drop_graph(h);  // the graph is captured with or without events
   h->timing = enable != 0;
   h->ms[0] = h->ms[1] = 0;
   h->n_timed[0] = h->n_timed[1] = 0;

@@ -58,6 +58,10 @@ struct teuk_s {
   bool timing = false;
   struct EvPair { int kind; cudaEvent_t a, b; };
   std::vector<EvPair> pending;
+  std::vector<EvPair> graph_events;  // timing events captured in the outer-step graph
+  bool graph_events_fresh = false;   // a replay has recorded them since they were last read
+  bool capturing = false;            // the outer-step graph is being captured
+  bool time_this = true;             // whether the launches being issued are timed
   std::vector<cudaEvent_t> free_events;
   double ms[2] = {0, 0};
   int64_t n_timed[2] = {0, 0};

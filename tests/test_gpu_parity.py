@@ -364,6 +364,40 @@ def test_engine_wide_rows_shapes():
     g2.close()
 
 
+@pytest.mark.parametrize("W,engine", [(1, 0), (2, 1)])
+def test_kernel_timing_inside_graphs(W, engine):
+    """Per-kernel timing keeps graph replay: the events are nodes of the captured outer step
+    around its last iteration, and one drain reports the last replay's half-step and full-step
+    launch; without graphs every launch is timed. Timing does not change the results."""
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p = small(n_r=57, n_theta=40, substeps=3)
+        states = []
+        for graphs, timing in [(True, True), (False, True), (True, False)]:
+            g = teuk.Teuk(precision=W, **p)
+            if engine:
+                g.set_engine(1)
+            g.use_graphs(graphs)
+            g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
+            g.set_observer(12.0, capacity=8)
+            g.timing(timing)
+            g.step(4)
+            g.sync()
+            ms_h, ms_f, n_h, n_f = g.kernel_times()
+            if timing:
+                expect = 1 if graphs else 4 * p["substeps"]
+                assert (n_h, n_f) == (expect, expect), (graphs, n_h, n_f)
+                assert ms_h > 0 and ms_f > 0
+            else:
+                assert (n_h, n_f) == (0, 0)
+            states.append((g.get_state(), g.read_waveform()))
+            g.close()
+        for st, wf in states[1:]:
+            np.testing.assert_array_equal(st, states[0][0])
+            np.testing.assert_array_equal(wf, states[0][1])
+
+
 def test_batch_chunks_of_200_steps():
     alone = [_member(1, kw) for kw in BATCH_MEMBERS[:2]]
     batched = [_member(1, kw) for kw in BATCH_MEMBERS[:2]]
