@@ -75,3 +75,31 @@ def _isnum(x):
         return True
     except ValueError:
         return False
+
+
+def test_roofline_arithmetic_on_a_sampled_timing():
+    """roofline_for on a synthetic c2 run whose kernel times are a sample (one timed launch of
+    each kernel, as graph replay gives): the dominant kernel is the one with the longer average
+    launch; achieved = instructions per point x points / duration against 128 x SMs x clock;
+    the step fraction scales the average launch by the launches of the timed steps."""
+    mod, root = _bench_module()
+    from paper_1006_0663_gb300 import workloads
+    prob = workloads.CONFIGS["c2"]
+    steps, k = 10, prob.substeps
+    res = {"kernel_times": (0.068, 0.080, 1, 1), "ms_total": 10 * 12.25, "launches": steps * 2 * k,
+           "rows_per_block": {"threads_theta": 128, "rows_per_block": 2, "variant": 1}}
+    r = mod.roofline_for(res, prob, 2, 1, {"sm_mhz": 2070.0}, 152, 0.5e12, "c2")
+    assert r["kernel"] == "full_ix_kernel<2, 1>"
+    inst = mod.IX_INST["full_ix_kernel<2, 1>"][0]
+    pts = (prob.n_r - 2) * prob.n_theta
+    assert abs(r["achieved"] * 1e12 - inst * pts / 0.080e-3) < 1e3
+    assert abs(r["peak"] * 1e12 - 128 * 152 * 2070e6) < 1e3
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert abs(r["fraction_of_step_in_dominant_kernel"] - 0.080 * steps * k / (10 * 12.25)) < 1e-12
+    assert r["traffic"] == mod.TRAFFIC[("c2", "full_ix_kernel<2, 1>")][0]
+    # the FP64 path counts the scheme's FP64 operations against 2 per SM per cycle
+    r1 = mod.roofline_for(dict(res, kernel_times=(0.10, 0.09, 1, 1)), prob, 2, 0, {"sm_mhz": 2000.0}, 152,
+                          0.5e12, "c2")
+    assert r1["kernel"].startswith("half_kernel<2")
+    assert abs(r1["achieved"] * 1e12 - mod.OPS_HALF[2] * (prob.n_r - 1) * prob.n_theta / 0.10e-3) < 1e3
+    assert abs(r1["peak"] * 1e12 - 2 * 152 * 2000e6) < 1e3
