@@ -730,6 +730,29 @@ def test_power_of_two_scale_covariance_bitwise(W, engine, scale):
 
 
 @pytest.mark.parametrize("W", [2, 4])
+def test_engine_switch_mid_run_parity(oracle_mod, W):
+    """The state stays in multi-word doubles whichever engine steps it: a run that alternates
+    engines (integer, FP64 transforms, integer) between outer steps stays within the
+    precision's tolerance of the 256-bit oracle, and its observer ring keeps its samples."""
+    p = small(a=0.6, s=-1, m=2, n_theta=40, n_r=53)
+    g, o = make_pair(oracle_mod, p, W)
+    ell = max(abs(p["m"]), abs(p["s"]))
+    g.set_initial_pulse(12.0, 4.0, 0.8, 0.55, ell)
+    o.pulse(12.0, 4.0, 0.8, 0.55, ell)
+    g.set_observer(15.0, capacity=8)
+    for engine in (1, 0, 1):
+        g.set_engine(engine)
+        g.step(1)
+    g.sync()
+    assert g.engine == 1
+    o.step(3 * p["substeps"])
+    err, umax = o.max_rel_err(g.get_state())
+    assert umax > 0.05
+    assert err < TOL[W], err
+    assert g.read_waveform().shape[0] == 3
+
+
+@pytest.mark.parametrize("W", [2, 4])
 def test_integer_engine_reports_nonfinite_and_rejects_fp64(W):
     p = small()
     g = teuk.Teuk(precision=W, **p)
