@@ -38,6 +38,10 @@ OPS_FULL = {1: 50, 2: 498, 4: 3734}
 # once (half kernel) / read once and state written once (full kernel), 8 folded coefficients.
 BYTES_HALF = {w: (4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
 BYTES_FULL = {w: (4 + 4 + 4 + 8) * 8 * w for w in (1, 2, 4)}
+# Integer engine: the tables are nine planes of a 16 kU4-byte mantissa and a 4-byte
+# exponent-sign word per point (kU4 = 1 for dd, 2 for qd) instead of eight multi-word reals.
+BYTES_HALF_IX = {w: (4 + 4) * 8 * w + 9 * (16 * (w // 2) + 4) for w in (2, 4)}
+BYTES_FULL_IX = {w: (4 + 4 + 4) * 8 * w + 9 * (16 * (w // 2) + 4) for w in (2, 4)}
 DTYPE = {1: "f64", 2: "f64x2 (double-double)", 4: "f64x4 (quad-double)"}
 ENGINE_NAME = {0: "FP64 error-free transforms", 1: "integer engine"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
@@ -386,7 +390,8 @@ def roofline_for(res, prob, W, engine, clocks, sms, probe, workload):
         "kernel": kname, "avg_launch_ms": avg, "launch_shape": res["rows_per_block"],
         "ops_per_point": ops_pt, "peak_source": peak_source, "op_unit": op_unit,
         "fma_chain_probe_tops": probe / 1e12,
-        "hbm_achieved_gbs": (BYTES_HALF[W] if dom == "half" else BYTES_FULL[W]) * pts / (avg * 1e-3) / 1e9,
+        "hbm_achieved_gbs": ((BYTES_HALF_IX if engine == 1 else BYTES_HALF)[W] if dom == "half"
+                             else (BYTES_FULL_IX if engine == 1 else BYTES_FULL)[W]) * pts / (avg * 1e-3) / 1e9,
         "fraction_of_step_in_dominant_kernel": (avg_h if dom == "half" else avg_f) * res["launches"] / 2
         / max(res["ms_total"], 1e-9),
     }

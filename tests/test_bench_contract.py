@@ -97,6 +97,9 @@ def test_roofline_arithmetic_on_a_sampled_timing():
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     assert abs(r["fraction_of_step_in_dominant_kernel"] - 0.080 * steps * k / (10 * 12.25)) < 1e-12
     assert r["traffic"] == mod.TRAFFIC[("c2", "full_ix_kernel<2, 1>")][0]
+    # algorithmic bytes of an engine full-step point: 12 dd values moved + 9 table entries of 20 B
+    assert mod.BYTES_FULL_IX[2] == 12 * 16 + 9 * 20
+    assert abs(r["hbm_achieved_gbs"] - 372 * pts / 0.080e-3 / 1e9) < 1e-6
     # the FP64 path counts the scheme's FP64 operations against 2 per SM per cycle
     r1 = mod.roofline_for(dict(res, kernel_times=(0.10, 0.09, 1, 1)), prob, 2, 0, {"sm_mhz": 2000.0}, 152,
                           0.5e12, "c2")
