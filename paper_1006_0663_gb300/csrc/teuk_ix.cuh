@@ -14,6 +14,11 @@
 // complement integer aligned to the row's largest), so D2 and D1 are exact integer
 // multiply-adds, and the factors H5 A2, H5 A1 cot theta (N5 ... in the full step) are folded
 // into the coefficient tables at set-up.
+//
+// A block's rows of the coefficient tables (and, where the footprint keeps as many blocks per
+// SM resident, its state rows) are brought into shared memory by bulk asynchronous copies
+// (cp.async.bulk completing on an mbarrier, issued by one thread at the start) while the block
+// builds its theta rows; the wait for them is bounded and reports through the status word.
 #pragma once
 
 #include "ix.cuh"
