@@ -117,6 +117,7 @@ CASES = [
     dict(a=0.6, s=-1, m=2, n_theta=40, n_r=53),                # odd parity (m+s odd)
     dict(a=0.99, s=0, m=0, n_theta=17, n_r=35, substeps=2),    # scalar field, tiny ragged theta
     dict(a=0.5, s=-2, m=1, theta_order=2, n_theta=30),         # 2nd-order theta operator
+    dict(a=0.7, s=0, m=1, n_theta=6, n_r=31),                  # narrowest rows: both pole images
 ]
 
 
