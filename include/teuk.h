@@ -228,8 +228,10 @@ int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int v
  *    state is neither read nor written.
  *  - u_in / u_out: caller-owned device buffers in the handle's layout
  *    [4][w][n_r][P] doubles, P = n_theta rounded up to a multiple of 16 (128 bytes); they may
- *    be the same buffer. The first iteration reads u_in, later ones run in place on u_out;
- *    rows 0 and n_r-1 of u_out are set to zero.
+ *    be the same buffer. Both must start on a 16-byte boundary (the integer engine copies
+ *    their rows into shared memory with bulk copies), else TEUK_ERR_INVALID_ARG; allocators
+ *    such as cudaMalloc and torch's return 256-byte aligned blocks. The first iteration reads
+ *    u_in, later ones run in place on u_out; rows 0 and n_r-1 of u_out are set to zero.
  *  - The half-step rows live in one fixed device array of 2^21 doubles (16 MiB) that every
  *    GPU loading the library holds until exit; 4 * w * (n_r - 1) * P above 2^21 is rejected
  *    with TEUK_ERR_INVALID_ARG. Every row of it that a call reads is written earlier in the
@@ -238,7 +240,10 @@ int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int v
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  *    make that first call before any stream capture. The handle's device must be current.
  *  - Calls no cudaMalloc, cudaFree or other allocating routine; work is queued on the
- *    handle's stream. */
+ *    handle's stream and the call returns without waiting for it.
+ *  - Errors found by the kernels themselves (a non-finite value, TEUK_ERR_NONFINITE; a bounded
+ *    wait that reached its limit, TEUK_ERR_TIMEOUT) are kept in the handle's status word and
+ *    reported by the next teuk_sync(h), as for teuk_substep. */
 int teuk_substep_noalloc(teuk_t h, const double* u_in, double* u_out, int64_t n_iterations);
 
 /* Per-kernel timing with CUDA events on the handle's stream: enable = 1 starts recording

@@ -84,6 +84,7 @@ def lib():
         L.oracle_theta_op.argtypes = [i32, i32, i32, i32, dp, i32, dp, i32]
         L.oracle_spin_profile.argtypes = [i32, i32, i32, i32, i32, dp, i32]
         L.oracle_set_row.argtypes = [vp, i32, dp, i32]
+        L.oracle_set_forcing.argtypes = [vp, d, dp, dp]
         L.oracle_fejer_weights.argtypes = [i32, i32, dp, i32]
         L.oracle_swsh.argtypes = [i32, i32, i32, i32, i32, dp, dp, i32]
         L.oracle_project.argtypes = [i32, i32, i32, i32, i32, i32, dp, i32, i64, dp, i32]
@@ -177,6 +178,18 @@ class Oracle:
         assert values.shape[0] == 4 and values.shape[2] == self.nth
         if lib().oracle_set_row(self._h, int(row), _dp(values), values.shape[1]) != 0:
             raise IndexError(row)
+
+    def set_forcing(self, omega, f_node, f_half):
+        """Test-only forcing of the Pi rows for manufactured solutions (not part of the
+        method): S_Pi += e^{-i omega t} F^, F^ complex arrays [nrow][n_theta] at nodes and
+        [nrow-1][n_theta] at half nodes. None switches it off."""
+        if f_node is None:
+            lib().oracle_set_forcing(self._h, 0.0, None, None)
+            return
+        fn = np.ascontiguousarray(np.stack([np.real(f_node), np.imag(f_node)]), dtype=np.float64)
+        fh = np.ascontiguousarray(np.stack([np.real(f_half), np.imag(f_half)]), dtype=np.float64)
+        assert fn.shape == (2, self.nrow, self.nth) and fh.shape == (2, self.nrow - 1, self.nth)
+        lib().oracle_set_forcing(self._h, float(omega), _dp(fn), _dp(fh))
 
     def coeffs(self, which: int, words: int = 1) -> np.ndarray:
         rows = self.nrow - 1 if which else self.nrow

@@ -20,9 +20,11 @@
 //   * zero r* boundaries and axis parity for theta (Sec. 3.B, last paragraph).
 //
 // Parity status: every function here is pinned by tests (symbolic reduction from Eq. 1,
-// theta operator on spin-weighted harmonics, tortoise closed form at a = 0, 2nd-order
-// convergence of a forced exact solution, a -> -a conjugation symmetry, a = 0
-// separability, and an independent transcription on tiny grids).
+// theta operator on spin-weighted harmonics, tortoise closed form at a = 0, a -> -a
+// conjugation symmetry, a = 0 separability and an independent radial solver, and a forced
+// manufactured solution at a != 0: a smooth complex field whose forcing is derived from
+// Eq. 1 itself, outside this file, converges at 2nd order, which pins how source()
+// combines the complex coefficients).
 
 #include <algorithm>
 #include <cmath>
@@ -136,6 +138,11 @@ struct Solver {
   std::vector<T> cn[8], ch[8];                       // coefficients [row*nth + j]
   std::vector<T> u[4], uh[4], un[4];                 // state, half state, next state
   int64_t substeps_done = 0;
+  // Test-only forcing of the Pi rows (manufactured solutions): F(t) = e^{-i omega t} F^ at
+  // nodes (fn) and half nodes (fh), real and imaginary parts; off unless set.
+  bool forced = false;
+  T f_omega;
+  std::vector<T> fn[2], fh[2];
 
   // ---- Sec. 3.B: tortoise coordinate.  dr*/dr = (r^2+a^2)/Delta, Delta = (r-r+)(r-r-).
   // With x = r - r+, partial fractions give
@@ -357,10 +364,23 @@ struct Solver {
     }
   }
 
+  // Forcing at time t: (Re, Im) of e^{-i omega t} F^ is (c F^_R + s F^_I, c F^_I - s F^_R).
+  void forcing_phase(const T& t, T& c, T& sn) const {
+    c = cos_(f_omega * t);
+    sn = sin_(f_omega * t);
+  }
+
   void substep() {
     if (p.ko_sigma > 0 && substeps_done % p.substeps == 0) dissipate();
     const T half = T(0.5);
     const T hdt = dts * half;
+    // forcing phases at t_n (half step) and t_n + dts/2 (full step)
+    T fc0 = T(0.0), fs0 = T(0.0), fc1 = T(0.0), fs1 = T(0.0);
+    if (forced) {
+      const T tn = T(double(substeps_done)) * dts;
+      forcing_phase(tn, fc0, fs0);
+      forcing_phase(tn + hdt, fc1, fs1);
+    }
     // Eq. lw1: u^{n+1/2}_{i+1/2} = (u_{i+1} + u_i)/2 - dt/2 [D (u_{i+1} - u_i)/dr - S^n_{i+1/2}].
 #pragma omp parallel for schedule(static)
     for (int h = 0; h < nrow - 1; ++h) {
@@ -380,6 +400,10 @@ struct Solver {
         for (int c = 0; c < 8; ++c) cf[c] = ch[c][k0];
         const T LR = theta_op(barR.data(), j), LI = theta_op(barI.data(), j);
         source(ub, du, LR, LI, cf, S);
+        if (forced) {
+          S[2] = S[2] + (fc0 * fh[0][k0] + fs0 * fh[1][k0]);
+          S[3] = S[3] + (fc0 * fh[1][k0] - fs0 * fh[0][k0]);
+        }
         const T& b = cf[0];
         uh[0][k0] = ub[0] - hdt * (b * du[0] - S[0]);
         uh[1][k0] = ub[1] - hdt * (b * du[1] - S[1]);
@@ -416,6 +440,10 @@ struct Solver {
         for (int c = 0; c < 8; ++c) cf[c] = cn[c][k];
         const T LR = theta_op(barR.data(), j), LI = theta_op(barI.data(), j);
         source(ub, du, LR, LI, cf, S);
+        if (forced) {
+          S[2] = S[2] + (fc1 * fn[0][k] + fs1 * fn[1][k]);
+          S[3] = S[3] + (fc1 * fn[1][k] - fs1 * fn[0][k]);
+        }
         const T& b = cf[0];
         un[0][k] = u[0][k] - dts * (b * du[0] - S[0]);
         un[1][k] = u[1][k] - dts * (b * du[1] - S[1]);
@@ -886,6 +914,31 @@ int oracle_project(int bits, int s, int m, int nth, int ell_min, int ell_max, co
 }  // extern "C"
 
 extern "C" {
+
+// Test-only forcing of the Pi equation for manufactured solutions (not part of the method):
+// Pi_t - b Pi' = S_Pi + e^{-i omega t} F^, with F^ given as doubles at the window's nodes,
+// fn [2 (re, im)][nrow][nth], and half nodes, fh [2][nrow-1][nth]. Eqs. lw1 / lw2 take it at
+// t_n at half nodes and at t_n + dt/2 at nodes, like the rest of S. NULL tables switch it off.
+int oracle_set_forcing(void* hv, double omega, const double* fn, const double* fh) {
+  Handle* h = (Handle*)hv;
+  return dispatch(h, [&](auto& S) {
+    using T = typename std::decay<decltype(S.dts)>::type;
+    if (!fn || !fh) {
+      S.forced = false;
+      return 0;
+    }
+    const size_t pn = (size_t)S.nrow * S.nth, ph = (size_t)(S.nrow - 1) * S.nth;
+    for (int part = 0; part < 2; ++part) {
+      S.fn[part].resize(pn);
+      S.fh[part].resize(ph);
+      for (size_t k = 0; k < pn; ++k) S.fn[part][k] = T(fn[part * pn + k]);
+      for (size_t k = 0; k < ph; ++k) S.fh[part][k] = T(fh[part * ph + k]);
+    }
+    S.f_omega = T(omega);
+    S.forced = true;
+    return 0;
+  });
+}
 
 // Overwrites one theta row of the state (window-relative row index) from in [4][words][nth]:
 // used to place halo rows received from a neighbouring slab.

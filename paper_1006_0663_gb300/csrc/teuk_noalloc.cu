@@ -11,6 +11,7 @@
 // library holds until the process exits. Nothing is allocated per call.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "teuk_internal.h"
@@ -60,8 +61,16 @@ extern "C" int teuk_substep_noalloc(teuk_t h, const double* u_in, double* u_out,
                     " (4 * words * (n_r - 1) * pitch must not exceed 2^21)";
     return TEUK_ERR_INVALID_ARG;
   }
+  // The integer engine copies rows of u_in into shared memory with bulk asynchronous copies,
+  // which need 16-byte aligned sources; rows are multiples of 128 bytes, so the base pointers
+  // decide. Refused here instead of faulting inside a kernel.
+  if (((uintptr_t)u_in | (uintptr_t)u_out) & 15u) {
+    h->last_error = "teuk_substep_noalloc: u_in and u_out must be 16-byte aligned";
+    return TEUK_ERR_INVALID_ARG;
+  }
   int dev = -1;
-  cudaGetDevice(&dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return teuk::cuda_fail(h, e, "cudaGetDevice");
   if (dev != h->device) {
     h->last_error = "teuk_substep_noalloc: the handle's device must be current";
     return TEUK_ERR_INVALID_ARG;

@@ -11,7 +11,6 @@ sympy. The first-order system u_t + D u' = S with Pi = Phi_t + b Phi' (Sec. 3.B)
 for the same operator (times -1), so the oracle's b, c, beta = B/Sigma^2, g = Delta/Sigma^2,
 nu = V/Sigma^2 are compared with the sympy-derived values at random points.
 """
-import functools
 import random
 
 import mpmath as mpm
@@ -19,41 +18,11 @@ import numpy as np
 import pytest
 
 sp = pytest.importorskip("sympy")
+from tests.eq1_symbolic import eq1_functions  # noqa: E402
 
 
-@functools.lru_cache(maxsize=None)
 def reduced_coefficients(s_val: int, m_val: int):
-    t, r, th, phi = sp.symbols("t r theta phi", real=True)
-    M, a = sp.symbols("M a", positive=True)
-    F = sp.Function("F")(t, r, th)
-    G = sp.Function("G")(r)
-    I = sp.I
-    s, m = sp.Integer(s_val), sp.Integer(m_val)
-    Delta = r**2 - 2 * M * r + a**2
-    E0 = sp.exp(I * m * (phi + G))
-    Psi = E0 * r**3 * F
-    # Eq. 1 as printed in Sec. 3.A
-    eq = (-((r**2 + a**2) ** 2 / Delta - a**2 * sp.sin(th) ** 2) * sp.diff(Psi, t, 2)
-          - 4 * M * a * r / Delta * sp.diff(Psi, t, phi)
-          - 2 * s * (r - M * (r**2 - a**2) / Delta + I * a * sp.cos(th)) * sp.diff(Psi, t)
-          + Delta ** (-s) * sp.diff(Delta ** (s + 1) * sp.diff(Psi, r), r)
-          + 1 / sp.sin(th) * sp.diff(sp.sin(th) * sp.diff(Psi, th), th)
-          + (1 / sp.sin(th) ** 2 - a**2 / Delta) * sp.diff(Psi, phi, 2)
-          + 2 * s * (a * (r - M) / Delta + I * sp.cos(th) / sp.sin(th) ** 2) * sp.diff(Psi, phi)
-          - (s**2 * sp.cot(th) ** 2 - s) * Psi)
-    E = eq / E0
-    E = E.subs(sp.Derivative(G, (r, 2)), sp.diff(a / Delta, r)).subs(sp.Derivative(G, r), a / Delta)
-    syms = sp.symbols("d_tt d_t d_rr d_r d_thth d_th d_0")
-    E = E.subs({sp.Derivative(F, (t, 2)): syms[0], sp.Derivative(F, (r, 2)): syms[2],
-                sp.Derivative(F, (th, 2)): syms[4]})
-    E = E.subs({sp.Derivative(F, t): syms[1], sp.Derivative(F, r): syms[3],
-                sp.Derivative(F, th): syms[5]})
-    E = E.subs(F, syms[6])
-    E = sp.expand(E)
-    coeffs = [E.coeff(v) for v in syms]
-    assert sp.expand(E - sum(c * v for c, v in zip(coeffs, syms))) == 0
-    # multiply by Delta / r^3 (Eq. 1 times Delta, divided by the r^3 of the ansatz)
-    return [sp.lambdify((r, th, M, a), c * Delta / r**3, "mpmath") for c in coeffs]
+    return eq1_functions(s_val, m_val, "mpmath")
 
 
 def expected_system(s, m, Mv, av, r, th):

@@ -2,14 +2,16 @@
 
 It is meant for callers whose device memory is owned by a pool of their own, or who cannot
 afford cudaMalloc / cudaFree in their stepping loop. The test drives it through the C ABI
-with caller-owned device buffers, twice in a row (out of place, then in place), and checks
-the result against teuk_substep on the same data, within the parity tolerances of the GPU
-tests. It also checks that sizes beyond the fixed scratch array are refused."""
+with caller-owned device buffers, twice in a row (out of place, then in place), on both
+multi-word arithmetic engines, and checks the result against teuk_substep on the same data
+and against the 256-bit CPU oracle, within the parity tolerances of the GPU tests. It also
+checks that sizes beyond the fixed scratch array and misaligned buffers are refused."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1006_0663_gb300 import teuk
 
 pytestmark = pytest.mark.gpu
@@ -31,12 +33,17 @@ def _word_rel_err(got, want):
     return np.abs(diff).max() / np.abs(want[:, 0]).max()
 
 
-@pytest.mark.parametrize("W", [1, 2, 4])
-def test_noalloc_matches_substep_two_calls(W):
+P_SMALL = dict(M=1.0, a=0.9, s=-2, m=2, rstar_min=-30.0, rstar_max=50.0, n_r=41, n_theta=24,
+               substeps=4)
+
+
+@pytest.mark.parametrize("W,engine", [(1, 0), (2, 0), (2, 1), (4, 0), (4, 1)])
+def test_noalloc_matches_substep_two_calls(W, engine):
     torch = _torch_cuda()
-    p = dict(M=1.0, a=0.9, s=-2, m=2, rstar_min=-30.0, rstar_max=50.0, n_r=41, n_theta=24,
-             substeps=4)
+    p = P_SMALL
     g = teuk.Teuk(precision=W, **p)
+    if engine:
+        g.set_engine(engine)
     g.set_initial_pulse(12.0, 4.0, 0.8, 0.55, 2)
     u0 = g.get_state()
     pitch = (p["n_theta"] + 15) // 16 * 16
@@ -59,6 +66,31 @@ def test_noalloc_matches_substep_two_calls(W):
     assert np.abs(want[:, 0]).max() > 0.05
     assert _word_rel_err(got, want) < TOL[W]
     assert np.all(got[:, :, 0] == 0) and np.all(got[:, :, -1] == 0)
+    # and against the oracle: the same six iterations in 256-bit arithmetic
+    o = oracle.Oracle(M=p["M"], a=p["a"], s=p["s"], m=p["m"], rstar_min=p["rstar_min"],
+                      rstar_max=p["rstar_max"], n_r=p["n_r"], n_theta=p["n_theta"], dt=0.0,
+                      substeps=p["substeps"], bits=256)
+    o.pulse(12.0, 4.0, 0.8, 0.55, 2)
+    o.step(6)
+    err, umax = o.max_rel_err(got)
+    assert umax > 0.05 and err < TOL[W], err
+
+
+def test_noalloc_rejects_misaligned_buffers():
+    torch = _torch_cuda()
+    p = P_SMALL
+    g = teuk.Teuk(precision=2, **p)
+    g.set_engine(1)
+    pitch = (p["n_theta"] + 15) // 16 * 16
+    n = 4 * 2 * p["n_r"] * pitch
+    buf = torch.zeros(n + 2, dtype=torch.float64, device="cuda")
+    L = teuk.lib()
+    base = buf.data_ptr()
+    for u_in, u_out in ((base + 8, base), (base, base + 8)):
+        rc = L.teuk_substep_noalloc(g._h, ctypes.c_void_p(u_in), ctypes.c_void_p(u_out), 1)
+        assert rc == teuk.ERR_INVALID_ARG
+        assert b"16-byte" in L.teuk_last_error(g._h)
+    g.sync()  # nothing was launched: the handle is still usable
 
 
 def test_noalloc_rejects_sizes_beyond_the_fixed_array():
