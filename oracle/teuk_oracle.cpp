@@ -117,6 +117,7 @@ struct oracle_params {
   int32_t parity;       // +1 or -1: sign of the reflection of Phi, Pi across each pole
   int32_t row_lo, row_hi;  // window of r* rows simulated (inclusive), 0 .. n_r-1 for all
   double ko_sigma;         // r* dissipation strength (not in the paper; 0 = off), see dissipate()
+  double ko_theta;         // theta dissipation strength (not in the paper; 0 = off), see dissipate()
 };
 
 }  // extern "C"
@@ -136,6 +137,7 @@ struct Solver {
   std::vector<T> th, sin_th, cos_th, cot_th;         // [nth]
   std::vector<T> rs_node, rs_half, x_node, x_half;   // [nrow], [nrow-1]
   std::vector<T> cn[8], ch[8];                       // coefficients [row*nth + j]
+  std::vector<T> c_theta;                            // [nrow] max_j sqrt(Delta/Sigma^2) at the node
   std::vector<T> u[4], uh[4], un[4];                 // state, half state, next state
   int64_t substeps_done = 0;
   // Test-only forcing of the Pi rows (manufactured solutions): F(t) = e^{-i omega t} F^ at
@@ -234,7 +236,7 @@ struct Solver {
     if (p.theta_order != 10 && p.theta_order != 2) return -1;
     if (p.parity != 1 && p.parity != -1) return -1;
     if (p.row_lo < 0 || p.row_hi >= p.n_r || p.row_hi - p.row_lo < 2) return -1;
-    if (!(p.rstar_max > p.rstar_min) || !(p.dt >= 0) || !(p.ko_sigma >= 0)) return -1;
+    if (!(p.rstar_max > p.rstar_min) || !(p.dt >= 0) || !(p.ko_sigma >= 0) || !(p.ko_theta >= 0)) return -1;
     nrow = p.row_hi - p.row_lo + 1;
     nth = p.n_theta;
     M = T(p.M);
@@ -279,6 +281,12 @@ struct Solver {
         }
       }
     }
+    c_theta.assign(nrow, T(0.0));
+    for (int i = 0; i < nrow; ++i)
+      for (int j = 0; j < nth; ++j) {
+        const T v = sqrt_(cn[5][(size_t)i * nth + j]);
+        if (c_theta[i] < v) c_theta[i] = v;
+      }
     for (int c = 0; c < 4; ++c) {
       u[c].assign((size_t)nrow * nth, T(0.0));
       un[c].assign((size_t)nrow * nth, T(0.0));
@@ -337,29 +345,53 @@ struct Solver {
     S[3] = -(cR * du[1] + cI * du[0]) - (bR * ub[3] + bI * ub[2]) + g * LI + (vR * ub[1] + vI * ub[0]);
   }
 
-  // One Lax-Wendroff iteration with step dts (Eqs. lw1, lw2), then the r* boundary rows.
-  // r* dissipation (NOT part of the paper's method; off unless ko_sigma > 0). The two-step
-  // Lax-Wendroff iteration damps short r* wavelengths only at a rate ~ (dt/dr*)^2 per
-  // iteration; with several iterations per dt = 0.25 dr* that damping is too weak for the
-  // modes of near-zero numerical group velocity in the region where the lower-order terms
-  // of the r^3-scaled system (c Phi' and V/Sigma^2 Phi) make a frozen wave grow. Once per
-  // outer step, before its first iteration, every component at rows 2 .. n_r - 3 becomes
-  //   u_i - eps (u_{i-2} - 4 u_{i-1} + 6 u_i - 4 u_{i+1} + u_{i+2}),  eps = sigma dt / (16 dr*),
-  // the fourth-order Kreiss-Oliger operator integrated over dt (an O(dr*^3) change for
-  // smooth fields). Window edges stay frozen as in substep().
+  // Dissipation (NOT part of the paper's method; off unless ko_sigma > 0 or ko_theta > 0).
+  // The two-step Lax-Wendroff iteration damps short r* wavelengths only at a rate
+  // ~ (dt/dr*)^2 per iteration; with several iterations per dt = 0.25 dr* that damping is
+  // too weak for the modes of near-zero numerical group velocity in the region where the
+  // lower-order terms of the r^3-scaled system (c Phi' and V/Sigma^2 Phi) make a frozen
+  // wave grow. And the theta terms sit in the source S, so for them the iteration is the
+  // explicit midpoint rule, whose amplification exceeds 1 for every oscillatory mode; the
+  // largest theta frequencies (grid-scale modes and the (m + s cos th)^2 / sin^2 th
+  // potential of the pole cells) set how many iterations per dt that needs.
+  // Once per outer step, before its first iteration, every component becomes
+  //   u - eps_r d_r^4 u - eps_th(i) d_th^12 u,
+  //   eps_r = ko_sigma dt / (16 dr*),  eps_th(i) = ko_theta c_th(i) dt / (4096 dth),
+  // with the undivided differences d_r^4 (5 points in r*, rows 2 .. n_r - 3 only) and
+  // d_th^12 = (d_th^2)^6 (13 points in theta with the parity ghosts, every interior row),
+  // c_th(i) = max_j sqrt(Delta/Sigma^2) at node i. These are Kreiss-Oliger operators of
+  // order 4 in r* and 12 in theta integrated over dt: changes of O(dr*^3) and O(dth^11)
+  // for smooth fields, so the scheme keeps its 2nd order in (t, r*) and 10th in theta.
+  // Both differences are taken from the same u. Window edges stay frozen as in substep().
   void dissipate() {
-    const T eps = T(p.ko_sigma) * dt / (T(16.0) * dr);
+    const T eps_r = T(p.ko_sigma) * dt / (T(16.0) * dr);
+    const bool do_r = p.ko_sigma > 0, do_th = p.ko_theta > 0;
     const int lo = std::max(2, 2 - p.row_lo), hi = std::min(nrow - 3, p.n_r - 3 - p.row_lo);
+    // (d^2)^6 = sum_q (-1)^q C(12, 6 + q) f_{j+q}
+    static const double kKO12[13] = {1, -12, 66, -220, 495, -792, 924, -792, 495, -220, 66, -12, 1};
     for (int c = 0; c < 4; ++c) {
       un[c] = u[c];
 #pragma omp parallel for schedule(static)
-      for (int i = lo; i <= hi; ++i)
+      for (int i = 1; i < nrow - 1; ++i) {
+        if (is_boundary_row(i)) continue;
+        const T eps_th = T(p.ko_theta) * c_theta[i] * dt / (T(4096.0) * dth);
+        const T* row = u[c].data() + (size_t)i * nth;
         for (int j = 0; j < nth; ++j) {
           const size_t k = (size_t)i * nth + j, n = (size_t)nth;
-          const T d4 = u[c][k - 2 * n] - T(4.0) * u[c][k - n] + T(6.0) * u[c][k] - T(4.0) * u[c][k + n] +
-                       u[c][k + 2 * n];
-          un[c][k] = u[c][k] - eps * d4;
+          T v = u[c][k];
+          if (do_r && i >= lo && i <= hi) {
+            const T d4 = u[c][k - 2 * n] - T(4.0) * u[c][k - n] + T(6.0) * u[c][k] - T(4.0) * u[c][k + n] +
+                         u[c][k + 2 * n];
+            v = v - eps_r * d4;
+          }
+          if (do_th) {
+            T d12 = T(0.0);
+            for (int q = -6; q <= 6; ++q) d12 = d12 + T(kKO12[q + 6]) * ext_signed(row, j + q);
+            v = v - eps_th * d12;
+          }
+          un[c][k] = v;
         }
+      }
       std::swap(u[c], un[c]);
     }
   }
@@ -370,8 +402,9 @@ struct Solver {
     sn = sin_(f_omega * t);
   }
 
+  // One Lax-Wendroff iteration with step dts (Eqs. lw1, lw2), then the r* boundary rows.
   void substep() {
-    if (p.ko_sigma > 0 && substeps_done % p.substeps == 0) dissipate();
+    if ((p.ko_sigma > 0 || p.ko_theta > 0) && substeps_done % p.substeps == 0) dissipate();
     const T half = T(0.5);
     const T hdt = dts * half;
     // forcing phases at t_n (half step) and t_n + dts/2 (full step)

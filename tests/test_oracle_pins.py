@@ -18,6 +18,8 @@
 import math
 
 import mpmath as mpm
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -349,3 +351,92 @@ def test_r_dissipation_step_by_linearity(oracle_mod):
     # the fourth difference vanishes at rows 3 .. n_r - 4 (away from the zeroed rows 0, n_r - 1);
     # one iteration spreads a difference by one row
     np.testing.assert_array_equal(one(cubic, sigma)[:, :, 4:-4], one(cubic, 0.0)[:, :, 4:-4])
+
+
+def _one_iteration(oracle_mod, p, state, ko_theta, words=4):
+    o = oracle_mod.Oracle(**p, bits=256, ko_theta=ko_theta)
+    o.set_state(state)
+    o.step(1)
+    return o.get_state(words=words)
+
+
+def _wsum(w):
+    return w[:, 0] + w[:, 1] + w[:, 2] + w[:, 3]
+
+
+def test_theta_dissipation_sawtooth_eigenvalue(oracle_mod):
+    """theta dissipation step (not part of the paper's scheme): with odd axis parity (s + m
+    odd) the theta sawtooth (-1)^j continues through the ghost cells, so it is an eigenvector
+    of (d^2)^6 with eigenvalue 4^6 and one step multiplies row i by
+    1 - sigma c_th(i) dt / dtheta, c_th(i) = max_j sqrt(Delta/Sigma^2) (the g coefficient,
+    pinned against Eq. 1). The iteration is linear, so
+    step_with(u) - step_without(u) = -step_without(sigma c_th dt / dtheta u)."""
+    n_r, nth, sigma = 19, 12, 0.8
+    p = dict(M=1.0, a=0.6, s=-1, m=2, rstar_min=-8.0, rstar_max=10.0, n_r=n_r, n_theta=nth, dt=0.0,
+             substeps=1, theta_order=10, parity=-1)
+    rng = np.random.default_rng(7)
+    saw = (-1.0) ** np.arange(nth)
+    u = rng.uniform(0.5, 1.0, (4, 1, n_r, 1)) * saw[None, None, None, :]
+    u[:, :, [0, -1]] = 0.0
+    g = oracle_mod.Oracle(**p, bits=256).coeffs(0, 1)[5, 0]  # Delta / Sigma^2 at the nodes
+    c_th = np.sqrt(g.max(axis=1))
+    dt = 0.25 * (p["rstar_max"] - p["rstar_min"]) / (n_r - 1)
+    dth = np.pi / nth
+    v = u * (sigma * c_th * dt / dth)[None, None, :, None]
+    v[:, :, [0, -1]] = 0.0
+    lhs = _wsum(_one_iteration(oracle_mod, p, u, sigma) - _one_iteration(oracle_mod, p, u, 0.0))
+    rhs = -_wsum(_one_iteration(oracle_mod, p, v, 0.0))
+    assert np.abs(rhs).max() > 0.05
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(rhs).max()
+
+
+def test_theta_dissipation_is_a_twelfth_difference(oracle_mod):
+    """(d^2)^6 annihilates every polynomial of degree <= 11 in the column index: away from the
+    poles (and from the columns the next iteration's 11-point theta stencil reads from there)
+    the step changes nothing; together with the sawtooth eigenvalue this fixes all 13
+    weights. With even parity a theta-constant row continues through the ghosts and is not
+    changed anywhere."""
+    n_r, nth, sigma = 9, 40, 1.0
+    p = dict(M=1.0, a=0.6, s=0, m=0, rstar_min=-8.0, rstar_max=10.0, n_r=n_r, n_theta=nth, dt=0.0,
+             substeps=1, theta_order=10, parity=1)
+    # an exact degree-11 polynomial in j: dyadic coefficients and x = (j - 20)/16, times dyadic
+    # row amplitudes; each value is a dyadic rational held exactly as two double words
+    coef = [Fraction(c, 8) for c in (3, -2, 5, 1, -4, 2, 6, -3, 2, 1, -3, 4)]
+    amps = [[Fraction(4 + (3 * c + 5 * i) % 5, 8) for i in range(n_r)] for c in range(4)]
+    u = np.zeros((4, 2, n_r, nth))
+    for c in range(4):
+        for i in range(1, n_r - 1):
+            for j in range(nth):
+                x = Fraction(j - 20, 16)
+                v = amps[c][i] * sum(ck * x ** k for k, ck in enumerate(coef))
+                hi = float(v)
+                lo = float(v - Fraction(hi))
+                assert Fraction(hi) + Fraction(lo) == v
+                u[c, 0, i, j], u[c, 1, i, j] = hi, lo
+    diff = _wsum(_one_iteration(oracle_mod, p, u, sigma) - _one_iteration(oracle_mod, p, u, 0.0))
+    assert np.abs(diff[:, :, :6]).max() > 1e-6          # the pole regions are changed
+    assert np.abs(diff[:, :, 11:nth - 11]).max() < 1e-40  # columns 6 .. nth-7 read none of them
+    rng = np.random.default_rng(8)
+    const = rng.uniform(0.5, 1.0, (4, 1, n_r, 1)) * np.ones((1, 1, 1, nth))
+    const[:, :, [0, -1]] = 0.0
+    d0 = _wsum(_one_iteration(oracle_mod, p, const, sigma) - _one_iteration(oracle_mod, p, const, 0.0))
+    assert np.abs(d0).max() < 1e-60
+
+
+def test_theta_dissipation_keeps_tenth_order(oracle_mod):
+    """On a smooth (regular, parity-consistent) field the step's change is
+    sigma c_th dt / (4096 dtheta) (d^2)^6 u = O(dtheta^11): halving dtheta divides it by about
+    2^11 (the scheme's 10th-order theta accuracy is kept)."""
+    sigma = 1.0
+    changes = []
+    for nth in (24, 48):
+        p = dict(M=1.0, a=0.0, s=0, m=0, rstar_min=-8.0, rstar_max=10.0, n_r=7, n_theta=nth, dt=0.0,
+                 substeps=1, theta_order=10, parity=1)
+        th = (np.arange(nth) + 0.5) * np.pi / nth
+        prof = np.cos(th) ** 2 + 0.3 * np.cos(th) ** 4 * np.sin(th) ** 2  # smooth, even at both poles
+        u = np.ones((4, 1, 7, 1)) * prof[None, None, None, :]
+        u[:, :, [0, -1]] = 0.0
+        d = _wsum(_one_iteration(oracle_mod, p, u, sigma) - _one_iteration(oracle_mod, p, u, 0.0))
+        changes.append(np.abs(d).max())
+    ratio = changes[0] / changes[1]
+    assert 2 ** 10.3 < ratio < 2 ** 11.7, (changes, np.log2(ratio))
