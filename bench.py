@@ -1,10 +1,11 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 Lax-Wendroff Teukolsky stepper: grid-point updates per second.
 
-One benchmark step is one outer time step dt = 0.25 dr* of the double-double workload
-(M = 1, a = 0.9, s = -2, m = 2, r* in [-100, 400] x 2048 nodes, theta x 128 cells), i.e.
-88 Lax-Wendroff iterations (Eqs. lw1, lw2 of arXiv:1006.0663) plus the waveform sample at
-r* = 300. A grid-point update is one point advanced by one Lax-Wendroff iteration.
+One benchmark step is one outer time step dt = 0.25 dr* of the large double-double workload
+(M = 1, a = 0.9, s = -2, m = 2, r* in [-200, 1800] x 16384 nodes, theta x 512 cells), i.e.
+81 Lax-Wendroff iterations (Eqs. lw1, lw2 of arXiv:1006.0663) on the integer engine plus the
+waveform sample at r* = 1000. A grid-point update is one point advanced by one Lax-Wendroff
+iteration. The same workload in FP64 is reported beside it with its own roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -26,7 +27,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "grid-point updates/sec (FP64, dd, qd) & % of FP64/HBM roofline at stated error"
 UNIT = "grid-point updates/s"
-WORKLOAD = "c2"
+WORKLOAD = "c5"
+# words per real of each workload's main line (c5 is measured in double-double; FP64 beside it)
+MAIN_WORDS = {"c5": 2}
 
 # FP64 pipe operations (add, mul and fma count one each) per grid point for one launch of
 # each kernel, from the operation list of the scheme in each arithmetic: dd accurate add 14,
@@ -60,15 +63,14 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
            ("c3", "full_ix_kernel<4, 1>"): (34.75e6 + 1.38e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt")}
 
 
-# Integer-engine kernels: executed thread instructions per grid point for one launch (ncu
-# thread_inst_executed / points), per kernel function (the register budgets differ in spill
-# code) from one capture of the kernel as it stands.
-IX_INST = {"half_ix_kernel<2, 2>": (4904, "profiles/step_kernels_ix_dd_c2.txt"),
-           "full_ix_kernel<2, 2>": (5289, "profiles/step_kernels_ix_dd_c2.txt"),
-           "half_ix_kernel<2, 1>": (4665, "profiles/step_kernels_ix_dd_c2.txt"),
-           "full_ix_kernel<2, 1>": (5198, "profiles/step_kernels_ix_dd_c2.txt"),
-           "half_ix_kernel<4, 1>": (9883, "profiles/step_kernels_ix_qd_c3.txt"),
-           "full_ix_kernel<4, 1>": (10954, "profiles/step_kernels_ix_qd_c3.txt")}
+# Integer engine: algorithmic work per grid point of one launch (half or full kernel), in
+# 32-bit limb multiply-add pairs (mad.lo / madc.hi with the carry, the product window's unit).
+# Each of the two components of a point forms 11 products (Phi row: the table term and the
+# h/4 or h/2 term, the 1/2 and 1 terms being shifts; Pi row: nine table terms), 10 partial
+# products each in double-double (4 x 4 limbs, columns 3..6) and 36 in quad-double (8 x 8
+# limbs, columns 7..14), and the theta stencil's 11 integer multiply-adds (6 for D2, 5 for D1)
+# on a row of 6 (dd) / 10 (qd) limbs: 22 x 10 + 22 x 6 = 352 and 22 x 36 + 22 x 10 = 1012.
+IX_PAIRS = {2: 22 * 10 + 22 * 6, 4: 22 * 36 + 22 * 10}
 
 
 def kernel_name(dom, W, shape, engine=0):
@@ -93,7 +95,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-member batched workload")
     ap.add_argument("--workload", default=WORKLOAD, choices=["c1", "c2", "c3", "c5", "tails"],
-                    help="workload of the main line (default c2, the benchmark configuration)")
+                    help="workload of the main line (default c5 in double-double, the roofline "
+                         "configuration)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 4],
                     help="words per real (0: the workload's own precision)")
     ap.add_argument("--engine", type=int, default=-1, choices=[-1, 0, 1],
@@ -104,6 +107,8 @@ def parse():
                          "instead of autotuning (profiling)")
     ap.add_argument("--digits", action="store_true",
                     help="print the cost-per-digit table (errors vs the oracle and each other)")
+    ap.add_argument("--c4-steps", type=int, default=4,
+                    help="outer steps of the 64-member batch timed in one cooperative launch")
     return ap.parse_args()
 
 
@@ -195,8 +200,8 @@ def run_workload(prob, words, steps, warmup, torch, teuk, flush, with_timing=Tru
 
 
 def stated_error(prob, words, teuk, nsub=12, engine=0):
-    """Error of this workload's GPU state against the 256-bit oracle (FP64 oracle for FP64)
-    after nsub Lax-Wendroff iterations, on a window of rows around the pulse, where the window
+    """Error of this workload's GPU state against the 256-bit oracle after nsub Lax-Wendroff
+    iterations, on a window of rows around the pulse, where the window
     interior is exact (domain of dependence)."""
     import oracle
     oracle.build()
@@ -212,10 +217,11 @@ def stated_error(prob, words, teuk, nsub=12, engine=0):
     ic = int(round((prob.center - prob.rstar_min) / prob.dr))
     lo, hi = ic - 12, ic + 12
     wlo, whi = max(0, lo - nsub - 1), min(prob.n_r - 1, hi + nsub + 1)
-    bits = 53 if words == 1 else 256
+    bits = 256
     o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
                       rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
-                      substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=bits)
+                      substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=bits,
+                      ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta)
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     o.step(nsub)
     err, _ = o.max_rel_err(full[:, :, wlo:whi + 1].copy(), lo - wlo, hi - wlo)
@@ -242,10 +248,10 @@ def run_batch1(prob, words, steps, torch, teuk):
     return prob.n_r * prob.n_theta * prob.substeps * steps / dt, dt / steps * 1e3
 
 
-def run_c4(torch, teuk, workloads, engine=1):
-    """The 64-member double-double batch: one cooperative launch per outer step against the
-    same members stepped one at a time (CUDA graphs on), equal arithmetic (bit-identical), on
-    the given multi-word engine."""
+def run_c4(torch, teuk, workloads, engine=1, steps=4):
+    """The 64-member double-double batch: `steps` outer steps in one cooperative launch against
+    the same members stepped one at a time (CUDA graphs on) over the same window, CUDA events
+    on the shared stream, equal arithmetic (bit-identical), on the given multi-word engine."""
     members = []
     for i in range(workloads.BATCH_SIZE):
         p = workloads.batch_member(i)
@@ -254,40 +260,48 @@ def run_c4(torch, teuk, workloads, engine=1):
             g.set_engine(engine)
         ar, ai = p.amps
         g.set_initial_pulse(p.center, p.width, ar, ai, p.ell)
-        g.set_observer(p.rstar_obs, capacity=8)
+        g.set_observer(p.rstar_obs, capacity=2 * steps + 4)
         members.append(g)
     pts = sum(g.n_r * g.n_theta * g.substeps for g in members)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for g in members:
         g.step(1)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    ev[0].record(stream)
     for g in members:
-        g.step(1)
+        g.step(steps)
+    ev[1].record(stream)
     torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
     b = teuk.Batch(members)
     b.step(1)
     b.sync()
-    t0 = time.perf_counter()
-    b.step(1)
+    launches0 = b.info()["launches"]
+    ev[2].record(stream)
+    b.step(steps)
+    ev[3].record(stream)
     b.sync()
-    t_bat = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t_seq = ev[0].elapsed_time(ev[1]) * 1e-3
+    t_bat = ev[2].elapsed_time(ev[3]) * 1e-3
     info = b.info()
     b.close()
     for g in members:
         g.close()
     return {"workload": "c4: 64 double-double members, n_r U[512,4096], n_theta {32..256}, "
                         "m in [-4,4], s in {0,-1,-2}, a U[0,0.99], substeps 1..454 (seeds 1000+i)",
+            "outer_steps_timed": steps, "cooperative_launches": info["launches"] - launches0,
             "updates_per_outer_step": pts,
-            "batched_updates_per_s": pts / t_bat, "one_at_a_time_updates_per_s": pts / t_seq,
-            "speedup": t_seq / t_bat, "batched_ms_per_step": t_bat * 1e3,
-            "one_at_a_time_ms_per_step": t_seq * 1e3, "grid_blocks": info["grid"],
-            "arithmetic": ENGINE_NAME[engine]}
+            "batched_updates_per_s": pts * steps / t_bat, "one_at_a_time_updates_per_s": pts * steps / t_seq,
+            "speedup": t_seq / t_bat, "batched_ms_per_step": t_bat * 1e3 / steps,
+            "one_at_a_time_ms_per_step": t_seq * 1e3 / steps, "grid_blocks": info["grid"],
+            "timing": "CUDA events on the shared stream", "arithmetic": ENGINE_NAME[engine]}
 
 
-def run_e2e(prob, words, steps, torch, teuk, engine=0):
+def run_e2e(prob, words, steps, torch, teuk, flush, engine=0):
     """Through the public API with host buffers: per step H2D of the state from pinned host
-    memory, one outer step, D2H of the observer row."""
+    memory, one outer step, D2H of the observer row. As in the device-timed loop, the 256 MiB
+    L2 flush runs between steps outside the timed interval."""
     import numpy as np
     g = teuk.Teuk.from_problem(prob, precision=words)
     if engine:
@@ -302,17 +316,20 @@ def run_e2e(prob, words, steps, torch, teuk, engine=0):
     g.step(1)  # warm-up
     g.observe(prob.rstar_obs)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    total = 0.0
     for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         g.set_state(host)
         g.step(1)
         obs, _ = g.observe(prob.rstar_obs)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+        total += time.perf_counter() - t0
     g.close()
     upd = prob.n_r * prob.n_theta * prob.substeps * steps
-    return dict(value=upd / dt, unit=UNIT, h2d_bytes_per_step=int(state.nbytes),
-                d2h_bytes_per_step=int(obs.nbytes))
+    return dict(value=upd / total, unit=UNIT, h2d_bytes_per_step=int(state.nbytes),
+                d2h_bytes_per_step=int(obs.nbytes),
+                l2="flushed between steps outside the timed interval, as for value")
 
 
 def run_design_a(prob, words, iters, torch, teuk, engine=0):
@@ -350,14 +367,26 @@ def run_design_a(prob, words, iters, torch, teuk, engine=0):
             "link_gbps_effective": link * iters / (t_a - t_r) / 1e9 if t_a > t_r else None}
 
 
-def roofline_for(res, prob, W, engine, clocks, sms, probe, workload):
+def measured_hbm_peak():
+    """HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def roofline_for(res, prob, W, engine, clocks, sms, fp64_probe, int_probe, workload):
     """Roofline of the dominant step kernel of a run (live CUDA-event launch durations).
 
-    FP64 error-free-transform kernels: bound by the FP64 pipe, 2 operations per SM per cycle
-    (ncu sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per cycle for
-    152 SMs), counted from the scheme's operation list. Integer-engine kernels (double-double):
-    bound by instruction issue, 4 warp instructions = 128 thread instructions per SM per cycle,
-    counted as the executed thread instructions per point of the ncu capture."""
+    FP64 error-free-transform kernels (and FP64): bound by the FP64 pipe, 2 operations per SM
+    per cycle (ncu sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per
+    cycle for 152 SMs) at the SM clock sampled during the timed region, counted from the
+    scheme's operation list (OPS_HALF / OPS_FULL). Integer-engine kernels: bound by the
+    integer multiply-add pipe, counted as the product windows' and stencils' 32-bit limb
+    multiply-add pairs the scheme needs per point (IX_PAIRS), against the measured throughput
+    of the engine's own product window on every SM (teuk_int_peak). The HBM fraction of the
+    kernel's algorithmic bytes is reported beside either."""
     ms_h, ms_f, n_h, n_f = res["kernel_times"]
     pts_h = (prob.n_r - 1) * prob.n_theta
     pts_f = (prob.n_r - 2) * prob.n_theta
@@ -371,30 +400,43 @@ def roofline_for(res, prob, W, engine, clocks, sms, probe, workload):
     mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
     kname = kernel_name(dom, W, res["rows_per_block"], engine)
     tr = TRAFFIC.get((workload, kname))
-    if engine == 1:
-        ops_pt, ops_src = IX_INST.get(kname, (None, "not captured"))
-        peak = 128.0 * sms * mhz * 1e6
-        peak_source = f"4 warp instructions/SM/cycle x 32 threads x {sms} SMs x {mhz:.0f} MHz (issue limit)"
-        op_unit = f"executed thread instructions per point, ncu capture ({ops_src})"
+    fp64_peak = 2.0 * sms * mhz * 1e6
+    fp64_ops = (OPS_HALF[W] if dom == "half" else OPS_FULL[W]) * pts / (avg * 1e-3)
+    ix = engine == 1 and W > 1
+    bpp = ((BYTES_HALF_IX if ix else BYTES_HALF)[W] if dom == "half" else (BYTES_FULL_IX if ix else BYTES_FULL)[W])
+    hbm_peak, hbm_src = measured_hbm_peak()
+    hbm = bpp * pts / (avg * 1e-3) / 1e9
+    if ix:
+        ops_pt = IX_PAIRS[W]
+        peak = int_probe
+        peak_source = ("measured product-window throughput of this GPU (teuk_int_peak: independent "
+                       "windows on every SM, 10 partial products each)")
+        op_unit = "32-bit limb multiply-add pairs (product windows and theta stencils) per point"
+        unit = "T pairs/s"
     else:
         ops_pt = OPS_HALF[W] if dom == "half" else OPS_FULL[W]
-        peak = 2.0 * sms * mhz * 1e6
+        peak = fp64_peak
         peak_source = f"2 FP64 ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (SM clock sampled during the timed region)"
         op_unit = "FP64 pipe operations (add, mul, fma count one each)"
-    achieved = ops_pt * pts / (avg * 1e-3) if ops_pt else None
-    return {
-        "bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
-        "unit": "T inst/s" if engine == 1 else "Tops/s",
-        "frac": achieved / peak if achieved else None, "traffic": tr[0] if tr else None,
+        unit = "Tops/s"
+    achieved = ops_pt * pts / (avg * 1e-3)
+    out = {
+        "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
+        "frac": achieved / peak, "traffic": tr[0] if tr else None,
         "traffic_source": f"{tr[2]} (launch shape {tr[1]})" if tr else None,
         "kernel": kname, "avg_launch_ms": avg, "launch_shape": res["rows_per_block"],
-        "ops_per_point": ops_pt, "peak_source": peak_source, "op_unit": op_unit,
-        "fma_chain_probe_tops": probe / 1e12,
-        "hbm_achieved_gbs": ((BYTES_HALF_IX if engine == 1 else BYTES_HALF)[W] if dom == "half"
-                             else (BYTES_FULL_IX if engine == 1 else BYTES_FULL)[W]) * pts / (avg * 1e-3) / 1e9,
-        "fraction_of_step_in_dominant_kernel": (avg_h if dom == "half" else avg_f) * res["launches"] / 2
-        / max(res["ms_total"], 1e-9),
+        "points_per_launch": pts, "ops_per_point": ops_pt, "peak_source": peak_source, "op_unit": op_unit,
+        "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak,
+                "bytes_per_point": bpp, "peak_source": hbm_src},
+        "fma_chain_probe_tops": fp64_probe / 1e12,
+        "fraction_of_step_in_dominant_kernel": avg * res["launches"] / 2 / max(res["ms_total"], 1e-9),
     }
+    if ix:
+        out["fp64_equivalent"] = {
+            "method_fp64_ops_per_point": OPS_HALF[W] if dom == "half" else OPS_FULL[W],
+            "x_fp64_pipe_peak": fp64_ops / fp64_peak,
+            "note": "the same step in FP64 error-free transforms would need this multiple of the FP64 pipe"}
+    return out
 
 
 def cpu_model():
@@ -434,7 +476,8 @@ def cpu_baseline(prob, words, seconds_target=15.0):
     o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
                       rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                       substeps=prob.substeps, parity=prob.parity, row_lo=lo,
-                      row_hi=min(prob.n_r - 1, lo + rows - 1), bits=bits)
+                      row_hi=min(prob.n_r - 1, lo + rows - 1), bits=bits, ko_sigma=prob.ko_sigma,
+                      ko_theta=prob.ko_theta)
     ar, ai = prob.amps
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     done, t0 = 0, time.perf_counter()
@@ -457,19 +500,20 @@ def reference_arm(args):
     if rank != 0:
         return 0
     prob = workloads.CONFIGS[WORKLOAD]
+    W = MAIN_WORDS.get(WORKLOAD, prob.words)
     per_step_s = 4.0
     # warm-up and K timed steps, each a bounded sample of the workload
     for _ in range(args.warmup):
-        cpu_baseline(prob, prob.words, seconds_target=0.5)
-    vals = [cpu_baseline(prob, prob.words, seconds_target=per_step_s) for _ in range(args.steps)]
+        cpu_baseline(prob, W, seconds_target=0.5)
+    vals = [cpu_baseline(prob, W, seconds_target=per_step_s) for _ in range(args.steps)]
     tot_upd = sum(v["value"] * per_step_s for v in vals)
     value = sum(v["value"] for v in vals) / len(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": DTYPE[prob.words], "data": "synthetic",
-        "config": {"workload": describe(prob)},
+        "dtype": DTYPE[W], "data": "synthetic",
+        "config": {"workload": describe(prob, W)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
                          "sample": vals[0]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -492,12 +536,16 @@ def aggregate_ranks(t_local_ms, updates_per_rank, world, dist, torch, device):
     return t_max, world * updates_per_rank / (t_max * 1e-3)
 
 
-def describe(prob):
-    return (f"{prob.name}: {DTYPE[prob.words]}, M={prob.M}, a={prob.a}, s={prob.s}, m={prob.m}, "
+def describe(prob, words=None):
+    w = words or prob.words
+    diss = ""
+    if prob.ko_sigma or prob.ko_theta:
+        diss = f", dissipation r* {prob.ko_sigma} theta {prob.ko_theta} (not in the paper)"
+    return (f"{prob.name}: {DTYPE[w]}, M={prob.M}, a={prob.a}, s={prob.s}, m={prob.m}, "
             f"r* in [{prob.rstar_min}, {prob.rstar_max}] x {prob.n_r} nodes, theta x {prob.n_theta} "
-            f"cells, 10th-order theta, dt=0.25 dr* with {prob.substeps} Lax-Wendroff iterations "
-            f"per step, Gaussian pulse (center {prob.center}, width {prob.width}, seed "
-            f"{prob.seed}), waveform at r*={prob.rstar_obs} every step")
+            f"cells, {prob.theta_order}th-order theta, dt=0.25 dr* with {prob.substeps} Lax-Wendroff "
+            f"iterations per step, Gaussian pulse (center {prob.center}, width {prob.width}, seed "
+            f"{prob.seed}), waveform at r*={prob.rstar_obs} every step{diss}")
 
 
 def word_diff(a, b):
@@ -606,7 +654,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prob = workloads.CONFIGS[args.workload]
-    W = args.precision or prob.words
+    W = args.precision or MAIN_WORDS.get(args.workload, prob.words)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)  # the library handles are created on this stream
@@ -624,39 +672,52 @@ def main():
 
     out = None
     if rank == 0:
-        describe_w = describe(prob) if W == prob.words else describe(prob).replace(DTYPE[prob.words], DTYPE[W])
+        describe_w = describe(prob, W)
         sms = torch.cuda.get_device_properties(local).multi_processor_count
-        roofline = roofline_for(res, prob, W, engine, clocks, sms, teuk.fp64_peak(), args.workload)
-        e2e = run_e2e(prob, W, max(3, args.steps // 2), torch, teuk, engine)
-        if W != prob.words or args.workload != WORKLOAD:
+        fp64_probe, int_probe = teuk.fp64_peak(), teuk.int_peak()
+        roofline = roofline_for(res, prob, W, engine, clocks, sms, fp64_probe, int_probe, args.workload)
+        e2e = run_e2e(prob, W, max(3, args.steps // 4), torch, teuk, flush, engine)
+        if args.workload != WORKLOAD or W != MAIN_WORDS.get(WORKLOAD):
             args.no_variants = args.no_batch = True
         variants = {}
         if not args.no_variants:
-            for name, w, nst in (("c1", 1, 20), ("c5", 1, 2), ("c3", 4, 2), ("c5", 2, 1)):
+            # the same workload in FP64: its own roofline, end-to-end figure and oracle error
+            r = run_workload(prob, 1, 3, 1, torch, teuk, flush)
+            variants[f"{prob.name}/f64"] = {
+                "updates_per_s": r["points"] * r["substeps"] * 3 / (r["ms_total"] * 1e-3),
+                "ms_per_step": r["ms_total"] / 3, "launch": "CUDA graph per outer step",
+                "roofline": roofline_for(r, prob, 1, 0, clocks, sms, fp64_probe, int_probe, args.workload),
+                "e2e": run_e2e(prob, 1, 3, torch, teuk, flush, 0),
+                "error_vs_oracle": None if args.no_cpu else stated_error(prob, 1, teuk)}
+            # the main workload on the other multi-word engine
+            other = 1 - engine
+            r0 = run_workload(prob, W, 2, 1, torch, teuk, flush, engine=other)
+            variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} {ENGINE_NAME[other]}"] = {
+                "updates_per_s": r0["points"] * r0["substeps"] * 2 / (r0["ms_total"] * 1e-3),
+                "roofline": roofline_for(r0, prob, W, other, clocks, sms, fp64_probe, int_probe, args.workload)}
+            for name, w, nst in (("c1", 1, 20), ("c2", 2, 4), ("c3", 4, 2)):
                 p = workloads.CONFIGS[name]
-                r = run_workload(p, w, nst, 1, torch, teuk, flush, with_timing=False, engine=1 if w > 1 else 0)
-                variants[f"{name}/{DTYPE[w].split(' ')[0]}"] = {
-                    "updates_per_s": p.n_r * p.n_theta * p.substeps * nst / (r["ms_total"] * 1e-3),
-                    "ms_per_step": r["ms_total"] / nst, "launch": "CUDA graph per outer step"}
+                r = run_workload(p, w, nst, 1, torch, teuk, flush, engine=1 if w > 1 else 0)
+                entry = {"updates_per_s": p.n_r * p.n_theta * p.substeps * nst / (r["ms_total"] * 1e-3),
+                         "ms_per_step": r["ms_total"] / nst, "launch": "CUDA graph per outer step"}
+                if w > 1:
+                    entry["roofline"] = roofline_for(r, p, w, 1, clocks, sms, fp64_probe, int_probe, name)
+                variants[f"{name}/{DTYPE[w].split(' ')[0]}"] = entry
             ups, msps = run_batch1(workloads.CONFIGS["c1"], 1, 20, torch, teuk)
             variants["c1/f64 batched kernel"] = {"updates_per_s": ups, "ms_per_step": msps,
                                                  "launch": "one cooperative launch, 20 steps"}
-            p2 = prob.with_(theta_order=2)
-            r = run_workload(p2, W, 2, 1, torch, teuk, flush, with_timing=False, engine=engine)
-            variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} 2nd-order theta"] = {
+            c2 = workloads.CONFIGS["c2"]
+            p2 = c2.with_(theta_order=2)
+            r = run_workload(p2, 2, 2, 1, torch, teuk, flush, with_timing=False, engine=1)
+            variants["c2/f64x2 2nd-order theta"] = {
                 "updates_per_s": p2.points * p2.substeps * 2 / (r["ms_total"] * 1e-3),
                 "ms_per_step": r["ms_total"] / 2, "launch": "CUDA graph per outer step"}
-            variants["design_a_host_state"] = run_design_a(prob, W, 2 * prob.substeps, torch, teuk, engine)
-            if W > 1:
-                other = 1 - engine
-                r0 = run_workload(prob, W, max(2, args.steps // 2), 2, torch, teuk, flush, engine=other)
-                variants[f"{prob.name}/{DTYPE[W].split(' ')[0]} {ENGINE_NAME[other]}"] = {
-                    "updates_per_s": r0["points"] * r0["substeps"] * max(2, args.steps // 2) / (r0["ms_total"] * 1e-3),
-                    "roofline": roofline_for(r0, prob, W, other, clocks, sms, teuk.fp64_peak(), args.workload)}
+            variants["design_a_host_state"] = run_design_a(c2, 2, 2 * c2.substeps, torch, teuk, 1)
+            variants["design_a_host_state"]["workload"] = "c2, double-double, integer engine"
         batched = None
         if not args.no_batch:
-            batched = run_c4(torch, teuk, workloads, engine=1)
-            batched["other_engine"] = run_c4(torch, teuk, workloads, engine=0)
+            batched = run_c4(torch, teuk, workloads, engine=1, steps=args.c4_steps)
+            batched["other_engine"] = run_c4(torch, teuk, workloads, engine=0, steps=1)
         cpu = None if args.no_cpu else cpu_baseline(prob, W)
         if cpu is not None:
             cpu["cpu_model"] = cpu_model()
@@ -670,7 +731,7 @@ def main():
             "config": {"workload": describe_w,
                        "arithmetic": ENGINE_NAME[engine] if W > 1 else "FP64",
                        "l2": "256 MiB buffer written between timed steps (outside the timed "
-                             "interval); the 100 MB working set is L2-resident within a step",
+                             "interval); the state and tables exceed L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -96,6 +96,13 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
  * FP64 handles accept 0 only. */
 int teuk_set_engine(teuk_t h, int engine);
 int teuk_engine(teuk_t h);
+/* Test hook of the integer engine's bounded wait (no counterpart in the paper): from the next
+ * launch on, thread block `block` of each engine step kernel arms its copy barrier with the
+ * expected byte count but issues no copy, so its wait gives up after 2^wait_log2 tries
+ * (10 <= wait_log2 <= 20) with nothing in flight; the kernel then skips that block's rows and
+ * teuk_sync reports TEUK_ERR_TIMEOUT. The kernels stage at least their table rows while the
+ * hook is set. block = -1 restores normal operation (wait limit 2^20). Engine 1 handles only. */
+int teuk_test_stall_copies(teuk_t h, int block, int wait_log2);
 
 /* r* dissipation. NOT part of the paper's method (sigma = 0, the default, is the paper's
  * scheme). With several Lax-Wendroff iterations per dt = 0.25 dr*, the scheme's own damping
@@ -109,6 +116,24 @@ int teuk_engine(teuk_t h);
  * state-sized device buffer. Handles with sigma > 0 cannot join a batch or use
  * teuk_substep_noalloc. */
 int teuk_set_dissipation(teuk_t h, double sigma);
+/* theta dissipation. NOT part of the paper's method (sigma = 0, the default, is the paper's
+ * scheme). The theta terms sit in the source S, so for them each Lax-Wendroff iteration acts
+ * like the explicit midpoint rule, which amplifies every oscillation; the grid-scale theta
+ * modes have the largest frequencies and set how many iterations per dt are needed. With
+ * sigma > 0 the dissipation step at the start of every outer step (the one of
+ * teuk_set_dissipation; both terms read the same input) also subtracts
+ *   eps_th(i) (d_th^2)^6 u,   eps_th(i) = sigma c_th(i) dt / (4096 dtheta),
+ *   (d_th^2)^6 u_j = sum_{q=-6..6} (-1)^q C(12, 6+q) u_{j+q} (parity ghosts at the poles),
+ * c_th(i) = max_j sqrt(Delta/Sigma^2) at node i, from every component at rows 1 .. n_r - 2: the
+ * 12th-order Kreiss-Oliger operator integrated over one outer step (an O(dtheta^11) change for
+ * smooth fields: the 10th-order theta accuracy is kept; the grid-scale mode is multiplied by
+ * 1 - sigma c_th dt / dtheta). 0 <= sigma <= 4 and sigma max_i c_th(i) dt / dtheta <= 2, else
+ * TEUK_ERR_INVALID_ARG and the sigma in use is kept. Allocates one state-sized buffer and one row table; handles with it
+ * cannot join a batch or use teuk_substep_noalloc. It damps grid-scale theta modes only: the
+ * pole-cell modes of the (m + s cos th)^2 / sin^2 th potential and resolved multipoles are
+ * left as they are. teuk_theta_dissipation returns the sigma in use. */
+int teuk_set_theta_dissipation(teuk_t h, double sigma);
+double teuk_theta_dissipation(teuk_t h);
 
 /* Advances n outer steps (n * substeps Lax-Wendroff iterations), asynchronously on the
  * handle's stream. The observer ring (if any) gets one sample per outer step. */
@@ -123,7 +148,8 @@ int teuk_use_graphs(teuk_t h, int enable);
 int teuk_substep(teuk_t h, int64_t n_iterations);
 /* Waits for the handle's stream; returns TEUK_ERR_NONFINITE if any Inf/NaN was produced, and
  * TEUK_ERR_TIMEOUT if a step kernel's wait for its own copies into shared memory reached its
- * iteration limit (the kernel then skipped its rows). */
+ * iteration limit (the kernel then skipped its rows). Either error stays until the state is
+ * replaced (teuk_set_initial, teuk_set_initial_pulse, teuk_set_state clear it). */
 int teuk_sync(teuk_t h);
 
 /* Phi at the node nearest rstar_obs (ties toward the lower index): out[2][w][n_theta]. */
@@ -210,7 +236,8 @@ int teuk_tune(teuk_t h, int* rows_per_block);
  * (blocks of up to 256 threads), or <= 102 registers in blocks of up to 128 threads;
  * 3, 4, 5 = one warp per (row, 32 theta columns) with <= 255, 128, 85 registers;
  * 6, 7, 8 = balanced: as many blocks of threads_theta threads as fit on the GPU at once,
- * each taking the same number of (row, theta) points, budgets as for 0, 1, 2. */
+ * each taking the same number of (row, theta) points, budgets as for 0, 1, 2; 9 = persistent
+ * (teuk_set_persistent). */
 int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant);
 /* Sets the launch shape explicitly (same meaning as above; threads_theta a multiple of 32,
  * threads_theta * rows_per_block <= 256; both ignored for variants 3..5, rows_per_block
@@ -219,6 +246,19 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
  * else TEUK_ERR_INVALID_ARG; the autotuner skips such shapes). Results do not depend on the
  * shape. */
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant);
+/* Persistent launches for small problems (FP64, or the FP64 error-free transforms): teuk_step
+ * runs steps_per_launch outer steps (k iterations each, Eqs. lw1, lw2) per cooperative launch
+ * of ceil((n_r - 1) / rows_per_block) blocks of threads_theta x rows_per_block threads
+ * (threads_theta 0: n_theta rounded up to 32, at most 256 / rows_per_block). Block b owns the
+ * half rows and nodes [b R, (b + 1) R); neighbouring blocks wait on each other's progress
+ * counters (bounded waits: a wait that reaches its limit ends the launch and teuk_sync reports
+ * TEUK_ERR_TIMEOUT) instead of the launch boundaries between phases. Results are bit-identical
+ * to the other launch shapes. teuk_step returns TEUK_ERR_INVALID_ARG if the blocks cannot all
+ * be resident at once; teuk_substep and handles with dissipation use the rows-per-block
+ * kernels of the same shape. teuk_launch_shape reports variant 9; teuk_tune tries it (1, 2, 4
+ * or 8 rows; 1 or 8 outer steps per launch) against the best other shape run as a CUDA graph,
+ * and keeps whichever is faster. 1 <= rows_per_block <= 8, 1 <= steps_per_launch <= 4096. */
+int teuk_set_persistent(teuk_t h, int threads_theta, int rows_per_block, int steps_per_launch);
 
 /* Lax-Wendroff iterations that allocate nothing, for callers that cannot let a library
  * allocate device memory while they step (their memory belongs to a pool of their own, or
@@ -258,6 +298,11 @@ int teuk_kernel_times(teuk_t h, double* ms_half, double* ms_full, int64_t* n_hal
 /* Measured FP64 pipe throughput of the current device (a chain of independent FMAs on every
  * SM): operations per second, counting one per FMA. */
 int teuk_fp64_peak(double* ops_per_second);
+/* Measured throughput of the integer engine's product window on the current device: 32-bit
+ * limb partial products per second (a mad.lo / madc.hi pair with its carry each; a
+ * double-double product window has 10, a quad-double one 36), from independent windows on
+ * every SM. The roofline unit of the integer engine. */
+int teuk_int_peak(double* pairs_per_second);
 
 const char* teuk_strerror(int code);
 const char* teuk_last_error(teuk_t h);

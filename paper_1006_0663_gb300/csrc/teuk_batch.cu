@@ -70,7 +70,7 @@ const void* kernel_for(int W) {
 teuk::IxArgs member_ix_args(const teuk_s* h) {
   const int U = h->W / 2;  // uint4 per engine mantissa: 1 (dd), 2 (qd)
   const size_t ncn = (size_t)teuk::kIxPlanes * h->n_r * h->pitch;
-  return teuk::IxArgs{member_args(h), h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, 0};
+  return teuk::IxArgs{member_args(h), h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, 0, 20, -1};
 }
 
 void free_batch(teuk_batch_s* b) {
@@ -102,7 +102,7 @@ int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members) {
   b->stream = b->members[0]->stream;
   b->engine = b->members[0]->engine;
   for (teuk_s* h : b->members)
-    if (h->W != b->W || h->device != b->device || h->ko_sigma > 0 || h->engine != b->engine ||
+    if (h->W != b->W || h->device != b->device || h->dissipating() || h->engine != b->engine ||
         (h->engine == 1 && !h->ix_m)) {
       delete b;
       return TEUK_ERR_INVALID_ARG;

@@ -26,6 +26,28 @@ int dispatch_substep(teuk_s* h, bool record, int64_t slot) {
   }
 }
 
+int dispatch_persist(teuk_s* h, int64_t n_outer, long long ring_base) {
+  switch (h->W) {
+    case 1: return teuk::persist_w1(h, n_outer, ring_base);
+    case 2: return teuk::persist_w2(h, n_outer, ring_base);
+    default: return teuk::persist_w4(h, n_outer, ring_base);
+  }
+}
+
+// Outer steps through the persistent kernel: one cooperative launch per persist_steps steps.
+int step_persistent(teuk_s* h, int64_t n) {
+  int64_t done = 0;
+  while (done < n) {
+    const int64_t chunk = std::min<int64_t>(h->persist_steps, n - done);
+    const int rc = dispatch_persist(h, chunk, h->ring ? h->n_recorded : 0);
+    if (rc != TEUK_OK) return rc;
+    h->substeps_done += chunk * h->k;
+    if (h->ring) h->n_recorded += chunk;
+    done += chunk;
+  }
+  return TEUK_OK;
+}
+
 int dispatch_dissipate(teuk_s* h) {
   switch (h->W) {
     case 1: return teuk::dissipate_w1(h);
@@ -37,7 +59,7 @@ int dispatch_dissipate(teuk_s* h) {
 // One Lax-Wendroff iteration, preceded by the r* dissipation step when it is enabled and an
 // outer step begins (the iteration count is a multiple of k).
 int iterate(teuk_s* h, bool record, int64_t slot) {
-  if (h->ko_sigma > 0 && h->substeps_done % h->k == 0) {
+  if (h->dissipating() && h->substeps_done % h->k == 0) {
     int rc = dispatch_dissipate(h);
     if (rc) return rc;
   }
@@ -56,7 +78,8 @@ void drop_graph(teuk_s* h);
 
 void free_all(teuk_s* h) {
   double** bufs[] = {&h->u, &h->uh, &h->cn_raw, &h->ch_raw, &h->cn, &h->ch, &h->wts, &h->lfac, &h->sin_th,
-                     &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring, &h->u_ko};
+                     &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring, &h->u_ko,
+                     &h->eps_th};
   for (double** b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -67,6 +90,9 @@ void free_all(teuk_s* h) {
   h->ix_e = nullptr;
   if (h->status) cudaFree(h->status);
   h->status = nullptr;
+  if (h->pflags) cudaFree(h->pflags);
+  h->pflags = nullptr;
+  h->pflags_cap = 0;
   if (h->d_ring_counter) cudaFree(h->d_ring_counter);
   h->d_ring_counter = nullptr;
   drop_graph(h);
@@ -145,7 +171,7 @@ void drop_graph(teuk_s* h) {
 bool graphs_possible(const teuk_s* h) {
   const cudaStream_t legacy = (cudaStream_t)0x1;
   return h->use_graphs && h->stream != nullptr && h->stream != legacy &&
-         (h->ko_sigma == 0 || h->substeps_done % h->k == 0);
+         (!h->dissipating() || h->substeps_done % h->k == 0);
 }
 
 // Captures one outer step: k iterations, the last one recording the observer row at slot
@@ -171,7 +197,7 @@ int build_graph(teuk_s* h, bool record) {
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return teuk::cuda_fail(h, e, "cudaStreamBeginCapture");
   h->capturing = true;
-  int rc = h->ko_sigma > 0 ? dispatch_dissipate(h) : TEUK_OK;
+  int rc = h->dissipating() ? dispatch_dissipate(h) : TEUK_OK;
   for (int q = 0; q < h->k && rc == TEUK_OK; ++q) {
     h->time_this = q == h->k - 1;  // the graph times the last iteration of the outer step only
     rc = dispatch_substep(h, record && q == h->k - 1, -1);
@@ -377,6 +403,7 @@ int teuk_set_initial(teuk_t h, const double* phi_pi) {
   }
   h->substeps_done = 0;
   h->n_recorded = 0;
+  TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   return TEUK_OK;
 }
@@ -393,6 +420,7 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
   }
   h->substeps_done = 0;
   h->n_recorded = 0;
+  if (rc == TEUK_OK) TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
   return rc;
 }
 
@@ -444,6 +472,18 @@ int teuk_set_engine(teuk_t h, int engine) {
 
 int teuk_engine(teuk_t h) { return h ? h->engine : TEUK_ERR_INVALID_ARG; }
 
+int teuk_test_stall_copies(teuk_t h, int block, int wait_log2) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (h->engine != 1) return invalid(h, "stall test: the bounded copy wait belongs to the integer engine");
+  if (block < -1 || wait_log2 < 10 || wait_log2 > 20)
+    return invalid(h, "stall test: block >= -1, 10 <= wait_log2 <= 20");
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  h->test_stall_block = block;
+  h->wait_log2 = block < 0 ? 20 : wait_log2;
+  return TEUK_OK;
+}
+
 int teuk_set_dissipation(teuk_t h, double sigma) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   if (!(sigma >= 0) || !std::isfinite(sigma) || sigma > 4.0)
@@ -460,8 +500,44 @@ int teuk_set_dissipation(teuk_t h, double sigma) {
   }
 }
 
+int teuk_set_theta_dissipation(teuk_t h, double sigma) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (!(sigma >= 0) || !std::isfinite(sigma) || sigma > 4.0)
+    return invalid(h, "theta dissipation: need 0 <= sigma <= 4");
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  if (sigma == 0) {
+    h->ko_theta = 0;
+    return TEUK_OK;
+  }
+  if (!h->u_ko) TEUK_CUDA(h, cudaMalloc(&h->u_ko, (size_t)4 * h->W * h->n_r * h->pitch * sizeof(double)));
+  if (!h->eps_th) TEUK_CUDA(h, cudaMalloc(&h->eps_th, (size_t)h->W * h->n_r * sizeof(double)));
+  auto table = [&](double sg, double* rate) {
+    switch (h->W) {
+      case 1: return teuk::theta_dissipation_w1(h, sg, rate);
+      case 2: return teuk::theta_dissipation_w2(h, sg, rate);
+      default: return teuk::theta_dissipation_w4(h, sg, rate);
+    }
+  };
+  double rate = 0;
+  int rc = table(sigma, &rate);
+  if (rc != TEUK_OK) return rc;
+  if (rate > 2.0) {  // refused: the table of the sigma in use is restored
+    double old_rate = 0;
+    if (h->ko_theta > 0 && (rc = table(h->ko_theta, &old_rate)) != TEUK_OK) return rc;
+    return invalid(h, "theta dissipation: sigma c_th dt / dtheta must not exceed 2 (the step would "
+                      "amplify the grid-scale theta mode)");
+  }
+  h->ko_theta = sigma;
+  return TEUK_OK;
+}
+
+double teuk_theta_dissipation(teuk_t h) { return h ? h->ko_theta : -1.0; }
+
 int teuk_step(teuk_t h, int64_t n) {
   if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
+  if (n > 0 && h->kernel_family == 3 && h->engine == 0 && !h->dissipating() && h->substeps_done % h->k == 0)
+    return step_persistent(h, n);
   if (n > 0 && graphs_possible(h)) {
     const bool record = h->ring != nullptr;
     if (!h->graph_exec || h->graph_record != record) {
@@ -476,7 +552,7 @@ int teuk_step(teuk_t h, int64_t n) {
     for (int64_t t = 0; t < n; ++t) TEUK_CUDA(h, cudaGraphLaunch(h->graph_exec, h->stream));
     if (!h->graph_events.empty()) h->graph_events_fresh = true;
     h->substeps_done += n * h->k;
-    h->launches += n * (2 * h->k + (h->ko_sigma > 0 ? 1 : 0));
+    h->launches += n * (2 * h->k + (h->dissipating() ? 1 : 0));
     if (record) h->n_recorded += n;
     return TEUK_OK;
   }
@@ -583,6 +659,7 @@ int teuk_set_state(teuk_t h, const double* planes, int64_t substeps_done) {
   int rc = copy_planes(h, h->u, planes, nullptr, 4, h->n_r);
   if (rc) return rc;
   h->substeps_done = substeps_done;
+  TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
   return TEUK_OK;
 }
 
@@ -681,10 +758,84 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
       if (tx == tx_top) break;
     }
   }
+  int best_p = 1;
+  if (rc == TEUK_OK && h->engine == 0 && !h->dissipating() && h->substeps_done % h->k == 0) {
+    // Persistent launches against the best shape above, both as teuk_step runs them (the
+    // regular kernels as a replayed graph where possible), over the same outer steps; the
+    // observer ring is left alone meanwhile.
+    double* ring = h->ring;
+    h->ring = nullptr;
+    h->kernel_family = best_f;
+    h->kernel_variant = best_v;
+    h->threads_theta = best_tx;
+    h->rows_per_block = best;
+    auto time_steps = [&](int outer, auto&& run) -> float {
+      if ((rc = run(1)) != TEUK_OK) return 1e30f;  // warm-up (and graph build)
+      cudaEventRecord(e0, h->stream);
+      rc = run(outer);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      return rc == TEUK_OK ? ms : 1e30f;
+    };
+    auto regular = [&](int outer) -> int {
+      if (graphs_possible(h)) {
+        if (!h->graph_exec) {
+          const int r = build_graph(h, false);
+          if (r != TEUK_OK) return r;
+        }
+        for (int t = 0; t < outer; ++t) TEUK_CUDA(h, cudaGraphLaunch(h->graph_exec, h->stream));
+        return TEUK_OK;
+      }
+      for (int t = 0; t < outer * h->k; ++t) {
+        const int r = dispatch_substep(h, false, 0);
+        if (r != TEUK_OK) return r;
+      }
+      return TEUK_OK;
+    };
+    const float reg_ms = time_steps(2, regular);
+    drop_graph(h);
+    float pers_ms = 1e30f;
+    int pers_r = 0;
+    for (int R = 1; R <= 8 && rc == TEUK_OK; R *= 2) {
+      h->kernel_family = 3;
+      h->rows_per_block = R;
+      h->threads_theta = 0;
+      const float ms = time_steps(2, [&](int outer) { return dispatch_persist(h, outer, 0); });
+      if (rc == TEUK_ERR_INVALID_ARG) {  // the blocks of this shape cannot all be resident
+        rc = TEUK_OK;
+        continue;
+      }
+      if (ms < pers_ms) {
+        pers_ms = ms;
+        pers_r = R;
+      }
+    }
+    if (rc == TEUK_OK && pers_r > 0 && pers_ms < reg_ms) {
+      // outer steps per launch: one launch per step against one launch for eight
+      h->rows_per_block = pers_r;
+      const float one = time_steps(8, [&](int outer) {
+        for (int t = 0; t < outer; ++t) {
+          const int r = dispatch_persist(h, 1, 0);
+          if (r != TEUK_OK) return r;
+        }
+        return (int)TEUK_OK;
+      });
+      const float eight = time_steps(8, [&](int outer) { return dispatch_persist(h, outer, 0); });
+      best_f = 3;
+      best = pers_r;
+      best_tx = 0;
+      best_v = 0;
+      best_p = eight < one ? 8 : 1;
+    }
+    h->ring = ring;
+  }
   cudaMemcpyAsync(h->u, saved, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(h->status, &status, sizeof(status), cudaMemcpyHostToDevice, h->stream);
   cudaStreamSynchronize(h->stream);
   cudaFree(saved);
+  h->persist_steps = best_p;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->timing = timing;
@@ -698,6 +849,21 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   return rc;
 }
 
+int teuk_set_persistent(teuk_t h, int threads_theta, int rows_per_block, int steps_per_launch) {
+  if (!h || rows_per_block < 1 || rows_per_block > 8 || steps_per_launch < 1 || steps_per_launch > 4096)
+    return invalid(h, "persistent: 1 <= rows_per_block <= 8, 1 <= steps_per_launch <= 4096");
+  if (threads_theta != 0 && (threads_theta < 32 || threads_theta % 32 != 0 || threads_theta * rows_per_block > 256))
+    return invalid(h, "persistent: threads_theta 0 or a multiple of 32 with threads_theta * rows <= 256");
+  if (h->engine == 1) return invalid(h, "persistent: not on the integer engine");
+  h->kernel_family = 3;
+  h->kernel_variant = 0;
+  h->threads_theta = threads_theta;
+  h->rows_per_block = rows_per_block;
+  h->persist_steps = steps_per_launch;
+  drop_graph(h);
+  return TEUK_OK;
+}
+
 int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   if (h->kernel_family == 1) {  // one warp per 32 columns: reported as 32 threads x 1 row, variant + 3
@@ -708,10 +874,15 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
   }
   int tx, ty;
   teuk::row_block_shape(h, tx, ty);
+  if (h->kernel_family == 3) {  // the persistent kernel's block (see persist_impl)
+    ty = h->rows_per_block;
+    tx = std::min(((h->n_th + 31) / 32) * 32, 256 / ty);
+    if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
+  }
   if (threads_theta) *threads_theta = tx;
   if (rows_per_block) *rows_per_block = ty;
-  // balanced kernels are reported as variant + 6
-  if (variant) *variant = (h->kernel_family == 2 ? 6 : 0) + h->kernel_variant;
+  // balanced kernels are reported as variant + 6, the persistent kernel as 9
+  if (variant) *variant = h->kernel_family == 3 ? 9 : (h->kernel_family == 2 ? 6 : 0) + h->kernel_variant;
   return TEUK_OK;
 }
 

@@ -20,7 +20,11 @@ struct teuk_s {
   int kernel_variant = 0;  // register budget of the step kernels: 0 (<= 255), 1 (<= 128), 2 (rows:
                            // <= 102 in blocks of <= 128 threads; warp segments: <= 85)
   int kernel_family = 0;   // 0: rows per block (half_kernel/full_kernel), 1: one warp per 32 columns,
-                           // 2: balanced (every resident block the same number of points)
+                           // 2: balanced (every resident block the same number of points),
+                           // 3: persistent (persist_kernel: outer steps per cooperative launch)
+  int persist_steps = 1;   // family 3: outer steps per launch
+  int* pflags = nullptr;   // family 3: neighbour counters and abort word of the launch
+  int pflags_cap = 0;
   int bal_key = -1;        // (variant, threads) the balanced grid sizes below were computed for
   int bal_grid[2] = {0, 0};  // blocks of the balanced half / full kernels (resident capacity)
   int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;
@@ -74,13 +78,18 @@ struct teuk_s {
   double dt_w[4] = {0, 0, 0, 0}, dr_w[4] = {0, 0, 0, 0};  // outer dt and dr* as words
   double ko_sigma = 0;                 // r* dissipation strength (0: off, the paper's scheme)
   double ko_eps_w[4] = {0, 0, 0, 0};   // sigma dt / (16 dr*) as words
+  double ko_theta = 0;                 // theta dissipation strength (0: off, the paper's scheme)
+  double* eps_th = nullptr;            // [W][n_r]: ko_theta c_th(i) dt / (4096 dtheta) per row
   double* u_ko = nullptr;              // output of the dissipation step (state layout)
+  bool dissipating() const { return ko_sigma > 0 || ko_theta > 0; }
   int engine = 0;                      // double-double arithmetic: 0 FP64 error-free transforms,
                                        // 1 integer engine (ix.cuh)
   uint4* ix_m = nullptr;               // integer-engine tables: node coefficients, half-node
   int* ix_e = nullptr;                 // coefficients, stencil weights (mantissas, exponent-sign)
   long long ix_stage_key = -1;         // launch shape the staging choice below was made for
   int ix_stage = 0;                    // integer-engine kernels copy their table rows to shared memory
+  int test_stall_block = -1;           // test hook: block that arms its copy barrier without copies
+  int wait_log2 = 20;                  // the engine kernels' copy wait gives up after 2^wait_log2 tries
   std::string last_error;
 };
 
@@ -102,6 +111,9 @@ int substep_buffers_w4(teuk_s* h, const double* u_in, double* u_out, double* scr
 int prepare_w1(teuk_s* h);
 int prepare_w2(teuk_s* h);
 int prepare_w4(teuk_s* h);
+int persist_w1(teuk_s* h, int64_t n_outer, long long ring_base);
+int persist_w2(teuk_s* h, int64_t n_outer, long long ring_base);
+int persist_w4(teuk_s* h, int64_t n_outer, long long ring_base);
 // Integer-engine kernels (double-double and quad-double; teuk_ixk.cu): the engine's tables,
 // the step's kernel pair of register-budget variant 0..2, and the batched executor.
 struct StepArgs;
@@ -127,6 +139,9 @@ int dissipation_w4(teuk_s* h, double sigma);
 int dissipate_w1(teuk_s* h);
 int dissipate_w2(teuk_s* h);
 int dissipate_w4(teuk_s* h);
+int theta_dissipation_w1(teuk_s* h, double sigma, double* max_rate);
+int theta_dissipation_w2(teuk_s* h, double sigma, double* max_rate);
+int theta_dissipation_w4(teuk_s* h, double sigma, double* max_rate);
 int project_w1(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);
 int project_w2(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);
 int project_w4(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first);

@@ -112,9 +112,11 @@ IXD void ix_bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
                "l"(src), "r"(bytes), "r"(ix_saddr(bar))
                : "memory");
 }
-// Waits for phase 0 of bar with an iteration limit; false if the limit was reached.
-IXD bool ix_bar_wait(uint64_t* bar) {
-  for (int it = 0; it < (1 << 20); ++it) {
+// Waits for phase 0 of bar with an iteration limit of 2^limit_log2 tries; false if the limit
+// was reached.
+IXD bool ix_bar_wait(uint64_t* bar, int limit_log2) {
+  const int limit = 1 << limit_log2;
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -769,9 +771,11 @@ inline size_t ix_smem_bytes(int rows, int gstride, int pitch, int stage, bool fu
 // With stage bit 2 also the state rows: Pi rows q0 .. q0 + nv of qsrc (planes qs doubles
 // apart) into [2][W][rows + 1][pitch], and (full step, usrc != null) rows r0 .. r0 + nv - 1
 // of all four components of usrc (planes us apart) into [4][W][rows][pitch] after them.
+// stall: this block arms the barrier with the expected byte count and issues no copy (a test
+// of the bounded wait's give-up path: nothing is in flight when the block gives up).
 template <int W>
 IXD void ix_stage(const IxSmem& sm, int stage, const uint4* gm, const int* ge, size_t per_plane, int pitch, int r0,
-                  int nv, const double* qsrc, size_t qs, int q0, const double* usrc, size_t us) {
+                  int nv, const double* qsrc, size_t qs, int q0, const double* usrc, size_t us, bool stall) {
   constexpr int U = IxT<W>::kU4;
   const int rows = blockDim.y;
   const uint32_t mb = (uint32_t)nv * pitch * sizeof(uint4), eb = (uint32_t)nv * pitch * sizeof(int);
@@ -780,6 +784,7 @@ IXD void ix_stage(const IxSmem& sm, int stage, const uint4* gm, const int* ge, s
   if (stage & 2) bytes += 2 * W * qb + (usrc ? 4 * W * ub : 0);
   ix_bar_init(sm.bar);
   ix_bar_expect(sm.bar, bytes);
+  if (stall) return;
   for (int q = 0; q < kIxPlanes; ++q) {
     for (int u = 0; u < U; ++u)
       ix_bulk_copy(sm.tm + ((size_t)(q * U + u) * rows) * pitch, gm + (q * U + u) * per_plane + (size_t)r0 * pitch,
@@ -805,7 +810,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) h
   const int h0 = blockIdx.x * blockDim.y, h = h0 + threadIdx.y;
   if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
     ix_stage<W>(sm, x.stage, x.chm, x.che, hs, pitch, h0, min((int)blockDim.y, nh - h0), x.a.u_in, ws, h0, nullptr,
-                0);
+                0, (int)blockIdx.x == x.stall_block);
   const bool ok = h < nh;
   int eR = ix::kZeroE, eI = ix::kZeroE;
   if (ok) ix_half_prep<W>(x, h, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
@@ -818,7 +823,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) h
   size_t base = (size_t)h * pitch;
   IxSt st{x.a.u_in + 2 * W * ws + (size_t)h * pitch, ws, nullptr, 0};
   if (x.stage) {
-    if (!ix_bar_wait(sm.bar)) {
+    if (!ix_bar_wait(sm.bar, x.wait_log2)) {
       atomicOr(x.a.status, 2u);
       return;
     }
@@ -842,7 +847,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   const int i0 = 1 + blockIdx.x * blockDim.y, i = i0 + threadIdx.y;
   if (x.stage && threadIdx.x == 0 && threadIdx.y == 0)
     ix_stage<W>(sm, x.stage, x.cnm, x.cne, ws, pitch, i0, min((int)blockDim.y, n_r - 1 - i0), x.a.uh, hs, i0 - 1,
-                x.a.u_in, ws);
+                x.a.u_in, ws, (int)blockIdx.x == x.stall_block);
   const bool ok = i < n_r - 1;
   int eR = ix::kZeroE, eI = ix::kZeroE;
   if (ok) ix_full_prep<W>(x, i, threadIdx.x, blockDim.x, sR, sI, gstride, eR, eI);
@@ -855,7 +860,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   size_t base = (size_t)i * pitch;
   IxSt st{x.a.uh + 2 * W * hs + (size_t)(i - 1) * pitch, hs, x.a.u_in + (size_t)i * pitch, ws};
   if (x.stage) {
-    if (!ix_bar_wait(sm.bar)) {
+    if (!ix_bar_wait(sm.bar, x.wait_log2)) {
       atomicOr(x.a.status, 2u);
       return;
     }

@@ -71,9 +71,11 @@ int launch_pair(teuk_s* h, const StepArgs& sa, dim3 blk) {
       if (occ[k] > 0 && occ[k] >= occ[0]) h->ix_stage = opts[k];
     h->ix_stage_key = key;
   }
-  IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, h->ix_stage};
-  const size_t ism_h = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage, false);
-  const size_t ism_f = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, h->ix_stage, true);
+  // the give-up test needs the copies: it stages the table rows at least
+  const int stage = h->test_stall_block >= 0 && h->ix_stage == 0 ? 1 : h->ix_stage;
+  IxArgs x{sa, h->ix_m, h->ix_e, h->ix_m + U * ncn, h->ix_e + ncn, stage, h->wait_log2, h->test_stall_block};
+  const size_t ism_h = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, stage, false);
+  const size_t ism_f = ix_smem_bytes<W>((int)blk.y, gs, h->pitch, stage, true);
   {
     int dev = 0, optin = 0;
     TEUK_CUDA(h, cudaGetDevice(&dev));
@@ -126,3 +128,65 @@ cudaError_t TEUK_SUFFIX(batch_ix_launch_w)(const BatchArgs& args, const IxArgs* 
 }
 
 }  // namespace teuk
+
+#if TEUK_WORDS == 2
+namespace {
+// Throughput of the integer engine's product window (ix::mul_window: 10 partial products of
+// 32-bit limbs, each a mad.lo.cc / madc.hi.cc pair with its carry), the work unit of the
+// engine's roofline: every thread runs 4 independent windows per iteration, each fed back
+// into the next so that none can be hoisted.
+__global__ void ix_window_peak_kernel(uint32_t* out, uint32_t seed, int iters) {
+  uint32_t a[4][4], b[4][4], p[4][5];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[c][k] = seed * (2654435761u + 97u * c + k) + threadIdx.x;
+      b[c][k] = seed ^ (40503u * (c + 1) + 7u * k + blockIdx.x);
+    }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      ix::mul_window(a[c], b[c], p[c]);
+      a[c][0] ^= p[c][4];
+      a[c][1] += p[c][3];
+    }
+  }
+  uint32_t x = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) x ^= p[c][0] ^ p[c][1] ^ p[c][2] ^ p[c][3] ^ p[c][4];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+}  // namespace
+
+extern "C" int teuk_int_peak(double* pairs_per_second) {
+  if (!pairs_per_second) return TEUK_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TEUK_ERR_NO_DEVICE;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TEUK_ERR_CUDA;
+  const int threads = 256, blocks = sms * 8, iters = 2048;
+  uint32_t* buf = nullptr;
+  if (cudaMalloc(&buf, (size_t)threads * blocks * sizeof(uint32_t)) != cudaSuccess) return TEUK_ERR_OOM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    ix_window_peak_kernel<<<blocks, threads>>>(buf, 12345u + rep, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (err != cudaSuccess) return TEUK_ERR_CUDA;
+  // 4 windows of 10 partial products per iteration and thread
+  *pairs_per_second = (double)threads * blocks * iters * 4 * 10 / (best * 1e-3);
+  return TEUK_OK;
+}
+#endif

@@ -369,19 +369,32 @@ __global__ void pulse_kernel(PulseArgs a) {
   st_r(a.u + 3 * W * ws + idx, ws, r_mul(b, r_mul_d(GpY, a.amp_im)));
 }
 
-// ---- r* dissipation (not part of the paper's method; off unless enabled) -------------------
-// Once per outer step, before its first Lax-Wendroff iteration, every component at rows
-// 2 .. n_r - 3 becomes u_i - eps (u_{i-2} - 4 u_{i-1} + 6 u_i - 4 u_{i+1} + u_{i+2}),
-// eps = sigma dt / (16 dr*): the fourth-order Kreiss-Oliger operator over one outer step. The
-// other rows are copied. Several iterations per dt = 0.25 dr* leave the scheme's own damping
-// of short r* wavelengths too weak for the modes of near-zero numerical group velocity in the
-// region where the lower-order terms of the system make a frozen wave grow (long runs).
+// ---- dissipation (not part of the paper's method; off unless enabled) ---------------------
+// Once per outer step, before its first Lax-Wendroff iteration, every component becomes
+//   u - eps_r d_r^4 u - eps_th(i) d_th^12 u,
+// eps_r = sigma_r dt / (16 dr*) (rows 2 .. n_r - 3 only), eps_th(i) = sigma_th c_th(i) dt /
+// (4096 dtheta) with c_th(i) = max_j sqrt(Delta/Sigma^2) at node i (rows 1 .. n_r - 2), d_r^4 the
+// undivided fourth difference along r* and d_th^12 = (d_th^2)^6 the undivided twelfth
+// difference along theta with the parity ghosts: Kreiss-Oliger operators of order 4 and 12
+// integrated over one outer step. Both differences read the same input u. Several iterations
+// per dt = 0.25 dr* leave the scheme's own damping of short r* wavelengths too weak where the
+// lower-order terms of the system make a frozen wave grow; the theta term damps the grid-scale
+// theta modes whose frequencies set how many iterations the explicit midpoint-like iteration
+// of the theta terms needs.
 struct DissArgs {
   Geom g;
-  const double* u;  // [4][W][n_r][pitch]
-  double* out;      // same layout
-  double eps[4];    // eps as W words
+  const double* u;       // [4][W][n_r][pitch]
+  double* out;           // same layout
+  double eps[4];         // eps_r as W words
+  int do_r;              // apply the r* term
+  const double* eps_th;  // [W][n_r] or null: no theta term
 };
+
+// (d^2)^6 f_j = sum_q (-1)^q C(12, 6 + q) f_{j+q}: exact small-integer weights.
+__device__ __forceinline__ double ko12_weight(int q) {
+  constexpr double w[7] = {924, -792, 495, -220, 66, -12, 1};
+  return w[q < 0 ? -q : q];
+}
 
 template <int W>
 __global__ void dissipate_kernel(DissArgs a) {
@@ -389,18 +402,74 @@ __global__ void dissipate_kernel(DissArgs a) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y, c = blockIdx.z;
   if (j >= a.g.n_th) return;
+  const int n_th = a.g.n_th;
   const size_t ws = (size_t)a.g.n_r * a.g.pitch, p = (size_t)a.g.pitch;
   const double* base = a.u + (size_t)c * W * ws + (size_t)i * p + j;
   R v = ld_s<R>(base, ws);
-  if (i >= 2 && i <= a.g.n_r - 3) {
-    using namespace mw;
+  using namespace mw;
+  if (a.do_r && i >= 2 && i <= a.g.n_r - 3) {
     R d4 = v_sub(ld_s<R>(base - 2 * p, ws), r_scale2(ld_s<R>(base - p, ws), 4.0));
     d4 = v_add(d4, r_mul_d(v, 6.0));
     d4 = v_sub(d4, r_scale2(ld_s<R>(base + p, ws), 4.0));
     d4 = v_add(d4, ld_s<R>(base + 2 * p, ws));
     v = v_sub(v, r_mul(from_words<R>(a.eps), d4));
   }
+  if (a.eps_th && i >= 1 && i <= a.g.n_r - 2) {
+    const double* row = base - j;
+    Acc<R> acc(r_from<R>(0.0));
+#pragma unroll
+    for (int q = -6; q <= 6; ++q) {
+      int jj = j + q;
+      bool ghost = false;
+      if (jj < 0) { jj = -1 - jj; ghost = true; }
+      else if (jj >= n_th) { jj = 2 * n_th - 1 - jj; ghost = true; }
+      R f = ld_s<R>(row + jj, ws);
+      if (ghost && a.g.parity < 0) f = v_neg(f);
+      acc.mac(r_from<R>(ko12_weight(q)), f);
+    }
+    double e[4] = {0, 0, 0, 0};
+    for (int k = 0; k < W; ++k) e[k] = a.eps_th[(size_t)k * a.g.n_r + i];
+    v = v_sub(v, r_mul(from_words<R>(e), acc.get()));
+  }
   st_r(a.out + (size_t)c * W * ws + (size_t)i * p + j, ws, v);
+}
+
+// eps_th(i) = factor * sqrt(max_j g(i, j)), g = Delta/Sigma^2 (plane 5 of the raw node
+// coefficients), factor = sigma_th dt / (4096 dtheta); one block per row. The largest g of a
+// row is found by comparing the word expansions (normalised, so the words order the values).
+template <int W>
+__global__ void theta_ko_eps_kernel(Geom g, const double* cn_raw, double* eps_th, double fac0, double fac1,
+                                    double fac2, double fac3) {
+  using R = typename RT<W>::T;
+  __shared__ double best[4][256];
+  const int i = blockIdx.x;
+  const size_t ws = (size_t)g.n_r * g.pitch;
+  const double* plane = cn_raw + (size_t)5 * W * ws + (size_t)i * g.pitch;
+  double m[4] = {-1.0, 0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < g.n_th; j += blockDim.x) {
+    double v[4] = {0, 0, 0, 0};
+    for (int k = 0; k < W; ++k) v[k] = plane[(size_t)k * ws + j];
+    bool gt = false;
+    for (int k = 0; k < W; ++k) {
+      if (v[k] != m[k]) { gt = v[k] > m[k]; break; }
+    }
+    if (gt) for (int k = 0; k < 4; ++k) m[k] = v[k];
+  }
+  for (int k = 0; k < 4; ++k) best[k][threadIdx.x] = m[k];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int t = 1; t < blockDim.x; ++t) {
+    bool gt = false;
+    for (int k = 0; k < W; ++k) {
+      if (best[k][t] != m[k]) { gt = best[k][t] > m[k]; break; }
+    }
+    if (gt) for (int k = 0; k < 4; ++k) m[k] = best[k][t];
+  }
+  const double fw[4] = {fac0, fac1, fac2, fac3};
+  const R e = mw::r_mul(from_words<R>(fw), mw::r_sqrt(from_words<R>(m)));
+  double w[4];
+  to_words(e, w);
+  for (int k = 0; k < W; ++k) eps_th[(size_t)k * g.n_r + i] = w[k];
 }
 
 // ---- multipole projection of the recorded waveform (Sec. 3.C, Fig. 1) ----------------------
@@ -826,6 +895,113 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   if (bad) atomicOr(a.status, 1u);
 }
 
+// ---- persistent kernel for small problems: many iterations in one launch ---------------------
+// A small grid cannot keep the GPU busy between launches: the launches of one iteration cost
+// more than its arithmetic. Here one cooperative launch runs n_outer outer steps of k
+// iterations. Block b owns the half rows and nodes [b R, (b + 1) R) (R = blockDim.y rows, one
+// thread row each). Only neighbouring blocks depend on each other:
+//   half step n of block b reads state row (b + 1) R, written by block b + 1's full step n - 1;
+//   full step n of block b reads half row b R - 1, written by block b - 1's half step n, and
+//   overwrites state row b R, which that half step reads.
+// So each block publishes two counters, half_done[b] and full_done[b] (iterations finished in
+// this launch), and before each phase waits for the neighbour's counter: thread 0 polls with
+// an acquire load (a bounded number of times), the block's barrier passes the ordering on to
+// its other threads; after each phase thread 0 publishes with a fence and a release store.
+// A wait that reaches its limit sets status bit 2 and the abort word, on which every other
+// wait gives up too, so the launch always ends. Arithmetic: the row kernels' point functions,
+// so the results are bit-identical to the one-launch-per-phase kernels.
+struct PersistArgs {
+  StepArgs a;             // state updated in place (u_in == u_out), half rows, tables, ring
+  int k;                  // iterations per outer step
+  int n_outer;            // outer steps in this launch
+  long long ring_base;    // samples recorded before this launch
+  int* flags;             // [2 * gridDim.x + 1]: half_done, full_done, abort (zeroed before the launch)
+  int spin_log2;          // a wait gives up after 2^spin_log2 polls
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until *f >= target (or gives up); the result reaches the whole block.
+__device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f, int target, int* ok_sm) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int ok = 1;
+    if (f) {
+      const long long limit = 1ll << p.spin_log2;
+      const int* abortw = p.flags + 2 * gridDim.x;
+      ok = 0;
+      for (long long it = 0; it < limit; ++it) {
+        if (ld_acquire_gpu(f) >= target) { ok = 1; break; }
+        if (ld_acquire_gpu(abortw)) break;
+      }
+      if (!ok) {
+        atomicOr(p.a.status, 2u);
+        atomicExch(p.flags + 2 * gridDim.x, 1);
+      }
+    }
+    *ok_sm = ok;
+  }
+  __syncthreads();
+  return *ok_sm != 0;
+}
+
+__device__ __forceinline__ void persist_publish(int* f, int value) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    st_release_gpu(f, value);
+  }
+}
+
+// blockDim = (threads along theta, R rows); grid = ceil((n_r - 1) / R) co-resident blocks.
+template <int W>
+__global__ void __launch_bounds__(256, 1) persist_kernel(PersistArgs p) {
+  extern __shared__ double sm[];
+  __shared__ int s_ok;
+  const StepArgs& a = p.a;
+  const int G = gridDim.x, b = blockIdx.x, ty = threadIdx.y, tx = threadIdx.x, TX = blockDim.x;
+  const int gstride = a.g.n_th + 2 * a.radius;
+  double* sR = sm + (size_t)ty * 2 * W * gstride;
+  double* sI = sR + (size_t)W * gstride;
+  const int h = b * (int)blockDim.y + ty;  // this thread row's half row and node
+  const bool h_ok = h < a.g.n_r - 1;
+  const bool i_ok = h >= 1 && h < a.g.n_r - 1;
+  int* half_done = p.flags;
+  int* full_done = p.flags + G;
+  const int* next_full = b + 1 < G ? full_done + b + 1 : nullptr;
+  const int* prev_half = b > 0 ? half_done + b - 1 : nullptr;
+  bool bad = false;
+  int n = 0;
+  for (int s = 0; s < p.n_outer; ++s) {
+    for (int q = 0; q < p.k; ++q) {
+      ++n;
+      // Eq. lw1: state row (b + 1) R must hold iteration n - 1
+      if (!persist_wait(p, n > 1 ? next_full : nullptr, n - 1, &s_ok)) goto done;
+      if (h_ok) half_row_prep<W>(a, h, tx, TX, sR, sI);
+      __syncthreads();
+      if (h_ok) half_row_out<W>(a, h, tx, TX, sR, sI);
+      persist_publish(half_done + b, n);
+      // Eq. lw2: half row b R - 1 must hold iteration n (and be read before row b R changes)
+      if (!persist_wait(p, prev_half, n, &s_ok)) goto done;
+      if (i_ok) full_row_prep<W>(a, h, tx, TX, sR, sI);
+      __syncthreads();
+      if (i_ok) {
+        const long long slot = (q == p.k - 1 && a.ring_cap > 0) ? (p.ring_base + s) % a.ring_cap : -1;
+        bad |= full_row_out<W>(a, h, tx, TX, sR, sI, slot);
+      }
+      persist_publish(full_done + b, n);
+    }
+  }
+done:
+  if (bad) atomicOr(a.status, 1u);
+}
+
 // Arguments of the integer-engine step kernels (teuk_ix.cuh). Planes of the engine's
 // coefficient tables: the eight folded coefficients of the step, with plane 5 (H5 / N5, the
 // factor of the theta operator) replaced by H5 A2 and plane 8 holding H5 A1 cot theta_j.
@@ -838,6 +1014,8 @@ struct IxArgs {
   const uint4* chm;     // half-node coefficients [kIxPlanes][kU4][n_r - 1][pitch]
   const int* che;
   int stage;            // 1: each block copies its rows of the tables into shared memory first
+  int wait_log2;        // the wait for those copies gives up after 2^wait_log2 tries
+  int stall_block;      // test hook: this block arms its copy barrier but issues no copy (-1: none)
 };
 
 // ---- batched execution: many problems of uneven size in one cooperative launch ------------

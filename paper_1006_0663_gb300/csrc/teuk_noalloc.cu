@@ -50,8 +50,8 @@ int rows_on_current_device(teuk_s* h, double** out) {
 
 extern "C" int teuk_substep_noalloc(teuk_t h, const double* u_in, double* u_out, int64_t n_iterations) {
   if (!h || !u_in || !u_out || n_iterations < 0) return TEUK_ERR_INVALID_ARG;
-  if (h->ko_sigma > 0) {
-    h->last_error = "teuk_substep_noalloc: the r* dissipation step needs the handle's own buffers";
+  if (h->dissipating()) {
+    h->last_error = "teuk_substep_noalloc: the dissipation step needs the handle's own buffers";
     return TEUK_ERR_INVALID_ARG;
   }
   const size_t needed = (size_t)4 * h->W * (size_t)(h->n_r - 1) * h->pitch;

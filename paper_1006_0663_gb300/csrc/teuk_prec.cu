@@ -2,6 +2,7 @@
 // -DTEUK_WORDS=1 (FP64), 2 (double-double) or 4 (quad-double).
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "ix.cuh"
@@ -295,6 +296,28 @@ int dissipation_impl(teuk_s* h, double sigma) {
   return TEUK_OK;
 }
 
+// theta dissipation: eps_th(i) = sigma c_th(i) dt / (4096 dtheta) per row, in the target
+// precision (h->eps_th allocated by the caller); *max_rate = max_i 4096 eps_th(i), the largest
+// damping factor of one step (the grid-scale theta mode is multiplied by 1 - max_rate).
+int theta_dissipation_impl(teuk_s* h, double sigma, double* max_rate) {
+  const R dt = from_words<R>(h->dt_w);
+  const R dth = r_div(r_pi<R>(), r_from<R>(double(h->n_th)));
+  const R fac = r_div(r_mul(r_from<R>(sigma), dt), r_mul(r_from<R>(4096.0), dth));
+  double f[4];
+  put(f, fac);
+  theta_ko_eps_kernel<W><<<h->n_r, 256, 0, h->stream>>>(Geom{h->n_r, h->n_th, h->pitch, h->parity}, h->cn_raw,
+                                                         h->eps_th, f[0], f[1], f[2], f[3]);
+  TEUK_CUDA(h, cudaGetLastError());
+  std::vector<double> lead_eps(h->n_r);
+  TEUK_CUDA(h, cudaMemcpyAsync(lead_eps.data(), h->eps_th, h->n_r * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  double mx = 0;
+  for (double e : lead_eps) mx = e > mx ? e : mx;
+  *max_rate = 4096.0 * mx;
+  return TEUK_OK;
+}
+
 // One dissipation step of the state (kernel into u_ko, copied back).
 int dissipate_impl(teuk_s* h) {
   DissArgs da{};
@@ -302,6 +325,8 @@ int dissipate_impl(teuk_s* h) {
   da.u = h->u;
   da.out = h->u_ko;
   std::memcpy(da.eps, h->ko_eps_w, sizeof(da.eps));
+  da.do_r = h->ko_sigma > 0;
+  da.eps_th = h->ko_theta > 0 ? h->eps_th : nullptr;
   dissipate_kernel<W><<<dim3((h->n_th + 63) / 64, h->n_r, 4), 64, 0, h->stream>>>(da);
   TEUK_CUDA(h, cudaGetLastError());
   TEUK_CUDA(h, cudaMemcpyAsync(h->u, h->u_ko, (size_t)4 * W * h->n_r * h->pitch * sizeof(double),
@@ -459,6 +484,75 @@ int substep_impl(teuk_s* h, bool record, int64_t slot) {
   step_shape(h, blk);
   const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
   return launch_pair(h, sa, blk, smem);
+}
+
+// Persistent launch (kernel family 3, FP64 error-free transforms or FP64): n_outer outer steps
+// of k iterations in one cooperative launch of ceil((n_r - 1) / R) blocks of
+// (threads_theta, R) threads, R = h->rows_per_block; the observer ring gets one sample per
+// outer step from slot ring_base on. TEUK_ERR_INVALID_ARG if the blocks cannot all be resident.
+int persist_impl(teuk_s* h, int64_t n_outer, long long ring_base) {
+  if (h->engine == 1) {
+    h->last_error = "persistent launches run the FP64 and FP64-error-free-transform kernels only";
+    return TEUK_ERR_INVALID_ARG;
+  }
+  const int R = h->rows_per_block > 0 ? h->rows_per_block : 1;
+  int tx = ((h->n_th + 31) / 32) * 32;
+  if (tx > 256 / R) tx = 256 / R;
+  if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
+  if (tx < 32 || tx * R > 256) {
+    h->last_error = "persistent launch: threads_theta x rows must be 32..256";
+    return TEUK_ERR_INVALID_ARG;
+  }
+  const int G = (h->n_r - 1 + R - 1) / R;
+  const size_t smem = (size_t)R * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);
+  if (smem > 48 * 1024)
+    TEUK_CUDA(h, cudaFuncSetAttribute(persist_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0;
+  TEUK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_kernel<W>, tx * R, smem));
+  TEUK_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (per_sm * sms < G) {
+    h->last_error = "persistent launch: " + std::to_string(G) + " blocks cannot all be resident (" +
+                    std::to_string(per_sm * sms) + " fit)";
+    return TEUK_ERR_INVALID_ARG;
+  }
+  if ((int64_t)n_outer * h->k >= ((int64_t)1 << 31)) return TEUK_ERR_INVALID_ARG;
+  if (h->pflags_cap < 2 * G + 1) {
+    if (h->pflags) cudaFree(h->pflags);
+    h->pflags = nullptr;
+    h->pflags_cap = 0;
+    TEUK_CUDA(h, cudaMalloc(&h->pflags, (size_t)(2 * G + 1) * sizeof(int)));
+    h->pflags_cap = 2 * G + 1;
+  }
+  TEUK_CUDA(h, cudaMemsetAsync(h->pflags, 0, (size_t)(2 * G + 1) * sizeof(int), h->stream));
+  PersistArgs pa{};
+  StepArgs& sa = pa.a;
+  sa.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
+  sa.u_in = h->u;
+  sa.u_out = h->u;
+  sa.uh = h->uh;
+  sa.cn = h->cn;
+  sa.ch = h->ch;
+  sa.wts = h->wts;
+  std::memcpy(sa.h4, h->h4_w, sizeof(sa.h4));
+  std::memcpy(sa.h2, h->h2_w, sizeof(sa.h2));
+  sa.radius = h->radius;
+  sa.record = 0;
+  sa.i_obs = h->i_obs;
+  sa.ring_slot = -1;
+  sa.ring_counter = nullptr;
+  sa.ring_cap = h->ring ? h->ring_cap : 0;
+  sa.ring = h->ring;
+  sa.status = h->status;
+  pa.k = h->k;
+  pa.n_outer = (int)n_outer;
+  pa.ring_base = ring_base;
+  pa.flags = h->pflags;
+  pa.spin_log2 = 22;
+  void* params[] = {&pa};
+  TEUK_CUDA(h, cudaLaunchCooperativeKernel((const void*)persist_kernel<W>, dim3(G), dim3(tx, R), params, smem,
+                                           h->stream));
+  h->launches += 1;
+  return TEUK_OK;
 }
 
 // One Lax-Wendroff iteration from u_in to u_out (may alias) with the half-step rows in a
@@ -647,9 +741,15 @@ int TEUK_SUFFIX(pulse_w)(teuk_s* h, double center, double width, double ar, doub
 }
 int TEUK_SUFFIX(substep_w)(teuk_s* h, bool record, int64_t slot) { return substep_impl(h, record, slot); }
 int TEUK_SUFFIX(prepare_w)(teuk_s* h) { return prepare_impl(h); }
+int TEUK_SUFFIX(persist_w)(teuk_s* h, int64_t n_outer, long long ring_base) {
+  return persist_impl(h, n_outer, ring_base);
+}
 int TEUK_SUFFIX(engine_w)(teuk_s* h, int engine) { return engine_impl(h, engine); }
 int TEUK_SUFFIX(dissipation_w)(teuk_s* h, double sigma) { return dissipation_impl(h, sigma); }
 int TEUK_SUFFIX(dissipate_w)(teuk_s* h) { return dissipate_impl(h); }
+int TEUK_SUFFIX(theta_dissipation_w)(teuk_s* h, double sigma, double* max_rate) {
+  return theta_dissipation_impl(h, sigma, max_rate);
+}
 int TEUK_SUFFIX(project_w)(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first) {
   return project_impl(h, ell_min, ell_max, out, n, first);
 }

@@ -28,7 +28,8 @@ SYMBOLS = [
     "teuk_tune", "teuk_batch_create", "teuk_batch_step", "teuk_batch_sync", "teuk_batch_info",
     "teuk_batch_destroy", "teuk_use_graphs", "teuk_launch_shape",
     "teuk_set_launch_shape", "teuk_read_multipoles", "teuk_substep_host_state",
-    "teuk_set_dissipation", "teuk_set_engine", "teuk_engine",
+    "teuk_set_dissipation", "teuk_set_engine", "teuk_engine", "teuk_set_theta_dissipation",
+    "teuk_theta_dissipation", "teuk_int_peak", "teuk_test_stall_copies", "teuk_set_persistent",
 ]
 
 
@@ -76,6 +77,9 @@ def lib(build_if_missing: bool = True):
         L.teuk_read_multipoles.argtypes = [vp, i32, i32, dp, P(i64)]
         L.teuk_substep_host_state.argtypes = [vp, dp, i64]
         L.teuk_set_dissipation.argtypes = [vp, d]
+        L.teuk_set_theta_dissipation.argtypes = [vp, d]
+        L.teuk_theta_dissipation.argtypes = [vp]
+        L.teuk_theta_dissipation.restype = d
         L.teuk_set_engine.argtypes = [vp, i32]
         L.teuk_engine.argtypes = [vp]
         L.teuk_get_state.argtypes = [vp, dp, P(i64)]
@@ -94,6 +98,9 @@ def lib(build_if_missing: bool = True):
         L.teuk_timing.argtypes = [vp, i32]
         L.teuk_kernel_times.argtypes = [vp, dp, dp, P(i64), P(i64)]
         L.teuk_fp64_peak.argtypes = [dp]
+        L.teuk_int_peak.argtypes = [dp]
+        L.teuk_test_stall_copies.argtypes = [vp, i32, i32]
+        L.teuk_set_persistent.argtypes = [vp, i32, i32, i32]
         L.teuk_substep_noalloc.argtypes = [vp, vp, vp, i64]
         L.teuk_tune.argtypes = [vp, P(i32)]
         L.teuk_batch_create.argtypes = [P(vp), P(vp), i32]
@@ -165,6 +172,8 @@ class Teuk:
                 precision=precision if precision is not None else p.words, **kw)
         if getattr(p, "ko_sigma", 0.0):
             g.set_dissipation(p.ko_sigma)
+        if getattr(p, "ko_theta", 0.0):
+            g.set_theta_dissipation(p.ko_theta)
         return g
 
     def close(self):
@@ -233,6 +242,15 @@ class Teuk:
         0 = off)."""
         _check(lib().teuk_set_dissipation(self._h, float(sigma)), self._h)
 
+    def set_theta_dissipation(self, sigma):
+        """12th-order theta Kreiss-Oliger dissipation once per outer step (not part of the
+        paper's scheme; 0 = off)."""
+        _check(lib().teuk_set_theta_dissipation(self._h, float(sigma)), self._h)
+
+    @property
+    def theta_dissipation(self) -> float:
+        return float(lib().teuk_theta_dissipation(self._h))
+
     def substep_host_state(self, planes, n=1):
         """n iterations with the state held in host memory (the paper's first CUDA design's
         data flow, Sec. 4): planes [4][words][n_r][n_theta], C-contiguous float64, updated
@@ -294,6 +312,11 @@ class Teuk:
     def set_launch_shape(self, threads_theta=128, rows_per_block=1, variant=0):
         _check(lib().teuk_set_launch_shape(self._h, int(threads_theta), int(rows_per_block),
                                            int(variant)), self._h)
+
+    def set_persistent(self, rows_per_block=2, steps_per_launch=1, threads_theta=0):
+        """Outer steps in persistent cooperative launches (variant 9; small problems)."""
+        _check(lib().teuk_set_persistent(self._h, int(threads_theta), int(rows_per_block),
+                                         int(steps_per_launch)), self._h)
 
     def use_graphs(self, enable=True):
         _check(lib().teuk_use_graphs(self._h, 1 if enable else 0), self._h)
@@ -363,6 +386,14 @@ def fp64_peak() -> float:
     """Measured FP64 pipe operations per second of the current device."""
     v = ctypes.c_double()
     _check(lib().teuk_fp64_peak(ctypes.byref(v)))
+    return v.value
+
+
+def int_peak() -> float:
+    """Measured product-window partial products (32-bit limb multiply-add pairs) per second of
+    the current device: the integer engine's roofline unit."""
+    v = ctypes.c_double()
+    _check(lib().teuk_int_peak(ctypes.byref(v)))
     return v.value
 
 

@@ -93,6 +93,7 @@ class Problem:
     rstar_obs: float = 300.0
     theta_order: int = 10
     ko_sigma: float = 0.0  # r* dissipation (not in the paper; 0 = the paper's scheme)
+    ko_theta: float = 0.0  # theta dissipation (not in the paper; 0 = the paper's scheme)
 
     @property
     def dr(self) -> float:
