@@ -107,6 +107,9 @@ def parse():
                          "instead of autotuning (profiling)")
     ap.add_argument("--digits", action="store_true",
                     help="print the cost-per-digit table (errors vs the oracle and each other)")
+    ap.add_argument("--n-r", type=int, default=0,
+                    help="profiling: the workload with this many r* nodes over the same r* range "
+                         "(a smaller case of the same kernels)")
     ap.add_argument("--c4-steps", type=int, default=4,
                     help="outer steps of the 64-member batch timed in one cooperative launch")
     return ap.parse_args()
@@ -559,13 +562,21 @@ def word_diff(a, b):
     return diff
 
 
-def digits_table():
-    """Errors of FP64 / double-double / quad-double runs and their cost.
+# Outer steps of the cost-per-digit runs: the stated length where the run stays bounded (c1),
+# else the prefix before the spurious growth of trapped high-l modes on these r* grids starts
+# (c2 from t ~ 850 M, c3 from t ~ 300 M; measured, see the stability study).
+DIGITS_STEPS = {"c1": 1000, "c2": 4000, "c3": 2000}
 
-    1. c1 at its full length (1000 outer steps = 46000 iterations) in all three arithmetics
-       on the GPU; quad-double is the reference for the FP64 and dd errors.
-    2. The reference itself: a prefix of c1 (3 outer steps) against the 256-bit oracle.
-    3. Throughput of each arithmetic on the c2 grid (CUDA events)."""
+
+def digits_table():
+    """Errors of FP64 / double-double / quad-double runs and their cost, on c1, c2 and c3.
+
+    For each workload: the FP64, double-double and quad-double runs of DIGITS_STEPS outer steps
+    on the GPU (dd and qd on the integer engine); quad-double is the reference for the other
+    two (max over the grid of |u - u_qd| / max |u_qd|). The reference itself: a 3-outer-step
+    prefix of each arithmetic against the 256-bit oracle (c1 whole grid; c2 and c3 a window
+    of rows around the pulse). Cost: ns per update of each arithmetic on the workload's grid
+    (CUDA events, tuned launch shape)."""
     import numpy as np
     import torch
 
@@ -574,64 +585,58 @@ def digits_table():
 
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    c1, c2 = workloads.CONFIGS["c1"], workloads.CONFIGS["c2"]
-    ar, ai = c1.amps
-    out = {"reference_check": {}, "c1_full_run": {}, "throughput_c2_grid": {}}
-    # prefix vs the 256-bit oracle
-    o = oracle.Oracle(M=c1.M, a=c1.a, s=c1.s, m=c1.m, rstar_min=c1.rstar_min, rstar_max=c1.rstar_max,
-                      n_r=c1.n_r, n_theta=c1.n_theta, dt=0.0, substeps=c1.substeps, bits=256)
-    o.pulse(c1.center, c1.width, ar, ai, c1.ell)
-    o.step(3 * c1.substeps)
-    for W in (1, 2, 4):
-        g = teuk.Teuk.from_problem(c1, precision=W)
-        g.set_initial_pulse(c1.center, c1.width, ar, ai, c1.ell)
-        g.step(3)
-        g.sync()
-        err, _ = o.max_rel_err(g.get_state())
-        out["reference_check"][DTYPE[W]] = {"steps": 3, "max_rel_err_vs_256bit": err}
-        g.close()
-    # full-length c1 in all arithmetics
-    states, times = {}, {}
-    for W in (4, 2, 1):
-        g = teuk.Teuk.from_problem(c1, precision=W)
-        g.set_initial_pulse(c1.center, c1.width, ar, ai, c1.ell)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        g.step(c1.steps)
-        g.sync()
-        times[W] = time.perf_counter() - t0
-        states[W] = g.get_state()
-        g.close()
-    ref = states[4]
-    scale = np.abs(ref[:, 0]).max()
-    for W in (1, 2):
-        err = float(np.abs(word_diff(states[W], ref)).max() / scale)
-        out["c1_full_run"][DTYPE[W]] = {"steps": c1.steps, "max_rel_err_vs_qd": err,
-                                        "digits": -np.log10(err) if err > 0 else None,
-                                        "seconds": times[W]}
-    out["c1_full_run"][DTYPE[4]] = {"steps": c1.steps, "seconds": times[4],
-                                    "max_abs_field": float(scale)}
-    # throughput on the c2 grid
-    for W, nst in ((1, 3), (2, 2), (4, 1)):
-        p = c2
-        g = teuk.Teuk.from_problem(p, precision=W)
-        g.set_initial_pulse(p.center, p.width, ar, ai, p.ell)
-        g.tune()
-        g.step(1)
-        g.sync()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        g.step(nst)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1)
-        ups = p.n_r * p.n_theta * p.substeps * nst / (ms * 1e-3)
-        out["throughput_c2_grid"][DTYPE[W]] = {"updates_per_s": ups, "ns_per_update": 1e9 / ups}
-        g.close()
-    for W in (1, 2):
-        d = out["c1_full_run"][DTYPE[W]]["digits"]
-        ns = out["throughput_c2_grid"][DTYPE[W]]["ns_per_update"]
-        out["c1_full_run"][DTYPE[W]]["ns_per_update_per_digit"] = ns / d if d else None
+    out = {}
+    for name in ("c1", "c2", "c3"):
+        prob = workloads.CONFIGS[name]
+        ar, ai = prob.amps
+        res = {"outer_steps": DIGITS_STEPS[name], "stated_steps": prob.steps, "reference_check": {},
+               "run": {}, "cost": {}}
+        # 256-bit check of a short prefix in every arithmetic
+        nsub = 3 * prob.substeps
+        if name == "c1":
+            lo, hi, wlo, whi = 0, prob.n_r - 1, 0, prob.n_r - 1
+        else:
+            ic = int(round((prob.center - prob.rstar_min) / prob.dr))
+            lo, hi = ic - 12, ic + 12
+            wlo, whi = lo - nsub - 3, hi + nsub + 3
+        o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
+                          rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
+                          substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=256,
+                          ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta)
+        o.pulse(prob.center, prob.width, ar, ai, prob.ell)
+        o.step(nsub)
+        states, cost = {}, {}
+        for W in (1, 2, 4):
+            g = teuk.Teuk.from_problem(prob, precision=W)
+            if W > 1:
+                g.set_engine(1)
+            g.tune()
+            g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+            g.step(3)
+            g.sync()
+            st = g.get_state()
+            err, _ = o.max_rel_err(np.ascontiguousarray(st[:, :, wlo:whi + 1]), lo - wlo, hi - wlo)
+            res["reference_check"][DTYPE[W]] = {"outer_steps": 3, "max_rel_err_vs_256bit": err,
+                                                "rows": f"{lo}..{hi}"}
+            g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.step(DIGITS_STEPS[name])
+            e1.record(stream)
+            g.sync()
+            ms = e0.elapsed_time(e1)
+            states[W] = g.get_state()
+            cost[W] = ms * 1e6 / (prob.points * prob.substeps * DIGITS_STEPS[name])
+            g.close()
+        ref = states[4]
+        scale = np.abs(ref[:, 0]).max()
+        for W in (1, 2):
+            err = float(np.abs(word_diff(states[W], ref)).max() / scale)
+            d = -np.log10(err) if err > 0 else None
+            res["run"][DTYPE[W]] = {"max_rel_err_vs_qd": err, "digits": d,
+                                    "ns_per_update": cost[W], "ns_per_update_per_digit": cost[W] / d if d else None}
+        res["run"][DTYPE[4]] = {"max_abs_field": float(scale), "ns_per_update": cost[4]}
+        out[name] = res
     print(json.dumps({"digits_table": out}))
     return 0
 
@@ -654,6 +659,9 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prob = workloads.CONFIGS[args.workload]
+    if args.n_r:
+        prob = prob.with_(n_r=args.n_r)
+        args.no_variants = args.no_batch = True
     W = args.precision or MAIN_WORDS.get(args.workload, prob.words)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.Stream()
@@ -703,9 +711,15 @@ def main():
                 if w > 1:
                     entry["roofline"] = roofline_for(r, p, w, 1, clocks, sms, fp64_probe, int_probe, name)
                 variants[f"{name}/{DTYPE[w].split(' ')[0]}"] = entry
-            ups, msps = run_batch1(workloads.CONFIGS["c1"], 1, 20, torch, teuk)
-            variants["c1/f64 batched kernel"] = {"updates_per_s": ups, "ms_per_step": msps,
-                                                 "launch": "one cooperative launch, 20 steps"}
+            c1_plain = workloads.CONFIGS["c1"].with_(ko_sigma=0.0)  # batches take no dissipation
+            ups, msps = run_batch1(c1_plain, 1, 20, torch, teuk)
+            variants["c1/f64 batched kernel, no dissipation"] = {
+                "updates_per_s": ups, "ms_per_step": msps, "launch": "one cooperative launch, 20 steps"}
+            r = run_workload(c1_plain, 1, 20, 1, torch, teuk, flush, with_timing=False)
+            variants["c1/f64 no dissipation"] = {
+                "updates_per_s": c1_plain.points * c1_plain.substeps * 20 / (r["ms_total"] * 1e-3),
+                "ms_per_step": r["ms_total"] / 20, "launch_shape": r["rows_per_block"],
+                "launch": "tuned: CUDA graph per outer step or persistent launches (variant 9)"}
             c2 = workloads.CONFIGS["c2"]
             p2 = c2.with_(theta_order=2)
             r = run_workload(p2, 2, 2, 1, torch, teuk, flush, with_timing=False, engine=1)

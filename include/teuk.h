@@ -72,6 +72,32 @@ int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
                 teuk_precision precision, void* cuda_stream);
 int teuk_destroy(teuk_t h);
 
+/* r* slabs: one problem split along r* over several handles (the paper's decomposition of
+ * the grid over processing elements, Sec. 4, applied across GPUs or streams). A slab handle
+ * advances the global nodes own_lo .. own_hi (0 <= own_lo <= own_hi <= n_r - 1) of the grid
+ * `grid` and holds one halo row beyond each end that lies inside the grid: local row 0 is
+ * global row row0 = max(own_lo - 1, 0). Its tables are those of the global rows, so one
+ * iteration gives bit for bit the values the whole-grid handle gives on the owned rows,
+ * provided the halo rows hold the neighbours' rows of the same iteration. Advance with
+ * teuk_substep(h, 1) (more than one iteration per call and teuk_step are refused), after
+ * copying the neighbours' edge rows in: per iteration, teuk_get_halo_rows on every slab, then
+ * teuk_set_halo_rows on every slab, then teuk_substep(h, 1). Array arguments of the slab
+ * calls (teuk_set_initial, teuk_get_state, ...) cover its local rows; the observer must be one
+ * of its owned nodes; no dissipation, batches or persistent launches. At least three local
+ * rows. The caller owns the exchange and its ordering between streams. */
+int teuk_create_slab(teuk_t* out, double M, double a, int s, int m, const teuk_grid* grid,
+                     teuk_precision precision, void* cuda_stream, int own_lo, int own_hi);
+/* The slab's first and last owned rows (global own_lo and own_hi), [4][w][n_theta] doubles
+ * each, into lo_out / hi_out (device or page-locked host memory; NULL to skip), queued on the
+ * handle's stream: what the neighbours below / above need as their halo rows. */
+int teuk_get_halo_rows(teuk_t h, double* lo_out, double* hi_out);
+/* Writes the halo rows (global own_lo - 1 from lo_in, own_hi + 1 from hi_in; same layout and
+ * memory kinds; NULL to skip), queued on the handle's stream. There is no halo beyond global
+ * row 0 or n_r - 1: a non-NULL pointer there is TEUK_ERR_INVALID_ARG. */
+int teuk_set_halo_rows(teuk_t h, const double* lo_in, const double* hi_in);
+/* Global index of local row 0 and the owned rows (a whole-grid handle: 0, 0, n_r - 1). */
+int teuk_slab_rows(teuk_t h, int* row0, int* own_lo, int* own_hi);
+
 /* Initial data from host word planes phi_pi[4][w][n_r][n_theta] (copied to the device).
  * Rows 0 and n_r-1 are set to zero (Sec. 3.B). Resets the step counter. */
 int teuk_set_initial(teuk_t h, const double* phi_pi);

@@ -102,7 +102,7 @@ int teuk_batch_create(teuk_batch_t* out, const teuk_t* members, int n_members) {
   b->stream = b->members[0]->stream;
   b->engine = b->members[0]->engine;
   for (teuk_s* h : b->members)
-    if (h->W != b->W || h->device != b->device || h->dissipating() || h->engine != b->engine ||
+    if (h->W != b->W || h->device != b->device || h->dissipating() || h->is_slab() || h->engine != b->engine ||
         (h->engine == 1 && !h->ix_m)) {
       delete b;
       return TEUK_ERR_INVALID_ARG;

@@ -114,13 +114,15 @@ int copy_planes(teuk_s* h, double* dev, const double* host_in, double* host_out,
   return TEUK_OK;
 }
 
+// Local row of the node nearest rstar_obs (ties toward the lower index, computed in FP64), or
+// -1 if a slab does not own that node.
 int observer_row(const teuk_s* h, double rstar_obs) {
-  // nearest node, ties toward the lower index, computed in FP64
   const double q = (rstar_obs - h->rsmin_d) / h->dr_d;
   int i = (int)std::ceil(q - 0.5);
   if (i < 0) i = 0;
-  if (i > h->n_r - 1) i = h->n_r - 1;
-  return i;
+  if (i > h->grid.n_r - 1) i = h->grid.n_r - 1;
+  if (h->is_slab() && (i < h->own_lo || i > h->own_hi)) return -1;
+  return i - h->row0;
 }
 
 __global__ void fp64_peak_kernel(double* out, double a, double b, int iters) {
@@ -277,6 +279,11 @@ void time_end(teuk_s* h, int kind, cudaEvent_t a) {
 }
 }  // namespace teuk
 
+namespace {
+int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* grid, teuk_precision precision,
+                void* cuda_stream, int own_lo, int own_hi);
+}
+
 extern "C" {
 
 const char* teuk_strerror(int code) {
@@ -297,6 +304,22 @@ const char* teuk_last_error(teuk_t h) { return h ? h->last_error.c_str() : ""; }
 
 int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* grid,
                 teuk_precision precision, void* cuda_stream) {
+  return create_impl(out, M, a, s, m, grid, precision, cuda_stream, 0, -1);
+}
+
+int teuk_create_slab(teuk_t* out, double M, double a, int s, int m, const teuk_grid* grid,
+                     teuk_precision precision, void* cuda_stream, int own_lo, int own_hi) {
+  if (!grid || own_lo < 0 || own_hi < own_lo || own_hi > grid->n_r - 1) return TEUK_ERR_INVALID_ARG;
+  const int lo = own_lo > 0 ? own_lo - 1 : 0, hi = own_hi < grid->n_r - 1 ? own_hi + 1 : own_hi;
+  if (hi - lo + 1 < 3) return TEUK_ERR_INVALID_ARG;  // the kernels need three rows
+  return create_impl(out, M, a, s, m, grid, precision, cuda_stream, own_lo, own_hi);
+}
+
+}  // extern "C"
+
+namespace {
+int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* grid, teuk_precision precision,
+                void* cuda_stream, int own_lo, int own_hi) {
   if (!out || !grid) return TEUK_ERR_INVALID_ARG;
   *out = nullptr;
   const int W = (int)precision;
@@ -325,6 +348,12 @@ int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   h->grid = g;
   h->W = W;
   h->n_r = g.n_r;
+  if (own_hi >= 0) {  // an r* slab: the owned rows and one halo row on each side inside the grid
+    h->own_lo = own_lo;
+    h->own_hi = own_hi;
+    h->row0 = own_lo > 0 ? own_lo - 1 : 0;
+    h->n_r = (own_hi < g.n_r - 1 ? own_hi + 1 : own_hi) - h->row0 + 1;
+  }
   h->n_th = g.n_theta;
   h->pitch = ((g.n_theta + 15) / 16) * 16;
   h->parity = g.parity != 0 ? g.parity : (((m + s) % 2 == 0) ? 1 : -1);
@@ -365,6 +394,9 @@ int teuk_create(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   *out = h;
   return TEUK_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int teuk_destroy(teuk_t h) {
   if (!h) return TEUK_ERR_INVALID_ARG;
@@ -375,6 +407,46 @@ int teuk_destroy(teuk_t h) {
   free_all(h);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
+  return TEUK_OK;
+}
+
+// One state row [4][W][n_theta] between local row `row` and a buffer (device or host memory).
+static int copy_row(teuk_s* h, int row, double* dst, const double* src) {
+  const size_t plane = (size_t)h->n_r * h->pitch * sizeof(double), line = (size_t)h->n_th * sizeof(double);
+  double* r = h->u + (size_t)row * h->pitch;
+  if (dst) {
+    TEUK_CUDA(h, cudaMemcpy2DAsync(dst, line, r, plane, line, (size_t)4 * h->W, cudaMemcpyDefault, h->stream));
+  } else {
+    TEUK_CUDA(h, cudaMemcpy2DAsync(r, plane, src, line, line, (size_t)4 * h->W, cudaMemcpyDefault, h->stream));
+  }
+  return TEUK_OK;
+}
+
+int teuk_get_halo_rows(teuk_t h, double* lo_out, double* hi_out) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (!h->is_slab()) return invalid(h, "halo rows: not a slab");
+  int rc = TEUK_OK;
+  if (lo_out) rc = copy_row(h, h->own_lo - h->row0, lo_out, nullptr);
+  if (rc == TEUK_OK && hi_out) rc = copy_row(h, h->own_hi - h->row0, hi_out, nullptr);
+  return rc;
+}
+
+int teuk_set_halo_rows(teuk_t h, const double* lo_in, const double* hi_in) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (!h->is_slab()) return invalid(h, "halo rows: not a slab");
+  if ((lo_in && h->own_lo == 0) || (hi_in && h->own_hi == h->grid.n_r - 1))
+    return invalid(h, "halo rows: no halo beyond an r* boundary row");
+  int rc = TEUK_OK;
+  if (lo_in) rc = copy_row(h, 0, nullptr, lo_in);
+  if (rc == TEUK_OK && hi_in) rc = copy_row(h, h->n_r - 1, nullptr, hi_in);
+  return rc;
+}
+
+int teuk_slab_rows(teuk_t h, int* row0, int* own_lo, int* own_hi) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  if (row0) *row0 = h->row0;
+  if (own_lo) *own_lo = h->is_slab() ? h->own_lo : 0;
+  if (own_hi) *own_hi = h->is_slab() ? h->own_hi : h->n_r - 1;
   return TEUK_OK;
 }
 
@@ -394,12 +466,14 @@ int teuk_set_initial(teuk_t h, const double* phi_pi) {
   if (!h || !phi_pi) return invalid(h, "null argument");
   int rc = copy_planes(h, h->u, phi_pi, nullptr, 4, h->n_r);
   if (rc) return rc;
-  // Phi = Pi = 0 on the r* boundary rows (Sec. 3.B)
+  // Phi = Pi = 0 on the r* boundary rows (Sec. 3.B); a slab's halo rows are data
   const size_t ws = (size_t)h->n_r * h->pitch;
+  const bool first = h->row0 == 0, last = h->row0 + h->n_r - 1 == h->grid.n_r - 1;
   for (int p = 0; p < 4 * h->W; ++p) {
-    TEUK_CUDA(h, cudaMemsetAsync(h->u + p * ws, 0, h->pitch * sizeof(double), h->stream));
-    TEUK_CUDA(h, cudaMemsetAsync(h->u + p * ws + (size_t)(h->n_r - 1) * h->pitch, 0, h->pitch * sizeof(double),
-                                 h->stream));
+    if (first) TEUK_CUDA(h, cudaMemsetAsync(h->u + p * ws, 0, h->pitch * sizeof(double), h->stream));
+    if (last)
+      TEUK_CUDA(h, cudaMemsetAsync(h->u + p * ws + (size_t)(h->n_r - 1) * h->pitch, 0, h->pitch * sizeof(double),
+                                   h->stream));
   }
   h->substeps_done = 0;
   h->n_recorded = 0;
@@ -426,6 +500,8 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
 
 int teuk_substep(teuk_t h, int64_t n) {
   if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
+  if (h->is_slab() && n > 1)
+    return invalid(h, "slab: one iteration per call (the halo rows are exchanged between iterations)");
   for (int64_t t = 0; t < n; ++t) {
     int rc = iterate(h, false, 0);
     if (rc) return rc;
@@ -488,6 +564,7 @@ int teuk_set_dissipation(teuk_t h, double sigma) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   if (!(sigma >= 0) || !std::isfinite(sigma) || sigma > 4.0)
     return invalid(h, "dissipation: need 0 <= sigma <= 4");
+  if (h->is_slab() && sigma > 0) return invalid(h, "dissipation: not on a slab (it reads two rows beyond the halo)");
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   if (sigma > 0 && !h->u_ko)
     TEUK_CUDA(h, cudaMalloc(&h->u_ko, (size_t)4 * h->W * h->n_r * h->pitch * sizeof(double)));
@@ -504,6 +581,7 @@ int teuk_set_theta_dissipation(teuk_t h, double sigma) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   if (!(sigma >= 0) || !std::isfinite(sigma) || sigma > 4.0)
     return invalid(h, "theta dissipation: need 0 <= sigma <= 4");
+  if (h->is_slab() && sigma > 0) return invalid(h, "theta dissipation: not on a slab");
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graph(h);
   if (sigma == 0) {
@@ -536,6 +614,7 @@ double teuk_theta_dissipation(teuk_t h) { return h ? h->ko_theta : -1.0; }
 
 int teuk_step(teuk_t h, int64_t n) {
   if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
+  if (h->is_slab()) return invalid(h, "slab: advance with teuk_substep(h, 1) and a halo exchange per iteration");
   if (n > 0 && h->kernel_family == 3 && h->engine == 0 && !h->dissipating() && h->substeps_done % h->k == 0)
     return step_persistent(h, n);
   if (n > 0 && graphs_possible(h)) {
@@ -588,17 +667,25 @@ int teuk_sync(teuk_t h) {
 int teuk_observe(teuk_t h, double rstar_obs, double* out_phi, double* rstar_used) {
   if (!h || !out_phi || !std::isfinite(rstar_obs)) return TEUK_ERR_INVALID_ARG;
   const int i = observer_row(h, rstar_obs);
+  if (i < 0) {
+    h->last_error = "observer: the node is not one of this slab's rows";
+    return TEUK_ERR_STATE_MISMATCH;
+  }
   const size_t ws = (size_t)h->n_r * h->pitch;
   for (int p = 0; p < 2 * h->W; ++p)
     TEUK_CUDA(h, cudaMemcpyAsync(out_phi + (size_t)p * h->n_th, h->u + p * ws + (size_t)i * h->pitch,
                                  h->n_th * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (rstar_used) *rstar_used = h->rsmin_d + i * h->dr_d;
+  if (rstar_used) *rstar_used = h->rsmin_d + (i + h->row0) * h->dr_d;
   return TEUK_OK;
 }
 
 int teuk_set_observer(teuk_t h, double rstar_obs, int64_t capacity) {
   if (!h || capacity < 1 || !std::isfinite(rstar_obs)) return TEUK_ERR_INVALID_ARG;
+  if (observer_row(h, rstar_obs) < 0) {
+    h->last_error = "observer: the node is not one of this slab's rows";
+    return TEUK_ERR_STATE_MISMATCH;
+  }
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->ring) cudaFree(h->ring);
   h->ring = nullptr;

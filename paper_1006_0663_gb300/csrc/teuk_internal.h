@@ -27,7 +27,10 @@ struct teuk_s {
   int pflags_cap = 0;
   int bal_key = -1;        // (variant, threads) the balanced grid sizes below were computed for
   int bal_grid[2] = {0, 0};  // blocks of the balanced half / full kernels (resident capacity)
-  int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;
+  int n_r = 0, n_th = 0, pitch = 0, parity = 1, radius = 5, k = 1;  // n_r: rows held (local)
+  int row0 = 0;            // global index of local row 0 (r* slab: own_lo - 1 or 0)
+  int own_lo = 0, own_hi = -1;  // global rows a slab advances; -1: the whole grid (no slab)
+  bool is_slab() const { return own_hi >= 0; }
   double dt_outer = 0;  // leading word of the outer step
   int device = 0;
   cudaStream_t stream = nullptr;

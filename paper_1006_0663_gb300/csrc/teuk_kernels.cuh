@@ -155,6 +155,7 @@ struct Geom {
 
 struct SetupArgs {
   Geom g;
+  int row0;      // global index of local row 0 (0 unless the handle holds an r* slab)
   int W;
   double M, a;
   int s, m;
@@ -187,7 +188,7 @@ __global__ void tortoise_kernel(SetupArgs a) {
   const R A = from_words<R>(a.tort_A), B = from_words<R>(a.tort_B);
   const R ln2 = from_words<R>(a.ln2), ln2M = from_words<R>(a.ln2M);
   const R dr = from_words<R>(a.dr);
-  const double fi = half ? double(i) + 0.5 : double(i);  // exact
+  const double fi = half ? double(i + a.row0) + 0.5 : double(i + a.row0);  // exact
   const R target = mw::r_add(from_words<R>(a.rsmin), mw::r_mul_d(dr, fi));
   const R twoM = mw::r_from<R>(2.0 * a.M);
   // double-precision bracket
@@ -330,6 +331,7 @@ __global__ void coeff_kernel(SetupArgs a, int half) {
 
 struct PulseArgs {
   Geom g;
+  int row0, n_r_global;   // global index of local row 0; rows of the whole grid
   double center, width, amp_re, amp_im;
   double ln2[4];
   const double* rs_node;  // [W][n_r]
@@ -349,7 +351,7 @@ __global__ void pulse_kernel(PulseArgs a) {
   if (j >= a.g.n_th || i >= a.g.n_r) return;
   const size_t ws = (size_t)a.g.n_r * a.g.pitch;
   const size_t idx = (size_t)i * a.g.pitch + j;
-  if (i == 0 || i == a.g.n_r - 1) {
+  if (i + a.row0 == 0 || i + a.row0 == a.n_r_global - 1) {  // r* boundary rows (Sec. 3.B)
     for (int c = 0; c < 4; ++c) st_r(a.u + (size_t)c * W * ws + idx, ws, r_from<R>(0.0));
     return;
   }
@@ -919,16 +921,18 @@ struct PersistArgs {
   int spin_log2;          // a wait gives up after 2^spin_log2 polls
 };
 
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
   int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_release_gpu(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0 waits until *f >= target (or gives up); the result reaches the whole block.
+// Thread 0 waits until *f >= target (or gives up); the result reaches the whole block. The
+// polls are relaxed loads; the fence after the one that sees the target makes it an acquire,
+// and the block barrier orders the other threads' later reads after it.
 __device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f, int target, int* ok_sm) {
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     int ok = 1;
@@ -937,10 +941,12 @@ __device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f,
       const int* abortw = p.flags + 2 * gridDim.x;
       ok = 0;
       for (long long it = 0; it < limit; ++it) {
-        if (ld_acquire_gpu(f) >= target) { ok = 1; break; }
-        if (ld_acquire_gpu(abortw)) break;
+        if (ld_relaxed_gpu(f) >= target) { ok = 1; break; }
+        if ((it & 63) == 63 && ld_relaxed_gpu(abortw)) break;
       }
-      if (!ok) {
+      if (ok) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      } else {
         atomicOr(p.a.status, 2u);
         atomicExch(p.flags + 2 * gridDim.x, 1);
       }
@@ -951,15 +957,17 @@ __device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f,
   return *ok_sm != 0;
 }
 
+// After the block barrier, thread 0's release store publishes every write the block made
+// before it (the barrier orders the other threads' writes before the store).
 __device__ __forceinline__ void persist_publish(int* f, int value) {
   __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    __threadfence();
-    st_release_gpu(f, value);
-  }
+  if (threadIdx.x == 0 && threadIdx.y == 0) st_release_gpu(f, value);
 }
 
 // blockDim = (threads along theta, R rows); grid = ceil((n_r - 1) / R) co-resident blocks.
+// (Doing a block's rows that need nothing from a neighbour before the wait, and only the
+// neighbour-dependent row after it, measured slower on the 256 x 64 FP64 grid: each stage
+// leaves part of the block idle.)
 template <int W>
 __global__ void __launch_bounds__(256, 1) persist_kernel(PersistArgs p) {
   extern __shared__ double sm[];

@@ -58,7 +58,7 @@ int setup_impl(teuk_s* h) {
   const R ln2 = r_ln2<R>();
   const R ln2M = r_log(twoM, ln2);
   const R rsmin = r_from<R>(g.rstar_min);
-  const R dr = r_div(r_sub(r_from<R>(g.rstar_max), rsmin), r_from<R>(double(n_r - 1)));
+  const R dr = r_div(r_sub(r_from<R>(g.rstar_max), rsmin), r_from<R>(double(g.n_r - 1)));  // global rows
   const R dt = g.dt > 0 ? r_from<R>(g.dt) : r_scale2(dr, 0.25);
   const R dts = r_div(dt, r_from<R>(double(h->k)));
   const R lambda = r_div(dts, dr);
@@ -110,6 +110,7 @@ int setup_impl(teuk_s* h) {
 
   SetupArgs sa{};
   sa.g = Geom{n_r, n_th, pitch, h->parity};
+  sa.row0 = h->row0;
   sa.W = W;
   sa.M = h->M;
   sa.a = h->a;
@@ -182,6 +183,8 @@ int pulse_impl(teuk_s* h, double center, double width, double ar, double ai, int
   TEUK_CUDA(h, cudaMemcpyAsync(h->prof, prof.data(), prof.size() * 8, cudaMemcpyHostToDevice, h->stream));
   PulseArgs pa{};
   pa.g = Geom{h->n_r, n_th, h->pitch, h->parity};
+  pa.row0 = h->row0;
+  pa.n_r_global = h->grid.n_r;
   pa.center = center;
   pa.width = width;
   pa.amp_re = ar;

@@ -30,6 +30,7 @@ SYMBOLS = [
     "teuk_set_launch_shape", "teuk_read_multipoles", "teuk_substep_host_state",
     "teuk_set_dissipation", "teuk_set_engine", "teuk_engine", "teuk_set_theta_dissipation",
     "teuk_theta_dissipation", "teuk_int_peak", "teuk_test_stall_copies", "teuk_set_persistent",
+    "teuk_create_slab", "teuk_get_halo_rows", "teuk_set_halo_rows", "teuk_slab_rows",
 ]
 
 
@@ -66,6 +67,10 @@ def lib(build_if_missing: bool = True):
         dp = P(d)
         L.teuk_create.argtypes = [P(vp), d, d, i32, i32, P(TeukGrid), i32, vp]
         L.teuk_destroy.argtypes = [vp]
+        L.teuk_create_slab.argtypes = [P(vp), d, d, i32, i32, P(TeukGrid), i32, vp, i32, i32]
+        L.teuk_get_halo_rows.argtypes = [vp, vp, vp]
+        L.teuk_set_halo_rows.argtypes = [vp, vp, vp]
+        L.teuk_slab_rows.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.teuk_set_initial.argtypes = [vp, dp]
         L.teuk_set_initial_pulse.argtypes = [vp, d, d, d, d, i32]
         L.teuk_step.argtypes = [vp, i64]
@@ -119,6 +124,13 @@ def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _addr(buf):
+    """A buffer argument as a pointer: a tensor's data, an integer address, or NULL."""
+    if buf is None:
+        return None
+    return ctypes.c_void_p(int(buf.data_ptr()) if hasattr(buf, "data_ptr") else int(buf) or None)
+
+
 def _check(rc, handle=None):
     if rc != OK:
         L = lib()
@@ -150,19 +162,32 @@ class Teuk:
     """One Teukolsky problem on the GPU (see include/teuk.h)."""
 
     def __init__(self, *, M, a, s, m, rstar_min, rstar_max, n_r, n_theta, dt=0.0, substeps=1,
-                 theta_order=10, parity=0, precision=FP64, stream="current"):
+                 theta_order=10, parity=0, precision=FP64, stream="current", own_rows=None):
+        """own_rows = (own_lo, own_hi): an r* slab of the grid (teuk_create_slab); n_r is then
+        the whole grid's and self.n_r the slab's local rows (owned rows and halos)."""
         L = lib()
         self.grid = TeukGrid(float(rstar_min), float(rstar_max), int(n_r), int(n_theta), float(dt),
                              int(substeps), int(theta_order), int(parity), 0)
         h = ctypes.c_void_p()
         st = _current_stream() if stream == "current" else stream
-        rc = L.teuk_create(ctypes.byref(h), float(M), float(a), int(s), int(m),
-                           ctypes.byref(self.grid), int(precision), st)
+        if own_rows is None:
+            rc = L.teuk_create(ctypes.byref(h), float(M), float(a), int(s), int(m),
+                               ctypes.byref(self.grid), int(precision), st)
+        else:
+            rc = L.teuk_create_slab(ctypes.byref(h), float(M), float(a), int(s), int(m),
+                                    ctypes.byref(self.grid), int(precision), st, int(own_rows[0]),
+                                    int(own_rows[1]))
         _check(rc)
         self._h = h
         self.words = int(precision)
-        self.n_r, self.n_theta = int(n_r), int(n_theta)
+        self.n_theta = int(n_theta)
         self.substeps = int(substeps)
+        r0, lo, hi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.teuk_slab_rows(h, ctypes.byref(r0), ctypes.byref(lo), ctypes.byref(hi)), h)
+        self.row0, self.own_lo, self.own_hi = r0.value, lo.value, hi.value
+        nr = ctypes.c_int()
+        _check(L.teuk_info(h, None, ctypes.byref(nr), None, None, None), h)
+        self.n_r = nr.value
 
     @classmethod
     def from_problem(cls, p, precision=None, **kw):
@@ -317,6 +342,15 @@ class Teuk:
         """Outer steps in persistent cooperative launches (variant 9; small problems)."""
         _check(lib().teuk_set_persistent(self._h, int(threads_theta), int(rows_per_block),
                                          int(steps_per_launch)), self._h)
+
+    def get_halo_rows(self, lo, hi):
+        """The slab's first / last owned rows into device (or page-locked host) buffers of
+        [4][words][n_theta] doubles: tensors or integer addresses (None / 0 to skip)."""
+        _check(lib().teuk_get_halo_rows(self._h, _addr(lo), _addr(hi)), self._h)
+
+    def set_halo_rows(self, lo, hi):
+        """The halo rows (own_lo - 1, own_hi + 1) from buffers like get_halo_rows' (None to skip)."""
+        _check(lib().teuk_set_halo_rows(self._h, _addr(lo), _addr(hi)), self._h)
 
     def use_graphs(self, enable=True):
         _check(lib().teuk_use_graphs(self._h, 1 if enable else 0), self._h)
