@@ -60,7 +60,9 @@ TRAFFIC = {("c2", "half_kernel<2, 1>"): (50.456e6 + 0.370e6, "128 x 1", "profile
            ("c2", "half_ix_kernel<2, 1>"): (64.05e6 + 1.68e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
            ("c2", "full_ix_kernel<2, 1>"): (81.10e6 + 2.65e6, "128 x 2", "profiles/step_kernels_ix_dd_c2.txt"),
            ("c3", "half_ix_kernel<4, 1>"): (27.01e6 + 0.12e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt"),
-           ("c3", "full_ix_kernel<4, 1>"): (34.75e6 + 1.38e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt")}
+           ("c3", "full_ix_kernel<4, 1>"): (34.75e6 + 1.38e6, "64 x 4", "profiles/step_kernels_ix_qd_c3.txt"),
+           # captured on the 2048-node case of c5, scaled to a full launch by the points
+           ("c5", "full_ix_kernel<2, 1>"): (3.00e9, "256 x 1", "profiles/step_kernels_ix_dd_c5.txt")}
 
 
 # Integer engine: algorithmic work per grid point of one launch (half or full kernel), in

@@ -55,7 +55,11 @@ typedef struct {
   int32_t n_r;          /* >= 3 */
   int32_t n_theta;      /* 6 .. 1024 */
   double dt;            /* outer step; 0 selects 0.25 dr* */
-  int32_t substeps;     /* >= 1 */
+  int32_t substeps;     /* >= 1, chosen by the caller: the smallest stable count comes from an
+                           eigenvalue study of the discrete operator (the midpoint-rule growth
+                           of the largest theta frequencies, those of the pole cells' (m + s cos
+                           th)^2 / sin^2 th potential for s != 0) that is run once per problem on
+                           the host; this library has no host arithmetic, so it does not pick k */
   int32_t theta_order;  /* 10 (Sec. 3.D, default if 0) or 2 (Sec. 3.B) */
   int32_t parity;       /* sign of the axis reflection of Phi and Pi: 0 selects (-1)^(m+s);
                            +1 / -1 explicit (the paper's rule is +1 for even |m|, -1 for odd) */

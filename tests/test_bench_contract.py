@@ -52,7 +52,7 @@ def test_roofline_tables_match_their_profiles():
         assert (workload, kname) in mod.TRAFFIC, kname
     # the engine's traffic figures are the ones printed in the summaries (MB, read + write)
     for (workload, kname), (traffic, shape, src) in mod.TRAFFIC.items():
-        if "_ix_kernel" not in kname:
+        if "_ix_kernel" not in kname or workload == "c5":  # c5: scaled from a smaller case
             continue
         text = open(os.path.join(root, src)).read()
         found = False
@@ -62,6 +62,16 @@ def test_roofline_tables_match_their_profiles():
                 pairs = [nums[k] + nums[k + 1] for k in range(0, len(nums) - 1, 2)]
                 found |= any(abs(p * 1e6 - traffic) < 0.02e6 for p in pairs)
         assert found, (kname, traffic, src)
+
+
+def test_c5_traffic_scaled_from_its_capture():
+    """The c5 engine kernel's traffic is the smaller case's bytes per point (375.1 MB over
+    2046 x 512 points) times a full launch's points."""
+    mod, root = _bench_module()
+    text = open(os.path.join(root, "profiles", "step_kernels_ix_dd_c5.txt")).read()
+    assert "375.1 MB" in text and "3.00 GB" in text
+    per_point = 375.1e6 / (2046 * 512)
+    assert abs(mod.TRAFFIC[("c5", "full_ix_kernel<2, 1>")][0] - per_point * 16382 * 512) < 0.01e9
 
 
 def _isnum(x):
