@@ -256,7 +256,10 @@ int teuk_batch_destroy(teuk_batch_t b);
 
 /* Autotuner: times a few Lax-Wendroff iterations for each candidate launch shape (threads
  * along theta x rows of theta per thread block, one warp per 32 columns, register budgets)
- * on a copy of the current state, keeps the fastest for this handle, restores the state and
+ * on a copy of the current state; when an outer step is short (under 5 ms) the four fastest
+ * are timed again over four outer steps as teuk_step runs them (a replayed CUDA graph), and the
+ * persistent launches are tried against them. It keeps the fastest for this handle, restores
+ * the state and
  * returns in *rows_per_block (may be NULL) the rows per block of the chosen shape, 0 when the
  * one-warp-per-32-columns kernels won (teuk_launch_shape reports the whole shape). Allocates
  * and frees one state-sized device buffer; call it before timing-critical work. */

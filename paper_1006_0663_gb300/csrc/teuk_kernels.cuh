@@ -921,18 +921,17 @@ struct PersistArgs {
   int spin_log2;          // a wait gives up after 2^spin_log2 polls
 };
 
-__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
-  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_release_gpu(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0 waits until *f >= target (or gives up); the result reaches the whole block. The
-// polls are relaxed loads; the fence after the one that sees the target makes it an acquire,
-// and the block barrier orders the other threads' later reads after it.
+// Thread 0 waits until *f >= target (or gives up); the result reaches the whole block. (Polling
+// with relaxed loads and one acquire fence at the end measured slower than acquire loads.)
 __device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f, int target, int* ok_sm) {
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     int ok = 1;
@@ -941,12 +940,10 @@ __device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f,
       const int* abortw = p.flags + 2 * gridDim.x;
       ok = 0;
       for (long long it = 0; it < limit; ++it) {
-        if (ld_relaxed_gpu(f) >= target) { ok = 1; break; }
-        if ((it & 63) == 63 && ld_relaxed_gpu(abortw)) break;
+        if (ld_acquire_gpu(f) >= target) { ok = 1; break; }
+        if (ld_acquire_gpu(abortw)) break;
       }
-      if (ok) {
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-      } else {
+      if (!ok) {
         atomicOr(p.a.status, 2u);
         atomicExch(p.flags + 2 * gridDim.x, 1);
       }
@@ -957,11 +954,13 @@ __device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f,
   return *ok_sm != 0;
 }
 
-// After the block barrier, thread 0's release store publishes every write the block made
-// before it (the barrier orders the other threads' writes before the store).
+// After the block barrier, thread 0 fences the block's writes and publishes with a release store.
 __device__ __forceinline__ void persist_publish(int* f, int value) {
   __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) st_release_gpu(f, value);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    st_release_gpu(f, value);
+  }
 }
 
 // blockDim = (threads along theta, R rows); grid = ceil((n_r - 1) / R) co-resident blocks.
