@@ -298,7 +298,7 @@ int teuk_set_persistent(teuk_t h, int threads_theta, int rows_per_block, int ste
  * they cannot afford cudaMalloc/cudaFree, which may synchronise the whole device). The paper
  * has no counterpart: this is an interface variant of teuk_substep.
  *  - h: an existing handle; only its constant tables, stream and device are used, its own
- *    state is neither read nor written.
+ *    state is neither read nor written. An r* slab handle takes one iteration per call.
  *  - u_in / u_out: caller-owned device buffers in the handle's layout
  *    [4][w][n_r][P] doubles, P = n_theta rounded up to a multiple of 16 (128 bytes); they may
  *    be the same buffer. Both must start on a 16-byte boundary (the integer engine copies

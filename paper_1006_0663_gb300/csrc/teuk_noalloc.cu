@@ -50,6 +50,10 @@ int rows_on_current_device(teuk_s* h, double** out) {
 
 extern "C" int teuk_substep_noalloc(teuk_t h, const double* u_in, double* u_out, int64_t n_iterations) {
   if (!h || !u_in || !u_out || n_iterations < 0) return TEUK_ERR_INVALID_ARG;
+  if (h->is_slab() && n_iterations > 1) {
+    h->last_error = "teuk_substep_noalloc: a slab takes one iteration per call (halo rows between iterations)";
+    return TEUK_ERR_INVALID_ARG;
+  }
   if (h->dissipating()) {
     h->last_error = "teuk_substep_noalloc: the dissipation step needs the handle's own buffers";
     return TEUK_ERR_INVALID_ARG;

@@ -5,6 +5,8 @@ C ABI's halo calls (paper_1006_0663_gb300.slab.LocalSlabs), reproduce the whole-
 bit for bit on their owned rows, and the 256-bit oracle within the parity tolerances. The
 multi-GPU form runs the same calls with torch.distributed messages between ranks (RankSlab,
 driven on CPU ranks in tests/test_multirank.py)."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -79,6 +81,11 @@ def test_slab_refusals_and_observer():
         g.set_observer(P["rstar_min"] + (hi_rows[0] + 2) * dr, 4)  # owned by the other slab
     obs, used = g.observe(P["rstar_min"] + 5 * dr)
     assert abs(used - (P["rstar_min"] + 5 * dr)) < 1e-12
+    pitch = (P["n_theta"] + 15) // 16 * 16
+    state = torch.zeros((4, 1, g.n_r, pitch), dtype=torch.float64, device="cuda")
+    L = teuk.lib()
+    rc = L.teuk_substep_noalloc(g._h, ctypes.c_void_p(state.data_ptr()), ctypes.c_void_p(state.data_ptr()), 2)
+    assert rc == teuk.ERR_INVALID_ARG       # several iterations need halo exchanges between them
     whole = teuk.Teuk(precision=1, **P)
     with pytest.raises(teuk.TeukError):
         whole.set_halo_rows(None, buf)  # not a slab
