@@ -173,6 +173,27 @@ inline void row_block_shape(const teuk_s* h, int& tx, int& ty) {
   while (ty > 1 && tx * ty > cap) ty /= 2;
 }
 
+// Launches a step kernel with programmatic stream serialization: its blocks may be scheduled
+// while the previous kernel of the stream runs; the kernel itself waits for that kernel's
+// completion before reading what it wrote (step_dependency in teuk_kernels.cuh). On the legacy
+// default stream it is an ordinary launch.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  const bool legacy = st == nullptr || st == (cudaStream_t)0x1;
+  cfg.attrs = legacy ? nullptr : &attr;
+  cfg.numAttrs = legacy ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 inline int cuda_fail(teuk_s* h, cudaError_t e, const char* what) {
   if (h) h->last_error = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? TEUK_ERR_OOM : TEUK_ERR_CUDA;

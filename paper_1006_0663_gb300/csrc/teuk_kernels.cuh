@@ -371,6 +371,19 @@ __global__ void pulse_kernel(PulseArgs a) {
   st_r(a.u + 3 * W * ws + idx, ws, r_mul(b, r_mul_d(GpY, a.amp_im)));
 }
 
+// ---- programmatic dependent launch ---------------------------------------------------------
+// The FP64 and FP64-error-free-transform step kernels (and the dissipation kernel) are
+// launched so that their blocks may be scheduled while the previous kernel of the stream still
+// runs (small grids spend more time in launches than in arithmetic: c1 +3 %; the integer
+// engine's kernels measured slower that way and are launched normally). Before reading anything that kernel wrote, a kernel waits for it to complete
+// and its writes to be visible (a no-op when it was launched without the attribute); only then
+// does it let the next kernel be scheduled, so at most two kernels' blocks are resident and
+// the earlier one's blocks have all started.
+__device__ __forceinline__ void step_dependency() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- dissipation (not part of the paper's method; off unless enabled) ---------------------
 // Once per outer step, before its first Lax-Wendroff iteration, every component becomes
 //   u - eps_r d_r^4 u - eps_th(i) d_th^12 u,
@@ -401,6 +414,7 @@ __device__ __forceinline__ double ko12_weight(int q) {
 template <int W>
 __global__ void dissipate_kernel(DissArgs a) {
   using R = typename RT<W>::T;
+  step_dependency();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y, c = blockIdx.z;
   if (j >= a.g.n_th) return;
@@ -780,6 +794,7 @@ __device__ __forceinline__ void seg_prep(const StepArgs& a, const double* src, s
 
 template <int W, int V = 0>
 __global__ void __launch_bounds__(128, 2 * (V + 1)) half_seg_kernel(StepArgs a, int nseg) {
+  step_dependency();
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -796,6 +811,7 @@ __global__ void __launch_bounds__(128, 2 * (V + 1)) half_seg_kernel(StepArgs a, 
 
 template <int W, int V = 0>
 __global__ void __launch_bounds__(128, 2 * (V + 1)) full_seg_kernel(StepArgs a, int nseg) {
+  step_dependency();
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -821,6 +837,7 @@ template <int V> struct RowBounds { static constexpr int threads = 256, blocks =
 template <> struct RowBounds<2> { static constexpr int threads = 128, blocks = 5; };
 template <int W, int V = 0>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) half_kernel(StepArgs a) {
+  step_dependency();
   extern __shared__ double sm[];
   const int gstride = a.g.n_th + 2 * a.radius;
   const int h = blockIdx.x * blockDim.y + threadIdx.y;
@@ -834,6 +851,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) h
 
 template <int W, int V = 0>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) full_kernel(StepArgs a) {
+  step_dependency();
   extern __shared__ double sm[];
   const int gstride = a.g.n_th + 2 * a.radius;
   const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
@@ -857,6 +875,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
 // row in shared memory, then take the range's columns of that row.
 template <int W, int V = 0>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) half_bal_kernel(StepArgs a) {
+  step_dependency();
   extern __shared__ double sm[];
   const int n_th = a.g.n_th, gstride = n_th + 2 * a.radius;
   const long long total = (long long)(a.g.n_r - 1) * n_th;
@@ -876,6 +895,7 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) h
 
 template <int W, int V = 0>
 __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) full_bal_kernel(StepArgs a) {
+  step_dependency();
   extern __shared__ double sm[];
   const int n_th = a.g.n_th, gstride = n_th + 2 * a.radius;
   const long long total = (long long)(a.g.n_r - 2) * n_th;

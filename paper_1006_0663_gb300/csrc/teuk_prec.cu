@@ -330,7 +330,7 @@ int dissipate_impl(teuk_s* h) {
   std::memcpy(da.eps, h->ko_eps_w, sizeof(da.eps));
   da.do_r = h->ko_sigma > 0;
   da.eps_th = h->ko_theta > 0 ? h->eps_th : nullptr;
-  dissipate_kernel<W><<<dim3((h->n_th + 63) / 64, h->n_r, 4), 64, 0, h->stream>>>(da);
+  TEUK_CUDA(h, launch_dep(dissipate_kernel<W>, dim3((h->n_th + 63) / 64, h->n_r, 4), dim3(64), 0, h->stream, da));
   TEUK_CUDA(h, cudaGetLastError());
   TEUK_CUDA(h, cudaMemcpyAsync(h->u, h->u_ko, (size_t)4 * W * h->n_r * h->pitch * sizeof(double),
                                cudaMemcpyDeviceToDevice, h->stream));
@@ -417,10 +417,12 @@ int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
     const int64_t units_h = (int64_t)nh * nseg, units_f = (int64_t)nf * nseg;
     cudaEvent_t ev = nullptr;
     time_begin(h, &ev);
-    half_seg_kernel<W, V><<<(unsigned)((units_h + 3) / 4), 128, seg_smem, h->stream>>>(sa, nseg);
+    TEUK_CUDA(h, launch_dep(half_seg_kernel<W, V>, dim3((unsigned)((units_h + 3) / 4)), dim3(128), seg_smem,
+                            h->stream, sa, nseg));
     time_end(h, 0, ev);
     time_begin(h, &ev);
-    full_seg_kernel<W, V><<<(unsigned)((units_f + 3) / 4), 128, seg_smem, h->stream>>>(sa, nseg);
+    TEUK_CUDA(h, launch_dep(full_seg_kernel<W, V>, dim3((unsigned)((units_f + 3) / 4)), dim3(128), seg_smem,
+                            h->stream, sa, nseg));
     time_end(h, 1, ev);
     h->launches += 2;
     TEUK_CUDA(h, cudaGetLastError());
@@ -431,10 +433,10 @@ int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
     if (rc != TEUK_OK) return rc;
     cudaEvent_t ev = nullptr;
     time_begin(h, &ev);
-    half_bal_kernel<W, V><<<h->bal_grid[0], blk.x, smem, h->stream>>>(sa);
+    TEUK_CUDA(h, launch_dep(half_bal_kernel<W, V>, dim3(h->bal_grid[0]), dim3(blk.x), smem, h->stream, sa));
     time_end(h, 0, ev);
     time_begin(h, &ev);
-    full_bal_kernel<W, V><<<h->bal_grid[1], blk.x, smem, h->stream>>>(sa);
+    TEUK_CUDA(h, launch_dep(full_bal_kernel<W, V>, dim3(h->bal_grid[1]), dim3(blk.x), smem, h->stream, sa));
     time_end(h, 1, ev);
     h->launches += 2;
     TEUK_CUDA(h, cudaGetLastError());
@@ -446,10 +448,10 @@ int launch_pair_v(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
   }
   cudaEvent_t ev = nullptr;
   time_begin(h, &ev);
-  half_kernel<W, V><<<(nh + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  TEUK_CUDA(h, launch_dep(half_kernel<W, V>, dim3((nh + blk.y - 1) / blk.y), blk, smem, h->stream, sa));
   time_end(h, 0, ev);
   time_begin(h, &ev);
-  full_kernel<W, V><<<(nf + blk.y - 1) / blk.y, blk, smem, h->stream>>>(sa);
+  TEUK_CUDA(h, launch_dep(full_kernel<W, V>, dim3((nf + blk.y - 1) / blk.y), blk, smem, h->stream, sa));
   time_end(h, 1, ev);
   h->launches += 2;
   TEUK_CUDA(h, cudaGetLastError());
