@@ -126,12 +126,15 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
  * FP64 handles accept 0 only. */
 int teuk_set_engine(teuk_t h, int engine);
 int teuk_engine(teuk_t h);
-/* Test hook of the integer engine's bounded wait (no counterpart in the paper): from the next
+/* Test hook of the bounded waits (no counterpart in the paper). Integer engine: from the next
  * launch on, thread block `block` of each engine step kernel arms its copy barrier with the
  * expected byte count but issues no copy, so its wait gives up after 2^wait_log2 tries
  * (10 <= wait_log2 <= 20) with nothing in flight; the kernel then skips that block's rows and
  * teuk_sync reports TEUK_ERR_TIMEOUT. The kernels stage at least their table rows while the
- * hook is set. block = -1 restores normal operation (wait limit 2^20). Engine 1 handles only. */
+ * hook is set. Persistent launches (teuk_set_persistent): block `block` never publishes its
+ * progress counters, so its neighbours' waits give up after 2^wait_log2 polls, every other
+ * wait ends on the abort word, and teuk_sync reports TEUK_ERR_TIMEOUT. block = -1 restores
+ * normal operation. Handles on the integer engine or on persistent launches only. */
 int teuk_test_stall_copies(teuk_t h, int block, int wait_log2);
 
 /* r* dissipation. NOT part of the paper's method (sigma = 0, the default, is the paper's

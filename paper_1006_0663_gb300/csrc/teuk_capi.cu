@@ -559,7 +559,8 @@ int teuk_engine(teuk_t h) { return h ? h->engine : TEUK_ERR_INVALID_ARG; }
 
 int teuk_test_stall_copies(teuk_t h, int block, int wait_log2) {
   if (!h) return TEUK_ERR_INVALID_ARG;
-  if (h->engine != 1) return invalid(h, "stall test: the bounded copy wait belongs to the integer engine");
+  if (h->engine != 1 && h->kernel_family != 3)
+    return invalid(h, "stall test: the bounded waits are the integer engine's and the persistent launches'");
   if (block < -1 || wait_log2 < 10 || wait_log2 > 20)
     return invalid(h, "stall test: block >= -1, 10 <= wait_log2 <= 20");
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));

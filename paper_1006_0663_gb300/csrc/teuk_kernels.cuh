@@ -939,6 +939,7 @@ struct PersistArgs {
   long long ring_base;    // samples recorded before this launch
   int* flags;             // [2 * gridDim.x + 1]: half_done, full_done, abort (zeroed before the launch)
   int spin_log2;          // a wait gives up after 2^spin_log2 polls
+  int stall_block;        // test hook: this block never publishes its counters (-1: none)
 };
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
@@ -975,9 +976,9 @@ __device__ __forceinline__ bool persist_wait(const PersistArgs& p, const int* f,
 }
 
 // After the block barrier, thread 0 fences the block's writes and publishes with a release store.
-__device__ __forceinline__ void persist_publish(int* f, int value) {
+__device__ __forceinline__ void persist_publish(const PersistArgs& p, int* f, int value) {
   __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
+  if (threadIdx.x == 0 && threadIdx.y == 0 && (int)blockIdx.x != p.stall_block) {
     __threadfence();
     st_release_gpu(f, value);
   }
@@ -1013,7 +1014,7 @@ __global__ void __launch_bounds__(256, 1) persist_kernel(PersistArgs p) {
       if (h_ok) half_row_prep<W>(a, h, tx, TX, sR, sI);
       __syncthreads();
       if (h_ok) half_row_out<W>(a, h, tx, TX, sR, sI);
-      persist_publish(half_done + b, n);
+      persist_publish(p, half_done + b, n);
       // Eq. lw2: half row b R - 1 must hold iteration n (and be read before row b R changes)
       if (!persist_wait(p, prev_half, n, &s_ok)) goto done;
       if (i_ok) full_row_prep<W>(a, h, tx, TX, sR, sI);
@@ -1022,7 +1023,7 @@ __global__ void __launch_bounds__(256, 1) persist_kernel(PersistArgs p) {
         const long long slot = (q == p.k - 1 && a.ring_cap > 0) ? (p.ring_base + s) % a.ring_cap : -1;
         bad |= full_row_out<W>(a, h, tx, TX, sR, sI, slot);
       }
-      persist_publish(full_done + b, n);
+      persist_publish(p, full_done + b, n);
     }
   }
 done:

@@ -552,7 +552,8 @@ int persist_impl(teuk_s* h, int64_t n_outer, long long ring_base) {
   pa.n_outer = (int)n_outer;
   pa.ring_base = ring_base;
   pa.flags = h->pflags;
-  pa.spin_log2 = 22;
+  pa.stall_block = h->test_stall_block;
+  pa.spin_log2 = h->test_stall_block >= 0 ? h->wait_log2 : 22;
   void* params[] = {&pa};
   TEUK_CUDA(h, cudaLaunchCooperativeKernel((const void*)persist_kernel<W>, dim3(G), dim3(tx, R), params, smem,
                                            h->stream));

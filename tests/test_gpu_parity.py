@@ -941,3 +941,25 @@ def test_persistent_c1_and_refusals():
     g.set_engine(1)
     with pytest.raises(teuk.TeukError):
         g.set_persistent(rows_per_block=2)
+
+
+def test_persistent_wait_gives_up_and_reports_timeout(oracle_mod):
+    """The persistent kernel's bounded waits: with the test hook one block never publishes its
+    progress counters, its neighbours give up after 2^10 polls, the abort word ends every
+    other wait, and teuk_sync reports TEUK_ERR_TIMEOUT; with the hook cleared and the state
+    replaced, the handle steps correctly again (bit-identical to graph replay)."""
+    p = small(n_r=53)
+    g = teuk.Teuk(precision=1, **p)
+    g.set_persistent(rows_per_block=2, steps_per_launch=2)
+    L = teuk.lib()
+    g.set_initial_pulse(8.0, 4.0, 0.8, 0.6, 2)
+    assert L.teuk_test_stall_copies(g._h, 3, 10) == teuk.OK
+    g.step(2)
+    assert L.teuk_sync(g._h) == teuk.ERR_TIMEOUT
+    assert L.teuk_test_stall_copies(g._h, -1, 20) == teuk.OK
+    ref = teuk.Teuk(precision=1, **p)
+    for h in (g, ref):
+        h.set_initial_pulse(8.0, 4.0, 0.8, 0.6, 2)
+        h.step(3)
+        h.sync()
+    np.testing.assert_array_equal(g.get_state(), ref.get_state())
