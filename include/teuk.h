@@ -61,9 +61,13 @@ typedef struct {
                            th)^2 / sin^2 th potential for s != 0) that is run once per problem on
                            the host; this library has no host arithmetic, so it does not pick k */
   int32_t theta_order;  /* 10 (Sec. 3.D, default if 0) or 2 (Sec. 3.B) */
-  int32_t parity;       /* sign of the axis reflection of Phi and Pi: 0 selects (-1)^(m+s);
-                           +1 / -1 explicit (the paper's rule is +1 for even |m|, -1 for odd) */
+  int32_t parity;       /* sign of the axis reflection of Phi and Pi: 0 selects (-1)^(m+s)
+                           (regularity of the spin-weighted harmonics), 2 the paper's rule
+                           (+1 for even |m|, -1 for odd, Sec. 3.B), +1 / -1 explicit */
   int32_t reserved;     /* must be 0 */
+  double ko_sigma;      /* r* dissipation (teuk_set_dissipation), not in the paper: 0 = off */
+  double ko_theta;      /* theta dissipation (teuk_set_theta_dissipation), not in the paper:
+                           0 = off; both are applied at creation with the setters' rules */
 } teuk_grid;
 
 typedef struct teuk_s* teuk_t;

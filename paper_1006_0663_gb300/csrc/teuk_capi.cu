@@ -343,7 +343,9 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   if (g.dt < 0 || !std::isfinite(g.dt)) return TEUK_ERR_INVALID_ARG;
   const int order = g.theta_order == 0 ? 10 : g.theta_order;
   if (order != 10 && order != 2) return TEUK_ERR_INVALID_ARG;
-  if (g.parity != 0 && g.parity != 1 && g.parity != -1) return TEUK_ERR_INVALID_ARG;
+  if (g.parity != 0 && g.parity != 1 && g.parity != -1 && g.parity != 2) return TEUK_ERR_INVALID_ARG;
+  if (!(g.ko_sigma >= 0) || !(g.ko_theta >= 0) || g.ko_sigma > 4.0 || g.ko_theta > 4.0) return TEUK_ERR_INVALID_ARG;
+  if (own_hi >= 0 && (g.ko_sigma > 0 || g.ko_theta > 0)) return TEUK_ERR_INVALID_ARG;  // slabs: no dissipation
   if ((int64_t)g.n_r * g.n_theta > (int64_t)1 << 31) return TEUK_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TEUK_ERR_NO_DEVICE;
@@ -365,7 +367,8 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   }
   h->n_th = g.n_theta;
   h->pitch = ((g.n_theta + 15) / 16) * 16;
-  h->parity = g.parity != 0 ? g.parity : (((m + s) % 2 == 0) ? 1 : -1);
+  h->parity = g.parity == 0 ? (((m + s) % 2 == 0) ? 1 : -1)
+              : g.parity == 2 ? ((std::abs(m) % 2 == 0) ? 1 : -1) : g.parity;
   h->radius = order == 10 ? 5 : 1;
   h->k = g.substeps;
   cudaGetDevice(&h->device);
@@ -400,6 +403,8 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   cudaMemsetAsync(h->d_ring_counter, 0, sizeof(long long), h->stream);
   rc = dispatch_setup(h);
   if (rc != TEUK_OK) return fail(rc);
+  if (g.ko_sigma > 0 && (rc = teuk_set_dissipation(h, g.ko_sigma)) != TEUK_OK) return fail(rc);
+  if (g.ko_theta > 0 && (rc = teuk_set_theta_dissipation(h, g.ko_theta)) != TEUK_OK) return fail(rc);
   *out = h;
   return TEUK_OK;
 }

@@ -41,6 +41,7 @@ class TeukGrid(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("substeps", ctypes.c_int32), ("theta_order", ctypes.c_int32),
         ("parity", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("ko_sigma", ctypes.c_double), ("ko_theta", ctypes.c_double),
     ]
 
 
@@ -162,12 +163,14 @@ class Teuk:
     """One Teukolsky problem on the GPU (see include/teuk.h)."""
 
     def __init__(self, *, M, a, s, m, rstar_min, rstar_max, n_r, n_theta, dt=0.0, substeps=1,
-                 theta_order=10, parity=0, precision=FP64, stream="current", own_rows=None):
+                 theta_order=10, parity=0, precision=FP64, stream="current", own_rows=None,
+                 ko_sigma=0.0, ko_theta=0.0):
         """own_rows = (own_lo, own_hi): an r* slab of the grid (teuk_create_slab); n_r is then
         the whole grid's and self.n_r the slab's local rows (owned rows and halos)."""
         L = lib()
         self.grid = TeukGrid(float(rstar_min), float(rstar_max), int(n_r), int(n_theta), float(dt),
-                             int(substeps), int(theta_order), int(parity), 0)
+                             int(substeps), int(theta_order), int(parity), 0, float(ko_sigma),
+                             float(ko_theta))
         h = ctypes.c_void_p()
         st = _current_stream() if stream == "current" else stream
         if own_rows is None:
@@ -194,11 +197,8 @@ class Teuk:
         g = cls(M=p.M, a=p.a, s=p.s, m=p.m, rstar_min=p.rstar_min, rstar_max=p.rstar_max,
                 n_r=p.n_r, n_theta=p.n_theta, dt=0.0, substeps=p.substeps,
                 theta_order=p.theta_order, parity=p.parity,
-                precision=precision if precision is not None else p.words, **kw)
-        if getattr(p, "ko_sigma", 0.0):
-            g.set_dissipation(p.ko_sigma)
-        if getattr(p, "ko_theta", 0.0):
-            g.set_theta_dissipation(p.ko_theta)
+                precision=precision if precision is not None else p.words,
+                ko_sigma=getattr(p, "ko_sigma", 0.0), ko_theta=getattr(p, "ko_theta", 0.0), **kw)
         return g
 
     def close(self):

@@ -963,3 +963,29 @@ def test_persistent_wait_gives_up_and_reports_timeout(oracle_mod):
         h.step(3)
         h.sync()
     np.testing.assert_array_equal(g.get_state(), ref.get_state())
+
+
+@pytest.mark.parametrize("W", [1, 2])
+def test_grid_fields_parity_rule_and_dissipation(W):
+    """teuk_grid.parity = 2 is the paper's |m| rule (bitwise equal to the explicit sign), and
+    ko_sigma / ko_theta given in the grid are the setters' dissipation (bitwise equal)."""
+    for m, s_, sign in ((1, -1, -1), (2, -1, 1), (3, 0, -1)):
+        p = small(m=m, s=s_)
+        a = teuk.Teuk(precision=W, **dict(p, parity=2))
+        b = teuk.Teuk(precision=W, **dict(p, parity=sign))
+        for g in (a, b):
+            g.set_initial_pulse(8.0, 4.0, 0.8, 0.6, max(abs(m), abs(s_)))
+            g.step(2)
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
+    p = small(s=0, m=0, n_theta=21)
+    a = teuk.Teuk(precision=W, ko_sigma=1.0, ko_theta=0.5, **p)
+    b = teuk.Teuk(precision=W, **p)
+    b.set_dissipation(1.0)
+    b.set_theta_dissipation(0.5)
+    assert a.theta_dissipation == 0.5
+    for g in (a, b):
+        g.set_initial_pulse(5.0, 3.0, 0.8, 0.55, 0)
+        g.step(3)
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
+    with pytest.raises(teuk.TeukError):
+        teuk.Teuk(precision=W, ko_sigma=-1.0, **p)
