@@ -226,7 +226,8 @@ def stated_error(prob, words, teuk, nsub=12, engine=0):
     o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
                       rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                       substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=bits,
-                      ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta)
+                      ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta,
+                      theta_filter=prob.theta_filter)
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     o.step(nsub)
     err, _ = o.max_rel_err(full[:, :, wlo:whi + 1].copy(), lo - wlo, hi - wlo)
@@ -483,7 +484,7 @@ def cpu_baseline(prob, words, seconds_target=15.0):
                       rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                       substeps=prob.substeps, parity=prob.parity, row_lo=lo,
                       row_hi=min(prob.n_r - 1, lo + rows - 1), bits=bits, ko_sigma=prob.ko_sigma,
-                      ko_theta=prob.ko_theta)
+                      ko_theta=prob.ko_theta, theta_filter=prob.theta_filter)
     ar, ai = prob.amps
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     done, t0 = 0, time.perf_counter()
@@ -547,6 +548,8 @@ def describe(prob, words=None):
     diss = ""
     if prob.ko_sigma or prob.ko_theta:
         diss = f", dissipation r* {prob.ko_sigma} theta {prob.ko_theta} (not in the paper)"
+    if prob.theta_filter:
+        diss += f", theta filter l < {prob.theta_filter} (not in the paper)"
     return (f"{prob.name}: {DTYPE[w]}, M={prob.M}, a={prob.a}, s={prob.s}, m={prob.m}, "
             f"r* in [{prob.rstar_min}, {prob.rstar_max}] x {prob.n_r} nodes, theta x {prob.n_theta} "
             f"cells, {prob.theta_order}th-order theta, dt=0.25 dr* with {prob.substeps} Lax-Wendroff "
@@ -565,10 +568,13 @@ def word_diff(a, b):
     return diff
 
 
-# Outer steps of the cost-per-digit runs: the stated length where the run stays bounded (c1),
-# else the prefix before the spurious growth of trapped high-l modes on these r* grids starts
-# (c2 from t ~ 850 M, c3 from t ~ 300 M; measured, see the stability study).
-DIGITS_STEPS = {"c1": 1000, "c2": 4000, "c3": 2000}
+# Outer steps of the cost-per-digit runs: the stated length for c1 and c3 (bounded with their
+# outer-step operators); for c2 a prefix (t = 244 M) well before the pulse, reflected by the
+# zero-field row at r* = 400, returns to the hole (t ~ 760 M): from then on the s = -2 field of
+# the problem as posed grows (so it does at a = 0 and on a twice finer r* grid, at a rate set
+# by the boundary's distance), and a 40,000-step run in all three arithmetics would cost
+# about 40 GPU-minutes.
+DIGITS_STEPS = {"c1": 1000, "c2": 4000, "c3": 40000}
 
 
 def digits_table():
@@ -605,7 +611,8 @@ def digits_table():
         o = oracle.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
                           rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                           substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=256,
-                          ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta)
+                          ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta,
+                          theta_filter=prob.theta_filter)
         o.pulse(prob.center, prob.width, ar, ai, prob.ell)
         o.step(nsub)
         states, cost = {}, {}

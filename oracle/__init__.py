@@ -39,6 +39,7 @@ class OracleParams(ctypes.Structure):
         ("row_lo", ctypes.c_int32), ("row_hi", ctypes.c_int32),
         ("ko_sigma", ctypes.c_double),
         ("ko_theta", ctypes.c_double),
+        ("theta_filter", ctypes.c_int32),
     ]
 
 
@@ -85,6 +86,7 @@ def lib():
         L.oracle_theta_op.argtypes = [i32, i32, i32, i32, dp, i32, dp, i32]
         L.oracle_spin_profile.argtypes = [i32, i32, i32, i32, i32, dp, i32]
         L.oracle_set_row.argtypes = [vp, i32, dp, i32]
+        L.oracle_filter_rows.argtypes = [vp]
         L.oracle_set_forcing.argtypes = [vp, d, dp, dp]
         L.oracle_fejer_weights.argtypes = [i32, i32, dp, i32]
         L.oracle_swsh.argtypes = [i32, i32, i32, i32, i32, dp, dp, i32]
@@ -126,7 +128,7 @@ class Oracle:
 
     def __init__(self, *, M, a, s, m, rstar_min, rstar_max, n_r, n_theta, dt, substeps=1,
                  theta_order=10, parity=None, row_lo=0, row_hi=None, bits=256, ko_sigma=0.0,
-                 ko_theta=0.0):
+                 ko_theta=0.0, theta_filter=0):
         if parity is None:
             parity = default_parity(m, s)
         if row_hi is None:
@@ -134,7 +136,7 @@ class Oracle:
         self.params = OracleParams(float(M), float(a), int(s), int(m), float(rstar_min),
                                    float(rstar_max), int(n_r), int(n_theta), float(dt),
                                    int(substeps), int(theta_order), int(parity), int(row_lo),
-                                   int(row_hi), float(ko_sigma), float(ko_theta))
+                                   int(row_hi), float(ko_sigma), float(ko_theta), int(theta_filter))
         self.bits = int(bits)
         self._h = lib().oracle_create(ctypes.byref(self.params), self.bits)
         if not self._h:
@@ -205,6 +207,12 @@ class Oracle:
         th = np.empty((words, self.nth)); ct = np.empty((words, self.nth))
         lib().oracle_get_grid(self._h, _dp(rn), _dp(xn), _dp(rh), _dp(xh), _dp(th), _dp(ct), words)
         return dict(rstar_node=rn, x_node=xn, rstar_half=rh, x_half=xh, theta=th, cot_theta=ct)
+
+    def filter_rows(self):
+        """Applies the theta filter (not part of the method; the `theta_filter` parameter) to
+        the current state, as at the start of an outer step."""
+        if lib().oracle_filter_rows(self._h) != 0:
+            raise ValueError("oracle: no theta filter on this problem")
 
     def step(self, n_substeps: int):
         lib().oracle_step(self._h, int(n_substeps))

@@ -118,6 +118,7 @@ struct oracle_params {
   int32_t row_lo, row_hi;  // window of r* rows simulated (inclusive), 0 .. n_r-1 for all
   double ko_sigma;         // r* dissipation strength (not in the paper; 0 = off), see dissipate()
   double ko_theta;         // theta dissipation strength (not in the paper; 0 = off), see dissipate()
+  int32_t theta_filter;    // theta filter (not in the paper; 0 = off): remove multipoles l >= this, see filter_rows()
 };
 
 }  // extern "C"
@@ -128,6 +129,9 @@ namespace {
 // scaled to integers: d2 * 25200 (second derivative), d1 * 2520 (first derivative).
 const double kD2_10[11] = {8, -125, 1000, -6000, 42000, -73766, 42000, -6000, 1000, -125, 8};
 const double kD1_10[11] = {-2, 25, -150, 600, -2100, 0, 2100, -600, 150, -25, 2};
+
+template <class T>
+T fejer_weight(int N, int j);
 
 template <class T>
 struct Solver {
@@ -237,6 +241,9 @@ struct Solver {
     if (p.parity != 1 && p.parity != -1) return -1;
     if (p.row_lo < 0 || p.row_hi >= p.n_r || p.row_hi - p.row_lo < 2) return -1;
     if (!(p.rstar_max > p.rstar_min) || !(p.dt >= 0) || !(p.ko_sigma >= 0) || !(p.ko_theta >= 0)) return -1;
+    const int l_low = std::max(std::abs(p.s), std::abs(p.m));
+    if (p.theta_filter < 0 || (p.theta_filter > 0 && (p.theta_filter <= l_low || p.theta_filter - l_low > p.n_theta)))
+      return -1;
     nrow = p.row_hi - p.row_lo + 1;
     nth = p.n_theta;
     M = T(p.M);
@@ -292,6 +299,7 @@ struct Solver {
       un[c].assign((size_t)nrow * nth, T(0.0));
       uh[c].assign((size_t)(nrow - 1) * nth, T(0.0));
     }
+    if (p.theta_filter > 0) setup_filter();
     return 0;
   }
 
@@ -396,6 +404,84 @@ struct Solver {
     }
   }
 
+  // Theta filter (NOT part of the paper's method; off unless theta_filter > 0). A multipole l
+  // oscillates near the photon sphere at about (l + 1/2) / (3 sqrt(3) M); once that exceeds
+  // what the central r* differences can carry (their frequencies stop at 1/dr*), the
+  // multipole is trapped there by the grid, and the lower-order term c Phi' of the
+  // r^3-scaled system makes it grow. The filter removes those multipoles once per outer step,
+  // after dissipate(): every row of every component becomes its orthogonal projection onto
+  //   span { y_l(theta_j) : max(|s|, |m|) <= l < theta_filter },
+  // y_l the (unnormalised) spin-weighted harmonic of the problem's s and m, in the discrete
+  // inner product <f, g> = sum_j w_j f_j g_j with Fejer's first-rule weights w_j. Written as
+  // its definition: the coefficients solve the Gram system G c = b, G_ab = <y_a, y_b>,
+  // b_a = <y_a, f>, and the row becomes sum_a c_a y_a.
+  int n_keep = 0;
+  std::vector<T> fy;     // [n_keep][nth]: y_l(theta_j), l = l_low .. theta_filter - 1
+  std::vector<T> fw;     // [nth]: Fejer weights
+  std::vector<T> fginv;  // [n_keep][n_keep]: G^-1
+
+  void setup_filter() {
+    const int l_low = std::max(std::abs(p.s), std::abs(p.m));
+    n_keep = p.theta_filter - l_low;
+    fy.assign((size_t)n_keep * nth, T(0.0));
+    fw.assign(nth, T(0.0));
+    for (int j = 0; j < nth; ++j) fw[j] = fejer_weight<T>(nth, j);
+    for (int q = 0; q < n_keep; ++q)
+      for (int j = 0; j < nth; ++j) fy[(size_t)q * nth + j] = spin_profile(l_low + q, th[j]);
+    // G is symmetric positive definite: Gauss-Jordan elimination without pivoting, on [G | I].
+    const int n = n_keep;
+    std::vector<T> aug((size_t)n * 2 * n, T(0.0));
+    for (int q = 0; q < n; ++q) {
+      for (int r = 0; r < n; ++r) {
+        T g = T(0.0);
+        for (int j = 0; j < nth; ++j) g = g + fw[j] * fy[(size_t)q * nth + j] * fy[(size_t)r * nth + j];
+        aug[(size_t)q * 2 * n + r] = g;
+      }
+      aug[(size_t)q * 2 * n + n + q] = T(1.0);
+    }
+    for (int c = 0; c < n; ++c) {
+      const T piv = aug[(size_t)c * 2 * n + c];
+      for (int r = 0; r < 2 * n; ++r) aug[(size_t)c * 2 * n + r] = aug[(size_t)c * 2 * n + r] / piv;
+      for (int q = 0; q < n; ++q) {
+        if (q == c) continue;
+        const T f = aug[(size_t)q * 2 * n + c];
+        for (int r = 0; r < 2 * n; ++r)
+          aug[(size_t)q * 2 * n + r] = aug[(size_t)q * 2 * n + r] - f * aug[(size_t)c * 2 * n + r];
+      }
+    }
+    fginv.assign((size_t)n * n, T(0.0));
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r) fginv[(size_t)q * n + r] = aug[(size_t)q * 2 * n + n + r];
+  }
+
+  // Projects every interior row (not the r* boundary rows, nor the frozen window edges).
+  void filter_rows() {
+    const int n = n_keep;
+    for (int c = 0; c < 4; ++c) {
+#pragma omp parallel for schedule(static)
+      for (int i = 1; i < nrow - 1; ++i) {
+        if (is_boundary_row(i)) continue;
+        T* row = u[c].data() + (size_t)i * nth;
+        std::vector<T> b(n, T(0.0)), coef(n, T(0.0));
+        for (int q = 0; q < n; ++q)
+          for (int j = 0; j < nth; ++j) b[q] = b[q] + fw[j] * fy[(size_t)q * nth + j] * row[j];
+        for (int q = 0; q < n; ++q)
+          for (int r = 0; r < n; ++r) coef[q] = coef[q] + fginv[(size_t)q * n + r] * b[r];
+        for (int j = 0; j < nth; ++j) {
+          T v = T(0.0);
+          for (int q = 0; q < n; ++q) v = v + coef[q] * fy[(size_t)q * nth + j];
+          row[j] = v;
+        }
+      }
+    }
+  }
+
+  // The operators applied once per outer step, before its first iteration.
+  void outer_step_ops() {
+    if (p.ko_sigma > 0 || p.ko_theta > 0) dissipate();
+    if (p.theta_filter > 0) filter_rows();
+  }
+
   // Forcing at time t: (Re, Im) of e^{-i omega t} F^ is (c F^_R + s F^_I, c F^_I - s F^_R).
   void forcing_phase(const T& t, T& c, T& sn) const {
     c = cos_(f_omega * t);
@@ -404,7 +490,8 @@ struct Solver {
 
   // One Lax-Wendroff iteration with step dts (Eqs. lw1, lw2), then the r* boundary rows.
   void substep() {
-    if ((p.ko_sigma > 0 || p.ko_theta > 0) && substeps_done % p.substeps == 0) dissipate();
+    if ((p.ko_sigma > 0 || p.ko_theta > 0 || p.theta_filter > 0) && substeps_done % p.substeps == 0)
+      outer_step_ops();
     const T half = T(0.5);
     const T hdt = dts * half;
     // forcing phases at t_n (half step) and t_n + dts/2 (full step)
@@ -975,6 +1062,16 @@ int oracle_set_forcing(void* hv, double omega, const double* fn, const double* f
 
 // Overwrites one theta row of the state (window-relative row index) from in [4][words][nth]:
 // used to place halo rows received from a neighbouring slab.
+// Applies the theta filter to the current state (as at the start of an outer step); -1 if the
+// problem has no filter.
+int oracle_filter_rows(void* hv) {
+  return dispatch((Handle*)hv, [&](auto& S) {
+    if (S.p.theta_filter <= 0) return -1;
+    S.filter_rows();
+    return 0;
+  });
+}
+
 int oracle_set_row(void* hv, int row, const double* in, int words) {
   Handle* h = (Handle*)hv;
   return dispatch(h, [&](auto& S) {

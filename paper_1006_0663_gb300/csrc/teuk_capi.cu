@@ -79,7 +79,7 @@ void drop_graph(teuk_s* h);
 void free_all(teuk_s* h) {
   double** bufs[] = {&h->u, &h->uh, &h->cn_raw, &h->ch_raw, &h->cn, &h->ch, &h->wts, &h->lfac, &h->sin_th,
                      &h->cos_th, &h->x_node, &h->x_half, &h->rs_node, &h->prof, &h->ring, &h->u_ko,
-                     &h->eps_th};
+                     &h->eps_th, &h->filt};
   for (double** b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -336,7 +336,7 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   if (!(M > 0) || !(std::fabs(a) < M) || !std::isfinite(M) || !std::isfinite(a)) return TEUK_ERR_INVALID_ARG;
   if (s < -2 || s > 2) return TEUK_ERR_INVALID_ARG;
   const teuk_grid& g = *grid;
-  if (g.n_r < 3 || g.n_theta < 6 || g.n_theta > 1024 || g.substeps < 1 || g.reserved != 0)
+  if (g.n_r < 3 || g.n_theta < 6 || g.n_theta > 1024 || g.substeps < 1 || g.reserved != 0 || g.reserved2 != 0)
     return TEUK_ERR_INVALID_ARG;
   if (!(g.rstar_max > g.rstar_min) || !std::isfinite(g.rstar_min) || !std::isfinite(g.rstar_max))
     return TEUK_ERR_INVALID_ARG;
@@ -345,7 +345,9 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   if (order != 10 && order != 2) return TEUK_ERR_INVALID_ARG;
   if (g.parity != 0 && g.parity != 1 && g.parity != -1 && g.parity != 2) return TEUK_ERR_INVALID_ARG;
   if (!(g.ko_sigma >= 0) || !(g.ko_theta >= 0) || g.ko_sigma > 4.0 || g.ko_theta > 4.0) return TEUK_ERR_INVALID_ARG;
-  if (own_hi >= 0 && (g.ko_sigma > 0 || g.ko_theta > 0)) return TEUK_ERR_INVALID_ARG;  // slabs: no dissipation
+  if (g.theta_filter < 0) return TEUK_ERR_INVALID_ARG;
+  // slabs: no dissipation and no filter
+  if (own_hi >= 0 && (g.ko_sigma > 0 || g.ko_theta > 0 || g.theta_filter > 0)) return TEUK_ERR_INVALID_ARG;
   if ((int64_t)g.n_r * g.n_theta > (int64_t)1 << 31) return TEUK_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TEUK_ERR_NO_DEVICE;
@@ -405,6 +407,7 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   if (rc != TEUK_OK) return fail(rc);
   if (g.ko_sigma > 0 && (rc = teuk_set_dissipation(h, g.ko_sigma)) != TEUK_OK) return fail(rc);
   if (g.ko_theta > 0 && (rc = teuk_set_theta_dissipation(h, g.ko_theta)) != TEUK_OK) return fail(rc);
+  if (g.theta_filter > 0 && (rc = teuk_set_theta_filter(h, g.theta_filter)) != TEUK_OK) return fail(rc);
   *out = h;
   return TEUK_OK;
 }
@@ -627,6 +630,34 @@ int teuk_set_theta_dissipation(teuk_t h, double sigma) {
 
 double teuk_theta_dissipation(teuk_t h) { return h ? h->ko_theta : -1.0; }
 
+int teuk_set_theta_filter(teuk_t h, int l_cut) {
+  if (!h) return TEUK_ERR_INVALID_ARG;
+  const int l_low = std::max(std::abs(h->s), std::abs(h->m));
+  if (l_cut != 0 && (l_cut <= l_low || l_cut > 41 || 2 * (l_cut - 1) >= h->n_th))
+    return invalid(h, "theta filter: need l_cut = 0 or max(|s|, |m|) < l_cut <= 41 with 2 (l_cut - 1) < n_theta");
+  if (h->is_slab() && l_cut > 0) return invalid(h, "theta filter: not on a slab");
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  if (l_cut == 0) {
+    h->filter_lcut = 0;
+    return TEUK_OK;
+  }
+  int rc;
+  switch (h->W) {
+    case 1: rc = teuk::filter_tables_w1(h, l_cut); break;
+    case 2: rc = teuk::filter_tables_w2(h, l_cut); break;
+    default: rc = teuk::filter_tables_w4(h, l_cut); break;
+  }
+  if (rc != TEUK_OK) {
+    h->filter_lcut = 0;  // the tables of the previous cut are gone
+    return rc;
+  }
+  h->filter_lcut = l_cut;
+  return TEUK_OK;
+}
+
+int teuk_theta_filter(teuk_t h) { return h ? h->filter_lcut : -1; }
+
 int teuk_step(teuk_t h, int64_t n) {
   if (!h || n < 0) return TEUK_ERR_INVALID_ARG;
   if (h->is_slab()) return invalid(h, "slab: advance with teuk_substep(h, 1) and a halo exchange per iteration");
@@ -646,7 +677,7 @@ int teuk_step(teuk_t h, int64_t n) {
     for (int64_t t = 0; t < n; ++t) TEUK_CUDA(h, cudaGraphLaunch(h->graph_exec, h->stream));
     if (!h->graph_events.empty()) h->graph_events_fresh = true;
     h->substeps_done += n * h->k;
-    h->launches += n * (2 * h->k + (h->dissipating() ? 1 : 0));
+    h->launches += n * (2 * h->k + h->outer_op_launches());
     if (record) h->n_recorded += n;
     return TEUK_OK;
   }

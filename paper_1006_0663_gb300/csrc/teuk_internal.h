@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -84,7 +86,13 @@ struct teuk_s {
   double ko_theta = 0;                 // theta dissipation strength (0: off, the paper's scheme)
   double* eps_th = nullptr;            // [W][n_r]: ko_theta c_th(i) dt / (4096 dtheta) per row
   double* u_ko = nullptr;              // output of the dissipation step (state layout)
-  bool dissipating() const { return ko_sigma > 0 || ko_theta > 0; }
+  int filter_lcut = 0;                 // theta filter: removes multipoles l >= filter_lcut (0: off)
+  double* filt = nullptr;              // its tables [2][n_ell][W][n_th] (analysis, synthesis)
+  int filter_n_ell() const { return filter_lcut - std::max(std::abs(s), std::abs(m)); }
+  // an operator runs once at the start of every outer step (dissipation or theta filter)
+  bool dissipating() const { return ko_sigma > 0 || ko_theta > 0 || filter_lcut > 0; }
+  // kernels those operators launch per outer step
+  int outer_op_launches() const { return (ko_sigma > 0 || ko_theta > 0 ? 1 : 0) + (filter_lcut > 0 ? 1 : 0); }
   int engine = 0;                      // double-double arithmetic: 0 FP64 error-free transforms,
                                        // 1 integer engine (ix.cuh)
   uint4* ix_m = nullptr;               // integer-engine tables: node coefficients, half-node
@@ -142,6 +150,11 @@ int dissipation_w4(teuk_s* h, double sigma);
 int dissipate_w1(teuk_s* h);
 int dissipate_w2(teuk_s* h);
 int dissipate_w4(teuk_s* h);
+int filter_tables_w1(teuk_s* h, int l_cut);
+int filter_tables_w2(teuk_s* h, int l_cut);
+int filter_tables_w4(teuk_s* h, int l_cut);
+// normalised sY_lm(theta_j) as quad-double words [n_ell][4][n_th] (times 2 pi w_j if weighted)
+std::vector<double> harmonics_w4(int s, int m, int n_th, int ell_min, int ell_max, bool weighted);
 int theta_dissipation_w1(teuk_s* h, double sigma, double* max_rate);
 int theta_dissipation_w2(teuk_s* h, double sigma, double* max_rate);
 int theta_dissipation_w4(teuk_s* h, double sigma, double* max_rate);

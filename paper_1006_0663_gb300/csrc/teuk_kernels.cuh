@@ -450,6 +450,57 @@ __global__ void dissipate_kernel(DissArgs a) {
   st_r(a.out + (size_t)c * W * ws + (size_t)i * p + j, ws, v);
 }
 
+// ---- theta filter (not part of the paper's method; off unless enabled) ----------------------
+// A multipole l oscillates near the photon sphere at about (l + 1/2) / (3 sqrt(3) M). Where
+// that exceeds what the central r* differences carry (their frequencies stop at 1/dr*), the
+// grid traps the multipole there and the first-order term c Phi' of the r^3-scaled system
+// makes it grow. Once per outer step, after the dissipation kernel, every interior row of
+// every component is replaced by its projection onto the normalised harmonics sY_lm,
+// max(|s|, |m|) <= l < l_cut:
+//   f_j <- sum_l sY_l(theta_j) c_l,   c_l = sum_j' 2 pi w_j' sY_l(theta_j') f_j',
+// w_j Fejer's first-rule weights on the cell centres. The rule integrates polynomials in
+// cos(theta) of degree < n_theta exactly, and sY_l sY_l' of one s and m is such a polynomial
+// of degree l + l', so with 2 (l_cut - 1) < n_theta the harmonics are exactly orthonormal in
+// this sum and the map is an orthogonal projection.
+struct FilterArgs {
+  Geom g;
+  const double* u;    // [4][W][n_r][pitch]
+  double* out;        // same layout; may be u (each block reads its row before writing)
+  const double* tab;  // [2][n_ell][W][n_th]: 2 pi w_j sY_l(theta_j), then sY_l(theta_j)
+  int n_ell;
+};
+
+// One block per (interior row, component): the row to shared memory, the n_ell coefficients
+// as dot products in the target precision, then the synthesis.
+template <int W>
+__global__ void filter_kernel(FilterArgs a) {
+  using R = typename RT<W>::T;
+  step_dependency();
+  extern __shared__ double fsm[];
+  const int i = blockIdx.x + 1, c = blockIdx.y;
+  const int n_th = a.g.n_th, n_ell = a.n_ell;
+  const size_t ws = (size_t)a.g.n_r * a.g.pitch;
+  const size_t off = (size_t)c * W * ws + (size_t)i * a.g.pitch;
+  double* row = fsm;                      // [W][n_th]
+  double* coef = fsm + (size_t)W * n_th;  // [W][n_ell]
+  for (int j = threadIdx.x; j < n_th; j += blockDim.x)
+    for (int k = 0; k < W; ++k) row[(size_t)k * n_th + j] = a.u[off + (size_t)k * ws + j];
+  __syncthreads();
+  const double* ta = a.tab;
+  const double* ts = a.tab + (size_t)n_ell * W * n_th;
+  for (int l = threadIdx.x; l < n_ell; l += blockDim.x) {
+    Acc<R> acc(mw::r_from<R>(0.0));
+    for (int j = 0; j < n_th; ++j) acc.mac(ld_r<R>(ta + (size_t)l * W * n_th + j, n_th), ld_s<R>(row + j, n_th));
+    st_r(coef + l, n_ell, acc.get());
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+    Acc<R> acc(mw::r_from<R>(0.0));
+    for (int l = 0; l < n_ell; ++l) acc.mac(ld_r<R>(ts + (size_t)l * W * n_th + j, n_th), ld_s<R>(coef + l, n_ell));
+    st_r(a.out + off + j, ws, acc.get());
+  }
+}
+
 // eps_th(i) = factor * sqrt(max_j g(i, j)), g = Delta/Sigma^2 (plane 5 of the raw node
 // coefficients), factor = sigma_th dt / (4096 dtheta); one block per row. The largest g of a
 // row is found by comparing the word expansions (normalised, so the words order the values).

@@ -55,7 +55,7 @@ extern "C" int teuk_substep_noalloc(teuk_t h, const double* u_in, double* u_out,
     return TEUK_ERR_INVALID_ARG;
   }
   if (h->dissipating()) {
-    h->last_error = "teuk_substep_noalloc: the dissipation step needs the handle's own buffers";
+    h->last_error = "teuk_substep_noalloc: the outer-step dissipation or theta filter needs the handle's own buffers";
     return TEUK_ERR_INVALID_ARG;
   }
   const size_t needed = (size_t)4 * h->W * (size_t)(h->n_r - 1) * h->pitch;

@@ -209,9 +209,10 @@ int pulse_impl(teuk_s* h, double center, double width, double ar, double ai, int
 //   w_j = (2/N) [1 - 2 sum_{k=1}^{floor(N/2)} cos(2 k theta_j) / (4 k^2 - 1)],
 // exact for polynomials of degree < N (the integrand of a regular field is a polynomial in x
 // times its smooth amplitude). The cosines are cos(pi q / (2N)) with the integer
-// q = 2k(2j+1) reduced exactly to the first quadrant.
-int project_impl(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first) {
-  const int n_th = h->n_th, s = h->s, m = h->m, n_ell = ell_max - ell_min + 1;
+// q = 2k(2j+1) reduced exactly to the first quadrant. harmonic_table gives sY_lm(theta_j) as
+// words [n_ell][W][n_th], times 2 pi w_j when `weighted` (the projection's table).
+std::vector<double> harmonic_table(int s, int m, int n_th, int ell_min, int ell_max, bool weighted) {
+  const int n_ell = ell_max - ell_min + 1;
   const R pi = r_pi<R>();
   // quarter-wave table cos(pi q / (2N)), q = 0 .. N
   std::vector<R> qc(n_th + 1);
@@ -252,10 +253,17 @@ int project_impl(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, in
     for (int j = 0; j < n_th; ++j) {
       R sh, ch;
       half_angle(pi, n_th, j, sh, ch);
-      store_plane(row, n_th, j, r_mul(wq[j], r_mul(norm, goldberg_sum(l, s, m, sh, ch))));
+      const R y = r_mul(norm, goldberg_sum(l, s, m, sh, ch));
+      store_plane(row, n_th, j, weighted ? r_mul(wq[j], y) : y);
     }
     std::memcpy(table.data() + (size_t)(l - ell_min) * W * n_th, row.data(), row.size() * sizeof(double));
   }
+  return table;
+}
+
+int project_impl(teuk_s* h, int ell_min, int ell_max, double* out, int64_t n, int64_t first) {
+  const int n_th = h->n_th, n_ell = ell_max - ell_min + 1;
+  const std::vector<double> table = harmonic_table(h->s, h->m, n_th, ell_min, ell_max, true);
   double* d_table = nullptr;
   double* d_out = nullptr;
   const size_t n_out = (size_t)n * n_ell * 2 * W;
@@ -321,20 +329,67 @@ int theta_dissipation_impl(teuk_s* h, double sigma, double* max_rate) {
   return TEUK_OK;
 }
 
-// One dissipation step of the state (kernel into u_ko, copied back).
+// Dynamic shared memory of filter_kernel: one row of W words plus its coefficients.
+size_t filter_smem(const teuk_s* h) {
+  return (size_t)W * (h->n_th + h->filter_n_ell()) * sizeof(double);
+}
+
+// Tables of the theta filter: [2][n_ell][W][n_th], first 2 pi w_j sY_lm(theta_j) (analysis),
+// then sY_lm(theta_j) (synthesis), l = max(|s|, |m|) .. l_cut - 1. The harmonics come from
+// the quad-double evaluation and keep their leading W words: the Goldberg sum alternates,
+// and at l ~ 20 its terms are ~1e5 times its value, which a W-word evaluation would leave in
+// the result.
+int filter_tables_impl(teuk_s* h, int l_cut) {
+  const int l_low = std::max(std::abs(h->s), std::abs(h->m)), n_ell = l_cut - l_low, n_th = h->n_th;
+  std::vector<double> tab((size_t)2 * n_ell * W * n_th);
+  for (int part = 0; part < 2; ++part) {
+    const std::vector<double> q = harmonics_w4(h->s, h->m, n_th, l_low, l_cut - 1, part == 0);
+    double* dst = tab.data() + (size_t)part * n_ell * W * n_th;
+    for (int l = 0; l < n_ell; ++l)
+      for (int k = 0; k < W; ++k)
+        std::memcpy(dst + ((size_t)l * W + k) * n_th, q.data() + ((size_t)l * 4 + k) * n_th, n_th * sizeof(double));
+  }
+  if (h->filt) cudaFree(h->filt);
+  h->filt = nullptr;
+  TEUK_CUDA(h, cudaMalloc(&h->filt, tab.size() * sizeof(double)));
+  TEUK_CUDA(h, cudaMemcpy(h->filt, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const size_t smem = (size_t)W * (n_th + n_ell) * sizeof(double);
+  if (smem > 48 * 1024)
+    TEUK_CUDA(h, cudaFuncSetAttribute(filter_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return TEUK_OK;
+}
+
+// The operators of an outer step's start: the dissipation kernel into u_ko, then either the
+// theta filter from u_ko back into the state or a copy back; the filter alone works in place.
 int dissipate_impl(teuk_s* h) {
-  DissArgs da{};
-  da.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
-  da.u = h->u;
-  da.out = h->u_ko;
-  std::memcpy(da.eps, h->ko_eps_w, sizeof(da.eps));
-  da.do_r = h->ko_sigma > 0;
-  da.eps_th = h->ko_theta > 0 ? h->eps_th : nullptr;
-  TEUK_CUDA(h, launch_dep(dissipate_kernel<W>, dim3((h->n_th + 63) / 64, h->n_r, 4), dim3(64), 0, h->stream, da));
-  TEUK_CUDA(h, cudaGetLastError());
-  TEUK_CUDA(h, cudaMemcpyAsync(h->u, h->u_ko, (size_t)4 * W * h->n_r * h->pitch * sizeof(double),
-                               cudaMemcpyDeviceToDevice, h->stream));
-  h->launches += 1;
+  const bool ko = h->ko_sigma > 0 || h->ko_theta > 0;
+  if (ko) {
+    DissArgs da{};
+    da.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
+    da.u = h->u;
+    da.out = h->u_ko;
+    std::memcpy(da.eps, h->ko_eps_w, sizeof(da.eps));
+    da.do_r = h->ko_sigma > 0;
+    da.eps_th = h->ko_theta > 0 ? h->eps_th : nullptr;
+    TEUK_CUDA(h, launch_dep(dissipate_kernel<W>, dim3((h->n_th + 63) / 64, h->n_r, 4), dim3(64), 0, h->stream,
+                            da));
+    TEUK_CUDA(h, cudaGetLastError());
+    h->launches += 1;
+  }
+  if (h->filter_lcut > 0) {
+    FilterArgs fa{};
+    fa.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
+    fa.u = ko ? h->u_ko : h->u;
+    fa.out = h->u;
+    fa.tab = h->filt;
+    fa.n_ell = h->filter_n_ell();
+    TEUK_CUDA(h, launch_dep(filter_kernel<W>, dim3(h->n_r - 2, 4), dim3(128), filter_smem(h), h->stream, fa));
+    TEUK_CUDA(h, cudaGetLastError());
+    h->launches += 1;
+  } else if (ko) {
+    TEUK_CUDA(h, cudaMemcpyAsync(h->u, h->u_ko, (size_t)4 * W * h->n_r * h->pitch * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, h->stream));
+  }
   return TEUK_OK;
 }
 
@@ -753,6 +808,10 @@ int TEUK_SUFFIX(persist_w)(teuk_s* h, int64_t n_outer, long long ring_base) {
 int TEUK_SUFFIX(engine_w)(teuk_s* h, int engine) { return engine_impl(h, engine); }
 int TEUK_SUFFIX(dissipation_w)(teuk_s* h, double sigma) { return dissipation_impl(h, sigma); }
 int TEUK_SUFFIX(dissipate_w)(teuk_s* h) { return dissipate_impl(h); }
+int TEUK_SUFFIX(filter_tables_w)(teuk_s* h, int l_cut) { return filter_tables_impl(h, l_cut); }
+std::vector<double> TEUK_SUFFIX(harmonics_w)(int s, int m, int n_th, int ell_min, int ell_max, bool weighted) {
+  return harmonic_table(s, m, n_th, ell_min, ell_max, weighted);
+}
 int TEUK_SUFFIX(theta_dissipation_w)(teuk_s* h, double sigma, double* max_rate) {
   return theta_dissipation_impl(h, sigma, max_rate);
 }

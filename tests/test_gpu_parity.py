@@ -4,6 +4,8 @@ Tolerances (max-norm relative error over all compared points and the four compon
 FP64 1e-12, double-double 1e-26, quad-double 1e-55. Grids span several thread blocks and a
 ragged theta tail (n_theta not a multiple of the warp width or of the 16-double pitch).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -989,3 +991,147 @@ def test_grid_fields_parity_rule_and_dissipation(W):
     np.testing.assert_array_equal(a.get_state(), b.get_state())
     with pytest.raises(teuk.TeukError):
         teuk.Teuk(precision=W, ko_sigma=-1.0, **p)
+
+
+def _rich_state(p, W, seed):
+    """Random theta content (all multipoles the grid holds) under a Gaussian in r*, zero
+    boundary rows: the filter then has something to remove."""
+    rng = np.random.default_rng(seed)
+    rs = np.linspace(p["rstar_min"], p["rstar_max"], p["n_r"])
+    env = np.exp(-((rs - 5.0) / 6.0) ** 2)
+    u = np.zeros((4, W, p["n_r"], p["n_theta"]))
+    u[:, 0] = rng.standard_normal((4, p["n_r"], p["n_theta"])) * env[None, :, None]
+    u[:, 0, 0] = 0.0
+    u[:, 0, -1] = 0.0
+    return u
+
+
+@pytest.mark.parametrize("W,engine", [(1, 0), (2, 0), (2, 1), (4, 0), (4, 1)])
+@pytest.mark.parametrize("s,m,ko", [(0, 0, 0.0), (-1, 2, 1.0), (-2, 2, 1.0)])
+def test_theta_filter_parity(oracle_mod, W, engine, s, m, ko):
+    """theta filter (not part of the paper's scheme), alone and after the r* dissipation,
+    against the 256-bit oracle (which solves the Gram system of its own profiles instead of
+    using orthonormal tables): random theta content, 3 outer steps and 2 iterations."""
+    p = small(s=s, m=m, a=0.9, n_r=45, n_theta=24, substeps=3)
+    l_cut = max(abs(s), abs(m)) + 5
+    g = teuk.Teuk(precision=W, **p)
+    if engine:
+        g.set_engine(engine)
+    g.set_dissipation(ko)
+    g.set_theta_filter(l_cut)
+    assert g.theta_filter == l_cut
+    o = oracle_mod.Oracle(M=p["M"], a=p["a"], s=s, m=m, rstar_min=p["rstar_min"], rstar_max=p["rstar_max"],
+                          n_r=p["n_r"], n_theta=p["n_theta"], dt=p["dt"], substeps=p["substeps"],
+                          theta_order=p["theta_order"], parity=workloads.parity_of(m, s), bits=256,
+                          ko_sigma=ko, theta_filter=l_cut)
+    u0 = _rich_state(p, W, 40 + 3 * abs(s) + m)
+    g.set_state(u0)
+    o.set_state(u0[:, :1])
+    g.step(3)
+    g.substep(2)
+    g.sync()
+    o.step(3 * 3 + 2)
+    err, umax = o.max_rel_err(g.get_state())
+    assert umax > 0.05
+    assert err < TOL[W], err
+    # the filter removed the high multipoles: the state differs from the unfiltered run
+    g2 = teuk.Teuk(precision=W, **p)
+    if engine:
+        g2.set_engine(engine)
+    g2.set_dissipation(ko)
+    g2.set_state(u0)
+    g2.step(3)
+    g2.substep(2)
+    assert np.abs(g2.get_state()[:, 0] - g.get_state()[:, 0]).max() > 1e-3 * umax
+
+
+@pytest.mark.parametrize("W", [1, 4])
+def test_theta_filter_rules(W):
+    """Grid field = setter (bit for bit); refused values keep the filter in use; l_cut = 0
+    switches it off (bit for bit the unfiltered run); slabs, batches and the no-allocation
+    entry point refuse filtered handles."""
+    p = small(s=-1, m=2, n_r=41, n_theta=24, substeps=3)
+    a = teuk.Teuk(precision=W, theta_filter=6, **p)
+    b = teuk.Teuk(precision=W, **p)
+    b.set_theta_filter(6)
+    assert a.theta_filter == 6 and b.theta_filter == 6
+    u0 = _rich_state(p, W, 7)
+    for h in (a, b):
+        h.set_state(u0)
+        h.step(2)
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
+    for bad in (-1, 2, 13, 42):  # below max(|s|, |m|) + 1, 2 (l_cut - 1) >= n_theta, > 41
+        with pytest.raises(teuk.TeukError):
+            b.set_theta_filter(bad)
+        assert b.theta_filter == 6
+    with pytest.raises(teuk.TeukError):
+        teuk.Teuk(precision=W, theta_filter=2, **p)
+    with pytest.raises(teuk.TeukError):
+        teuk.Teuk(precision=W, own_rows=(0, 20), theta_filter=6, **p)
+    c, d = teuk.Teuk(precision=W, **p), teuk.Teuk(precision=W, **p)
+    c.set_theta_filter(6)
+    c.set_theta_filter(0)
+    assert c.theta_filter == 0
+    for h in (c, d):
+        h.set_state(u0)
+        h.step(2)
+    np.testing.assert_array_equal(c.get_state(), d.get_state())
+    with pytest.raises(teuk.TeukError):
+        teuk.Batch([a, b])
+    torch = pytest.importorskip("torch")
+    pitch = (p["n_theta"] + 15) // 16 * 16
+    buf = torch.zeros((4, W, p["n_r"], pitch), dtype=torch.float64, device="cuda")
+    rc = teuk.lib().teuk_substep_noalloc(a._h, ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(buf.data_ptr()), 1)
+    assert rc == teuk.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_c3_outer_step_operators_full_size(oracle_mod, engine):
+    """c3 at full size in quad-double with its own outer-step operators (r* dissipation
+    sigma = 2 and theta filter l_cut = 7, neither in the paper's scheme), tuned launch shape,
+    2 k + 3 iterations (three dissipation and filter steps) against a 256-bit oracle window:
+    each iteration reaches one row and each dissipation step two."""
+    prob = workloads.CONFIGS["c3"]
+    assert prob.theta_filter == 7 and prob.ko_sigma == 2.0
+    g = teuk.Teuk.from_problem(prob, precision=4)
+    if engine:
+        g.set_engine(engine)
+    g.tune()
+    assert g.theta_filter == 7
+    nsub = 2 * prob.substeps + 3
+    reach = nsub + 2 * 3
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    g.substep(nsub)
+    g.sync()
+    full = g.get_state()
+    ic = int(round((prob.center - prob.rstar_min) / prob.dr))
+    lo, hi = ic - 12, ic + 12
+    wlo, whi = lo - reach - 1, hi + reach + 1
+    o = oracle_mod.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
+                          rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
+                          substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=256,
+                          ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta, theta_filter=prob.theta_filter)
+    o.pulse(prob.center, prob.width, ar, ai, prob.ell)
+    o.step(nsub)
+    err, umax = o.max_rel_err(np.ascontiguousarray(full[:, :, wlo:whi + 1]), lo - wlo, hi - wlo)
+    assert umax > 0.05
+    assert err < TOL[4], err
+
+
+def test_c3_bounded_over_its_stated_length():
+    """c3 (a = 0.99, s = m = 0, 1024 x 64, 40,000 outer steps of k = 20) in FP64 with its
+    outer-step operators stays bounded: the largest |u| of the last 10,000 steps is below that
+    of the first 10,000 (the r^-3 amplification of the ingoing pulse near the hole), and the
+    run ends without a non-finite value. Without the theta filter it overflows."""
+    prob = workloads.CONFIGS["c3"]
+    g = teuk.Teuk.from_problem(prob, precision=1)
+    ar, ai = prob.amps
+    g.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+    peaks = []
+    for _ in range(8):
+        g.step(prob.steps // 8)
+        g.sync()
+        peaks.append(float(np.abs(g.get_state()).max()))
+    assert all(np.isfinite(peaks))
+    assert max(peaks[6:]) < max(peaks[:2]), peaks
