@@ -24,7 +24,10 @@
 // conjugation symmetry, a = 0 separability and an independent radial solver, and a forced
 // manufactured solution at a != 0: a smooth complex field whose forcing is derived from
 // Eq. 1 itself, outside this file, converges at 2nd order, which pins how source()
-// combines the complex coefficients).
+// combines the complex coefficients). The optional dissipation and theta filter (not part
+// of the paper's method) are pinned too: the dissipation through its linearity and its
+// action on polynomials and the sawtooth, the filter against Legendre series and
+// spin-weighted harmonics.
 
 #include <algorithm>
 #include <cmath>
