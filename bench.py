@@ -227,7 +227,8 @@ def stated_error(prob, words, teuk, nsub=12, engine=0):
                       rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                       substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=bits,
                       ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta,
-                      theta_filter=prob.theta_filter)
+                      theta_filter=prob.theta_filter,
+                      theta_filter_period=prob.theta_filter_period)
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     o.step(nsub)
     err, _ = o.max_rel_err(full[:, :, wlo:whi + 1].copy(), lo - wlo, hi - wlo)
@@ -484,7 +485,8 @@ def cpu_baseline(prob, words, seconds_target=15.0):
                       rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                       substeps=prob.substeps, parity=prob.parity, row_lo=lo,
                       row_hi=min(prob.n_r - 1, lo + rows - 1), bits=bits, ko_sigma=prob.ko_sigma,
-                      ko_theta=prob.ko_theta, theta_filter=prob.theta_filter)
+                      ko_theta=prob.ko_theta, theta_filter=prob.theta_filter,
+                      theta_filter_period=prob.theta_filter_period)
     ar, ai = prob.amps
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     done, t0 = 0, time.perf_counter()
@@ -612,7 +614,8 @@ def digits_table():
                           rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                           substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=256,
                           ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta,
-                          theta_filter=prob.theta_filter)
+                          theta_filter=prob.theta_filter,
+                          theta_filter_period=prob.theta_filter_period)
         o.pulse(prob.center, prob.width, ar, ai, prob.ell)
         o.step(nsub)
         states, cost = {}, {}

@@ -70,7 +70,7 @@ typedef struct {
                            0 = off; both are applied at creation with the setters' rules */
   int32_t theta_filter; /* theta filter (teuk_set_theta_filter), not in the paper: 0 = off,
                            else l_cut; applied at creation with the setter's rules */
-  int32_t reserved2;    /* must be 0 */
+  int32_t theta_filter_period; /* its period in outer steps (0 = 1) */
 } teuk_grid;
 
 typedef struct teuk_s* teuk_t;
@@ -180,9 +180,9 @@ double teuk_theta_dissipation(teuk_t h);
  * the iteration carry (they stop at 1/dr*), the grid traps the multipole there and the
  * first-order term c Phi_{r*} of the r^3-scaled system makes it grow (rates ~0.1/M on
  * r* in [-100, 400] with 1024 points from l = 7 at a = 0.99); neither substeps nor the
- * dissipation terms remove that. With l_cut > 0, every outer step begins (after the
- * dissipation kernel, when there is one) by replacing every interior row of every component
- * with its projection onto the harmonics of the problem's s and m below l_cut:
+ * dissipation terms remove that. With l_cut > 0, every period-th outer step begins (after
+ * the dissipation kernel, when there is one) by replacing every interior row of every
+ * component with its projection onto the harmonics of the problem's s and m below l_cut:
  *   f_j <- sum_l sY_lm(theta_j) c_l,  c_l = sum_j' 2 pi w_j' sY_lm(theta_j') f_j',
  *   max(|s|, |m|) <= l < l_cut,
  * sY_lm normalised, w_j Fejer's first-rule weights on the cell centres; with
@@ -190,10 +190,18 @@ double teuk_theta_dissipation(teuk_t h);
  * orthogonal projection. The tables are computed once, in quad-double, and kept in the run's
  * words. Rules: l_cut = 0, or max(|s|, |m|) < l_cut <= 41 and 2 (l_cut - 1) < n_theta, else
  * TEUK_ERR_INVALID_ARG (also on slabs) and the filter in use is kept. Allocates one table of
- * 2 (l_cut - max(|s|, |m|)) n_theta words; handles with it cannot join a batch or use
- * teuk_substep_noalloc. teuk_theta_filter returns the l_cut in use (-1 for a null handle). */
-int teuk_set_theta_filter(teuk_t h, int l_cut);
+ * 2 (l_cut - max(|s|, |m|)) n_theta words and a two-word counter; handles with it cannot
+ * join a batch or use teuk_substep_noalloc. The projection runs at the outer steps whose
+ * index (iterations done / substeps, counted from the iteration count given with the state)
+ * is a multiple of period (0 or 1: every outer step; at most 1024; the kernel runs at every
+ * outer step and keeps the count on the device): the trapped multipoles grow by at most a factor
+ * e^{rate period dt} between projections, so a period of about 1 M keeps them at the level
+ * the projection leaves while the projection's cost (multi-word dot products on the FP64 pipe)
+ * falls by the period. teuk_theta_filter / teuk_theta_filter_period return the values in use
+ * (-1 for a null handle). */
+int teuk_set_theta_filter(teuk_t h, int l_cut, int period);
 int teuk_theta_filter(teuk_t h);
+int teuk_theta_filter_period(teuk_t h);
 
 /* Advances n outer steps (n * substeps Lax-Wendroff iterations), asynchronously on the
  * handle's stream. The observer ring (if any) gets one sample per outer step. */

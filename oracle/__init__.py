@@ -40,6 +40,7 @@ class OracleParams(ctypes.Structure):
         ("ko_sigma", ctypes.c_double),
         ("ko_theta", ctypes.c_double),
         ("theta_filter", ctypes.c_int32),
+        ("theta_filter_period", ctypes.c_int32),
     ]
 
 
@@ -128,7 +129,7 @@ class Oracle:
 
     def __init__(self, *, M, a, s, m, rstar_min, rstar_max, n_r, n_theta, dt, substeps=1,
                  theta_order=10, parity=None, row_lo=0, row_hi=None, bits=256, ko_sigma=0.0,
-                 ko_theta=0.0, theta_filter=0):
+                 ko_theta=0.0, theta_filter=0, theta_filter_period=1):
         if parity is None:
             parity = default_parity(m, s)
         if row_hi is None:
@@ -136,7 +137,8 @@ class Oracle:
         self.params = OracleParams(float(M), float(a), int(s), int(m), float(rstar_min),
                                    float(rstar_max), int(n_r), int(n_theta), float(dt),
                                    int(substeps), int(theta_order), int(parity), int(row_lo),
-                                   int(row_hi), float(ko_sigma), float(ko_theta), int(theta_filter))
+                                   int(row_hi), float(ko_sigma), float(ko_theta), int(theta_filter),
+                                   int(theta_filter_period))
         self.bits = int(bits)
         self._h = lib().oracle_create(ctypes.byref(self.params), self.bits)
         if not self._h:

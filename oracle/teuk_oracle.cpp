@@ -122,6 +122,7 @@ struct oracle_params {
   double ko_sigma;         // r* dissipation strength (not in the paper; 0 = off), see dissipate()
   double ko_theta;         // theta dissipation strength (not in the paper; 0 = off), see dissipate()
   int32_t theta_filter;    // theta filter (not in the paper; 0 = off): remove multipoles l >= this, see filter_rows()
+  int32_t theta_filter_period;  // ... at the outer steps whose index is a multiple of this (0 = 1)
 };
 
 }  // extern "C"
@@ -247,6 +248,7 @@ struct Solver {
     const int l_low = std::max(std::abs(p.s), std::abs(p.m));
     if (p.theta_filter < 0 || (p.theta_filter > 0 && (p.theta_filter <= l_low || p.theta_filter - l_low > p.n_theta)))
       return -1;
+    if (p.theta_filter_period < 0) return -1;
     nrow = p.row_hi - p.row_lo + 1;
     nth = p.n_theta;
     M = T(p.M);
@@ -479,10 +481,12 @@ struct Solver {
     }
   }
 
-  // The operators applied once per outer step, before its first iteration.
+  // The operators applied once per outer step, before its first iteration; the filter at the
+  // outer steps whose index is a multiple of its period.
   void outer_step_ops() {
     if (p.ko_sigma > 0 || p.ko_theta > 0) dissipate();
-    if (p.theta_filter > 0) filter_rows();
+    const int64_t period = p.theta_filter_period > 0 ? p.theta_filter_period : 1;
+    if (p.theta_filter > 0 && (substeps_done / p.substeps) % period == 0) filter_rows();
   }
 
   // Forcing at time t: (Re, Im) of e^{-i omega t} F^ is (c F^_R + s F^_I, c F^_I - s F^_R).

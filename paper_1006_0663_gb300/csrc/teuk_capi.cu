@@ -69,6 +69,15 @@ int iterate(teuk_s* h, bool record, int64_t slot) {
   return TEUK_OK;
 }
 
+// The theta filter's outer-step count restarts from the state's iteration count.
+int sync_filter_counter(teuk_s* h) {
+  if (!h->d_filter_ctr) return TEUK_OK;
+  const long long v[2] = {(long long)(h->substeps_done / h->k), 0};
+  TEUK_CUDA(h, cudaMemcpyAsync(h->d_filter_ctr, v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
 int invalid(teuk_s* h, const char* msg) {
   if (h) h->last_error = msg;
   return TEUK_ERR_INVALID_ARG;
@@ -90,6 +99,8 @@ void free_all(teuk_s* h) {
   h->ix_e = nullptr;
   if (h->status) cudaFree(h->status);
   h->status = nullptr;
+  if (h->d_filter_ctr) cudaFree(h->d_filter_ctr);
+  h->d_filter_ctr = nullptr;
   if (h->pflags) cudaFree(h->pflags);
   h->pflags = nullptr;
   h->pflags_cap = 0;
@@ -336,7 +347,7 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   if (!(M > 0) || !(std::fabs(a) < M) || !std::isfinite(M) || !std::isfinite(a)) return TEUK_ERR_INVALID_ARG;
   if (s < -2 || s > 2) return TEUK_ERR_INVALID_ARG;
   const teuk_grid& g = *grid;
-  if (g.n_r < 3 || g.n_theta < 6 || g.n_theta > 1024 || g.substeps < 1 || g.reserved != 0 || g.reserved2 != 0)
+  if (g.n_r < 3 || g.n_theta < 6 || g.n_theta > 1024 || g.substeps < 1 || g.reserved != 0)
     return TEUK_ERR_INVALID_ARG;
   if (!(g.rstar_max > g.rstar_min) || !std::isfinite(g.rstar_min) || !std::isfinite(g.rstar_max))
     return TEUK_ERR_INVALID_ARG;
@@ -345,7 +356,7 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   if (order != 10 && order != 2) return TEUK_ERR_INVALID_ARG;
   if (g.parity != 0 && g.parity != 1 && g.parity != -1 && g.parity != 2) return TEUK_ERR_INVALID_ARG;
   if (!(g.ko_sigma >= 0) || !(g.ko_theta >= 0) || g.ko_sigma > 4.0 || g.ko_theta > 4.0) return TEUK_ERR_INVALID_ARG;
-  if (g.theta_filter < 0) return TEUK_ERR_INVALID_ARG;
+  if (g.theta_filter < 0 || g.theta_filter_period < 0) return TEUK_ERR_INVALID_ARG;
   // slabs: no dissipation and no filter
   if (own_hi >= 0 && (g.ko_sigma > 0 || g.ko_theta > 0 || g.theta_filter > 0)) return TEUK_ERR_INVALID_ARG;
   if ((int64_t)g.n_r * g.n_theta > (int64_t)1 << 31) return TEUK_ERR_INVALID_ARG;
@@ -407,7 +418,8 @@ int create_impl(teuk_t* out, double M, double a, int s, int m, const teuk_grid* 
   if (rc != TEUK_OK) return fail(rc);
   if (g.ko_sigma > 0 && (rc = teuk_set_dissipation(h, g.ko_sigma)) != TEUK_OK) return fail(rc);
   if (g.ko_theta > 0 && (rc = teuk_set_theta_dissipation(h, g.ko_theta)) != TEUK_OK) return fail(rc);
-  if (g.theta_filter > 0 && (rc = teuk_set_theta_filter(h, g.theta_filter)) != TEUK_OK) return fail(rc);
+  if (g.theta_filter > 0 && (rc = teuk_set_theta_filter(h, g.theta_filter, g.theta_filter_period)) != TEUK_OK)
+    return fail(rc);
   *out = h;
   return TEUK_OK;
 }
@@ -496,7 +508,7 @@ int teuk_set_initial(teuk_t h, const double* phi_pi) {
   h->n_recorded = 0;
   TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
-  return TEUK_OK;
+  return sync_filter_counter(h);
 }
 
 int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re, double amp_im, int ell) {
@@ -512,6 +524,7 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
   h->substeps_done = 0;
   h->n_recorded = 0;
   if (rc == TEUK_OK) TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
+  if (rc == TEUK_OK) rc = sync_filter_counter(h);
   return rc;
 }
 
@@ -630,11 +643,12 @@ int teuk_set_theta_dissipation(teuk_t h, double sigma) {
 
 double teuk_theta_dissipation(teuk_t h) { return h ? h->ko_theta : -1.0; }
 
-int teuk_set_theta_filter(teuk_t h, int l_cut) {
+int teuk_set_theta_filter(teuk_t h, int l_cut, int period) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   const int l_low = std::max(std::abs(h->s), std::abs(h->m));
   if (l_cut != 0 && (l_cut <= l_low || l_cut > 41 || 2 * (l_cut - 1) >= h->n_th))
     return invalid(h, "theta filter: need l_cut = 0 or max(|s|, |m|) < l_cut <= 41 with 2 (l_cut - 1) < n_theta");
+  if (period < 0 || period > 1024) return invalid(h, "theta filter: need 0 <= period <= 1024 (0 = 1)");
   if (h->is_slab() && l_cut > 0) return invalid(h, "theta filter: not on a slab");
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graph(h);
@@ -652,9 +666,13 @@ int teuk_set_theta_filter(teuk_t h, int l_cut) {
     h->filter_lcut = 0;  // the tables of the previous cut are gone
     return rc;
   }
+  if (!h->d_filter_ctr) TEUK_CUDA(h, cudaMalloc(&h->d_filter_ctr, 2 * sizeof(long long)));
   h->filter_lcut = l_cut;
-  return TEUK_OK;
+  h->filter_period = period > 0 ? period : 1;
+  return sync_filter_counter(h);
 }
+
+int teuk_theta_filter_period(teuk_t h) { return h ? h->filter_period : -1; }
 
 int teuk_theta_filter(teuk_t h) { return h ? h->filter_lcut : -1; }
 
@@ -793,7 +811,7 @@ int teuk_set_state(teuk_t h, const double* planes, int64_t substeps_done) {
   if (rc) return rc;
   h->substeps_done = substeps_done;
   TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
-  return TEUK_OK;
+  return sync_filter_counter(h);
 }
 
 int teuk_get_state_device(teuk_t h, double* dev_planes) {
@@ -993,6 +1011,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
   cudaMemcpyAsync(h->status, &status, sizeof(status), cudaMemcpyHostToDevice, h->stream);
   cudaStreamSynchronize(h->stream);
   cudaFree(saved);
+  if (rc == TEUK_OK) rc = sync_filter_counter(h);
   h->persist_steps = best_p;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -87,6 +87,8 @@ struct teuk_s {
   double* eps_th = nullptr;            // [W][n_r]: ko_theta c_th(i) dt / (4096 dtheta) per row
   double* u_ko = nullptr;              // output of the dissipation step (state layout)
   int filter_lcut = 0;                 // theta filter: removes multipoles l >= filter_lcut (0: off)
+  int filter_period = 1;               // ... at every filter_period-th outer step
+  long long* d_filter_ctr = nullptr;   // [2] device: outer steps begun, blocks finished
   double* filt = nullptr;              // its tables [2][n_ell][W][n_th] (analysis, synthesis)
   int filter_n_ell() const { return filter_lcut - std::max(std::abs(s), std::abs(m)); }
   // an operator runs once at the start of every outer step (dissipation or theta filter)

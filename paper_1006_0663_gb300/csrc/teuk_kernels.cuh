@@ -401,6 +401,7 @@ struct DissArgs {
   const double* u;       // [4][W][n_r][pitch]
   double* out;           // same layout
   double eps[4];         // eps_r as W words
+  int eps_single;        // eps_r is one double (sigma / 64 when dt = 0.25 dr*): a cheaper product
   int do_r;              // apply the r* term
   const double* eps_th;  // [W][n_r] or null: no theta term
 };
@@ -428,7 +429,7 @@ __global__ void dissipate_kernel(DissArgs a) {
     d4 = v_add(d4, r_mul_d(v, 6.0));
     d4 = v_sub(d4, r_scale2(ld_s<R>(base + p, ws), 4.0));
     d4 = v_add(d4, ld_s<R>(base + 2 * p, ws));
-    v = v_sub(v, r_mul(from_words<R>(a.eps), d4));
+    v = v_sub(v, a.eps_single ? r_mul_d(d4, a.eps[0]) : r_mul(from_words<R>(a.eps), d4));
   }
   if (a.eps_th && i >= 1 && i <= a.g.n_r - 2) {
     const double* row = base - j;
@@ -468,36 +469,89 @@ struct FilterArgs {
   double* out;        // same layout; may be u (each block reads its row before writing)
   const double* tab;  // [2][n_ell][W][n_th]: 2 pi w_j sY_l(theta_j), then sY_l(theta_j)
   int n_ell;
+  int split;          // partial dot products per coefficient (a power of two)
+  long long* ctr;     // [2]: outer steps begun, blocks finished in this launch
+  int period;         // project at outer steps whose index is a multiple of period
 };
 
-// One block per (interior row, component): the row to shared memory, the n_ell coefficients
-// as dot products in the target precision, then the synthesis.
+// Shared memory of filter_kernel, in doubles: the row's 4 components, the partial sums, the
+// coefficients.
+__host__ __device__ inline size_t filter_smem_doubles(int W, int n_th, int n_ell, int split) {
+  return (size_t)W * (4 * (size_t)n_th + 4 * (size_t)n_ell * split + 4 * (size_t)n_ell);
+}
+
+// One block per interior row, all four components: the row to shared memory; each
+// coefficient as `split` interleaved partial dot products in the target precision, added in
+// the target precision; then the synthesis, one output per thread. At outer steps that do not
+// project, the row is copied to `out` when it is another buffer. The last block to finish
+// counts the outer step (every block has read the count before it finishes).
+template <int W>
+__device__ void filter_row(const FilterArgs& a, double* fsm);
+
 template <int W>
 __global__ void filter_kernel(FilterArgs a) {
-  using R = typename RT<W>::T;
-  step_dependency();
   extern __shared__ double fsm[];
-  const int i = blockIdx.x + 1, c = blockIdx.y;
-  const int n_th = a.g.n_th, n_ell = a.n_ell;
-  const size_t ws = (size_t)a.g.n_r * a.g.pitch;
-  const size_t off = (size_t)c * W * ws + (size_t)i * a.g.pitch;
-  double* row = fsm;                      // [W][n_th]
-  double* coef = fsm + (size_t)W * n_th;  // [W][n_ell]
-  for (int j = threadIdx.x; j < n_th; j += blockDim.x)
-    for (int k = 0; k < W; ++k) row[(size_t)k * n_th + j] = a.u[off + (size_t)k * ws + j];
+  __shared__ int project;
+  if (threadIdx.x == 0) project = (*(volatile long long*)a.ctr) % a.period == 0;
+  __syncthreads();
+  if (project) filter_row<W>(a, fsm);
+  else if (a.out != a.u) {
+    const size_t ws = (size_t)a.g.n_r * a.g.pitch, off = (size_t)(blockIdx.x + 1) * a.g.pitch;
+    for (int t = threadIdx.x; t < 4 * W * a.g.n_th; t += blockDim.x) {
+      const int pl = t / a.g.n_th, j = t - pl * a.g.n_th;
+      a.out[(size_t)pl * ws + off + j] = a.u[(size_t)pl * ws + off + j];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long done = atomicAdd(reinterpret_cast<unsigned long long*>(a.ctr + 1), 1ULL);
+    if (done == gridDim.x - 1) {
+      a.ctr[1] = 0;
+      a.ctr[0] = a.ctr[0] + 1;
+    }
+  }
+}
+
+template <int W>
+__device__ void filter_row(const FilterArgs& a, double* fsm) {
+  using R = typename RT<W>::T;
+  const int i = blockIdx.x + 1;
+  const int n_th = a.g.n_th, n_ell = a.n_ell, S = a.split;
+  const size_t ws = (size_t)a.g.n_r * a.g.pitch, p = (size_t)a.g.pitch;
+  const int n_part = 4 * n_ell * S;
+  double* row = fsm;                                 // [4][W][n_th]
+  double* part = row + (size_t)4 * W * n_th;         // word planes of stride n_part
+  double* coef = part + (size_t)n_part * W;          // [4][W][n_ell]
+  for (int t = threadIdx.x; t < 4 * W * n_th; t += blockDim.x) {
+    const int c = t / (W * n_th), r = t - c * W * n_th, k = r / n_th, j = r - k * n_th;
+    row[t] = a.u[(size_t)(c * W + k) * ws + (size_t)i * p + j];
+  }
   __syncthreads();
   const double* ta = a.tab;
   const double* ts = a.tab + (size_t)n_ell * W * n_th;
-  for (int l = threadIdx.x; l < n_ell; l += blockDim.x) {
+  for (int t = threadIdx.x; t < n_part; t += blockDim.x) {
+    const int q = t % S, cl = t / S, l = cl % n_ell, c = cl / n_ell;
+    const double* tl = ta + (size_t)l * W * n_th;
+    const double* rc = row + (size_t)c * W * n_th;
     Acc<R> acc(mw::r_from<R>(0.0));
-    for (int j = 0; j < n_th; ++j) acc.mac(ld_r<R>(ta + (size_t)l * W * n_th + j, n_th), ld_s<R>(row + j, n_th));
-    st_r(coef + l, n_ell, acc.get());
+    for (int j = q; j < n_th; j += S) acc.mac(ld_r<R>(tl + j, n_th), ld_s<R>(rc + j, n_th));
+    st_r(part + t, n_part, acc.get());
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n_th; j += blockDim.x) {
+  for (int t = threadIdx.x; t < 4 * n_ell; t += blockDim.x) {
+    R sum = ld_s<R>(part + (size_t)t * S, n_part);
+    for (int q = 1; q < S; ++q) sum = mw::r_add(sum, ld_s<R>(part + (size_t)t * S + q, n_part));
+    const int c = t / n_ell, l = t - c * n_ell;
+    st_r(coef + (size_t)c * W * n_ell + l, n_ell, sum);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 4 * n_th; t += blockDim.x) {
+    const int c = t / n_th, j = t - c * n_th;
+    const double* cc = coef + (size_t)c * W * n_ell;
     Acc<R> acc(mw::r_from<R>(0.0));
-    for (int l = 0; l < n_ell; ++l) acc.mac(ld_r<R>(ts + (size_t)l * W * n_th + j, n_th), ld_s<R>(coef + l, n_ell));
-    st_r(a.out + off + j, ws, acc.get());
+    for (int l = 0; l < n_ell; ++l) acc.mac(ld_r<R>(ts + (size_t)l * W * n_th + j, n_th), ld_s<R>(cc + l, n_ell));
+    st_r(a.out + (size_t)c * W * ws + (size_t)i * p + j, ws, acc.get());
   }
 }
 

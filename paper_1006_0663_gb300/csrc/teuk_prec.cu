@@ -329,9 +329,16 @@ int theta_dissipation_impl(teuk_s* h, double sigma, double* max_rate) {
   return TEUK_OK;
 }
 
-// Dynamic shared memory of filter_kernel: one row of W words plus its coefficients.
-size_t filter_smem(const teuk_s* h) {
-  return (size_t)W * (h->n_th + h->filter_n_ell()) * sizeof(double);
+// Launch of filter_kernel: 256 threads per row; each coefficient split into the largest power
+// of two (at most 8) of partial dot products that keeps the 4 n_ell coefficients within them.
+constexpr int kFilterThreads = 256;
+int filter_split(int n_ell) {
+  int sp = 1;
+  while (sp < 8 && 4 * n_ell * sp * 2 <= kFilterThreads) sp *= 2;
+  return sp;
+}
+size_t filter_smem(int n_th, int n_ell) {
+  return filter_smem_doubles(W, n_th, n_ell, filter_split(n_ell)) * sizeof(double);
 }
 
 // Tables of the theta filter: [2][n_ell][W][n_th], first 2 pi w_j sY_lm(theta_j) (analysis),
@@ -353,14 +360,17 @@ int filter_tables_impl(teuk_s* h, int l_cut) {
   h->filt = nullptr;
   TEUK_CUDA(h, cudaMalloc(&h->filt, tab.size() * sizeof(double)));
   TEUK_CUDA(h, cudaMemcpy(h->filt, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
-  const size_t smem = (size_t)W * (n_th + n_ell) * sizeof(double);
+  const size_t smem = filter_smem(n_th, n_ell);
   if (smem > 48 * 1024)
     TEUK_CUDA(h, cudaFuncSetAttribute(filter_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return TEUK_OK;
 }
 
 // The operators of an outer step's start: the dissipation kernel into u_ko, then either the
-// theta filter from u_ko back into the state or a copy back; the filter alone works in place.
+// theta filter kernel from u_ko back into the state (it projects every filter_period-th outer
+// step and copies otherwise) or a copy back; the filter alone works in place. The filter
+// kernel is launched without programmatic dependence: its blocks would otherwise become
+// resident early behind the dissipation kernel, and the step kernels behind it.
 int dissipate_impl(teuk_s* h) {
   const bool ko = h->ko_sigma > 0 || h->ko_theta > 0;
   if (ko) {
@@ -369,6 +379,7 @@ int dissipate_impl(teuk_s* h) {
     da.u = h->u;
     da.out = h->u_ko;
     std::memcpy(da.eps, h->ko_eps_w, sizeof(da.eps));
+    da.eps_single = h->ko_eps_w[1] == 0 && h->ko_eps_w[2] == 0 && h->ko_eps_w[3] == 0;
     da.do_r = h->ko_sigma > 0;
     da.eps_th = h->ko_theta > 0 ? h->eps_th : nullptr;
     TEUK_CUDA(h, launch_dep(dissipate_kernel<W>, dim3((h->n_th + 63) / 64, h->n_r, 4), dim3(64), 0, h->stream,
@@ -383,7 +394,10 @@ int dissipate_impl(teuk_s* h) {
     fa.out = h->u;
     fa.tab = h->filt;
     fa.n_ell = h->filter_n_ell();
-    TEUK_CUDA(h, launch_dep(filter_kernel<W>, dim3(h->n_r - 2, 4), dim3(128), filter_smem(h), h->stream, fa));
+    fa.split = filter_split(fa.n_ell);
+    fa.ctr = h->d_filter_ctr;
+    fa.period = h->filter_period;
+    filter_kernel<W><<<dim3(h->n_r - 2), dim3(kFilterThreads), filter_smem(h->n_th, fa.n_ell), h->stream>>>(fa);
     TEUK_CUDA(h, cudaGetLastError());
     h->launches += 1;
   } else if (ko) {

@@ -31,7 +31,7 @@ SYMBOLS = [
     "teuk_set_dissipation", "teuk_set_engine", "teuk_engine", "teuk_set_theta_dissipation",
     "teuk_theta_dissipation", "teuk_int_peak", "teuk_test_stall_copies", "teuk_set_persistent",
     "teuk_create_slab", "teuk_get_halo_rows", "teuk_set_halo_rows", "teuk_slab_rows",
-    "teuk_set_theta_filter", "teuk_theta_filter",
+    "teuk_set_theta_filter", "teuk_theta_filter", "teuk_theta_filter_period",
 ]
 
 
@@ -43,7 +43,7 @@ class TeukGrid(ctypes.Structure):
         ("substeps", ctypes.c_int32), ("theta_order", ctypes.c_int32),
         ("parity", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("ko_sigma", ctypes.c_double), ("ko_theta", ctypes.c_double),
-        ("theta_filter", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("theta_filter", ctypes.c_int32), ("theta_filter_period", ctypes.c_int32),
     ]
 
 
@@ -88,8 +88,9 @@ def lib(build_if_missing: bool = True):
         L.teuk_set_theta_dissipation.argtypes = [vp, d]
         L.teuk_theta_dissipation.argtypes = [vp]
         L.teuk_theta_dissipation.restype = d
-        L.teuk_set_theta_filter.argtypes = [vp, ctypes.c_int]
+        L.teuk_set_theta_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.teuk_theta_filter.argtypes = [vp]
+        L.teuk_theta_filter_period.argtypes = [vp]
         L.teuk_set_engine.argtypes = [vp, i32]
         L.teuk_engine.argtypes = [vp]
         L.teuk_get_state.argtypes = [vp, dp, P(i64)]
@@ -168,13 +169,13 @@ class Teuk:
 
     def __init__(self, *, M, a, s, m, rstar_min, rstar_max, n_r, n_theta, dt=0.0, substeps=1,
                  theta_order=10, parity=0, precision=FP64, stream="current", own_rows=None,
-                 ko_sigma=0.0, ko_theta=0.0, theta_filter=0):
+                 ko_sigma=0.0, ko_theta=0.0, theta_filter=0, theta_filter_period=1):
         """own_rows = (own_lo, own_hi): an r* slab of the grid (teuk_create_slab); n_r is then
         the whole grid's and self.n_r the slab's local rows (owned rows and halos)."""
         L = lib()
         self.grid = TeukGrid(float(rstar_min), float(rstar_max), int(n_r), int(n_theta), float(dt),
                              int(substeps), int(theta_order), int(parity), 0, float(ko_sigma),
-                             float(ko_theta), int(theta_filter), 0)
+                             float(ko_theta), int(theta_filter), int(theta_filter_period))
         h = ctypes.c_void_p()
         st = _current_stream() if stream == "current" else stream
         if own_rows is None:
@@ -203,7 +204,8 @@ class Teuk:
                 theta_order=p.theta_order, parity=p.parity,
                 precision=precision if precision is not None else p.words,
                 ko_sigma=getattr(p, "ko_sigma", 0.0), ko_theta=getattr(p, "ko_theta", 0.0),
-                theta_filter=getattr(p, "theta_filter", 0), **kw)
+                theta_filter=getattr(p, "theta_filter", 0),
+                theta_filter_period=getattr(p, "theta_filter_period", 1), **kw)
         return g
 
     def close(self):
@@ -281,14 +283,18 @@ class Teuk:
     def theta_dissipation(self) -> float:
         return float(lib().teuk_theta_dissipation(self._h))
 
-    def set_theta_filter(self, l_cut):
-        """Projection of every row onto the harmonics sY_lm with l < l_cut once per outer step
-        (not part of the paper's scheme; 0 = off)."""
-        _check(lib().teuk_set_theta_filter(self._h, int(l_cut)), self._h)
+    def set_theta_filter(self, l_cut, period=1):
+        """Projection of every row onto the harmonics sY_lm with l < l_cut at every period-th
+        outer step (not part of the paper's scheme; l_cut = 0 = off)."""
+        _check(lib().teuk_set_theta_filter(self._h, int(l_cut), int(period)), self._h)
 
     @property
     def theta_filter(self) -> int:
         return int(lib().teuk_theta_filter(self._h))
+
+    @property
+    def theta_filter_period(self) -> int:
+        return int(lib().teuk_theta_filter_period(self._h))
 
     def substep_host_state(self, planes, n=1):
         """n iterations with the state held in host memory (the paper's first CUDA design's

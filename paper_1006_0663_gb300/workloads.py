@@ -95,6 +95,7 @@ class Problem:
     ko_sigma: float = 0.0  # r* dissipation (not in the paper; 0 = the paper's scheme)
     ko_theta: float = 0.0  # theta dissipation (not in the paper; 0 = the paper's scheme)
     theta_filter: int = 0  # theta filter l_cut (not in the paper; 0 = the paper's scheme)
+    theta_filter_period: int = 1  # outer steps between its projections
 
     @property
     def dr(self) -> float:
@@ -129,7 +130,7 @@ class Problem:
 C1 = Problem("c1", 1.0, 0.5, -2, 2, -50.0, 150.0, 256, 64, 1000, 46, 1, 2, 1, rstar_obs=100.0, ko_sigma=2.0)
 C2 = Problem("c2", 1.0, 0.9, -2, 2, -100.0, 400.0, 2048, 128, 40000, 88, 2, 2, 2, ko_sigma=2.0)
 C3 = Problem("c3", 1.0, 0.99, 0, 0, -100.0, 400.0, 1024, 64, 40000, 20, 4, 0, 3, ko_sigma=2.0,
-             theta_filter=7)
+             theta_filter=7, theta_filter_period=8)
 C5 = Problem("c5", 1.0, 0.9, -2, 2, -200.0, 1800.0, 16384, 512, 2000, 81, 1, 2, 5, rstar_obs=1000.0,
              ko_sigma=2.0)
 

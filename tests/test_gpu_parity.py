@@ -1007,23 +1007,24 @@ def _rich_state(p, W, seed):
 
 
 @pytest.mark.parametrize("W,engine", [(1, 0), (2, 0), (2, 1), (4, 0), (4, 1)])
-@pytest.mark.parametrize("s,m,ko", [(0, 0, 0.0), (-1, 2, 1.0), (-2, 2, 1.0)])
-def test_theta_filter_parity(oracle_mod, W, engine, s, m, ko):
+@pytest.mark.parametrize("s,m,ko,period", [(0, 0, 0.0, 1), (-1, 2, 1.0, 2), (-2, 2, 1.0, 1), (0, 0, 0.0, 2)])
+def test_theta_filter_parity(oracle_mod, W, engine, s, m, ko, period):
     """theta filter (not part of the paper's scheme), alone and after the r* dissipation,
-    against the 256-bit oracle (which solves the Gram system of its own profiles instead of
-    using orthonormal tables): random theta content, 3 outer steps and 2 iterations."""
+    every outer step or every second one, against the 256-bit oracle (which solves the Gram
+    system of its own profiles instead of using orthonormal tables): random theta content, 3
+    outer steps and 2 iterations."""
     p = small(s=s, m=m, a=0.9, n_r=45, n_theta=24, substeps=3)
     l_cut = max(abs(s), abs(m)) + 5
     g = teuk.Teuk(precision=W, **p)
     if engine:
         g.set_engine(engine)
     g.set_dissipation(ko)
-    g.set_theta_filter(l_cut)
-    assert g.theta_filter == l_cut
+    g.set_theta_filter(l_cut, period)
+    assert g.theta_filter == l_cut and g.theta_filter_period == period
     o = oracle_mod.Oracle(M=p["M"], a=p["a"], s=s, m=m, rstar_min=p["rstar_min"], rstar_max=p["rstar_max"],
                           n_r=p["n_r"], n_theta=p["n_theta"], dt=p["dt"], substeps=p["substeps"],
                           theta_order=p["theta_order"], parity=workloads.parity_of(m, s), bits=256,
-                          ko_sigma=ko, theta_filter=l_cut)
+                          ko_sigma=ko, theta_filter=l_cut, theta_filter_period=period)
     u0 = _rich_state(p, W, 40 + 3 * abs(s) + m)
     g.set_state(u0)
     o.set_state(u0[:, :1])
@@ -1051,19 +1052,29 @@ def test_theta_filter_rules(W):
     switches it off (bit for bit the unfiltered run); slabs, batches and the no-allocation
     entry point refuse filtered handles."""
     p = small(s=-1, m=2, n_r=41, n_theta=24, substeps=3)
-    a = teuk.Teuk(precision=W, theta_filter=6, **p)
+    a = teuk.Teuk(precision=W, theta_filter=6, theta_filter_period=2, **p)
     b = teuk.Teuk(precision=W, **p)
-    b.set_theta_filter(6)
-    assert a.theta_filter == 6 and b.theta_filter == 6
+    b.set_theta_filter(6, 2)
+    assert a.theta_filter == 6 and b.theta_filter == 6 and a.theta_filter_period == b.theta_filter_period == 2
     u0 = _rich_state(p, W, 7)
     for h in (a, b):
         h.set_state(u0)
         h.step(2)
     np.testing.assert_array_equal(a.get_state(), b.get_state())
-    for bad in (-1, 2, 13, 42):  # below max(|s|, |m|) + 1, 2 (l_cut - 1) >= n_theta, > 41
-        with pytest.raises(teuk.TeukError):
-            b.set_theta_filter(bad)
-        assert b.theta_filter == 6
+    for bad, per in ((-1, 1), (2, 1), (13, 1), (42, 1), (6, -1), (6, 1025)):
+        with pytest.raises(teuk.TeukError):  # l_cut <= max(|s|, |m|), 2 (l_cut - 1) >= n_theta, > 41; period
+            b.set_theta_filter(bad, per)
+        assert b.theta_filter == 6 and b.theta_filter_period == 2
+    # the outer-step count restarts from the state's iteration count: from outer step 1 with
+    # period 2 the first outer step does not project (bit for bit the unfiltered step)
+    e, f = teuk.Teuk(precision=W, theta_filter=6, theta_filter_period=2, **p), teuk.Teuk(precision=W, **p)
+    for h in (e, f):
+        h.set_state(u0, substeps_done=p["substeps"])
+        h.step(1)
+    np.testing.assert_array_equal(e.get_state(), f.get_state())
+    e.step(1)  # outer step 2 projects
+    f.step(1)
+    assert np.abs(e.get_state() - f.get_state()).max() > 0
     with pytest.raises(teuk.TeukError):
         teuk.Teuk(precision=W, theta_filter=2, **p)
     with pytest.raises(teuk.TeukError):
@@ -1111,7 +1122,8 @@ def test_c3_outer_step_operators_full_size(oracle_mod, engine):
     o = oracle_mod.Oracle(M=prob.M, a=prob.a, s=prob.s, m=prob.m, rstar_min=prob.rstar_min,
                           rstar_max=prob.rstar_max, n_r=prob.n_r, n_theta=prob.n_theta, dt=0.0,
                           substeps=prob.substeps, parity=prob.parity, row_lo=wlo, row_hi=whi, bits=256,
-                          ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta, theta_filter=prob.theta_filter)
+                          ko_sigma=prob.ko_sigma, ko_theta=prob.ko_theta, theta_filter=prob.theta_filter,
+                          theta_filter_period=prob.theta_filter_period)
     o.pulse(prob.center, prob.width, ar, ai, prob.ell)
     o.step(nsub)
     err, umax = o.max_rel_err(np.ascontiguousarray(full[:, :, wlo:whi + 1]), lo - wlo, hi - wlo)

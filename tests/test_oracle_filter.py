@@ -123,15 +123,40 @@ def test_filter_parameter_rules(oracle_mod):
         o.filter_rows()
 
 
+def test_filter_period_schedule(oracle_mod):
+    """With period 3 the filter projects at outer steps 0 and 3: four outer steps equal three
+    outer steps that project at step 0 only (period 1024), then one outer step that projects
+    (a fresh run with period 1 from that state); and differ from projecting every step."""
+    kw = dict(M=1.0, a=0.9, s=-1, m=2, rstar_min=-30.0, rstar_max=50.0, n_r=41, n_theta=24, dt=0.0,
+              substeps=3, bits=53, ko_sigma=1.0, theta_filter=6, parity=oracle_mod.default_parity(2, -1))
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((4, 1, 41, 24))
+    u[:, :, 0] = 0.0
+    u[:, :, -1] = 0.0
+    runs = {}
+    for period in (3, 1024, 1):
+        runs[period] = oracle_mod.Oracle(theta_filter_period=period, **kw)
+        runs[period].set_state(u)
+    runs[3].step(4 * 3)
+    runs[1].step(4 * 3)
+    runs[1024].step(3 * 3)
+    last = oracle_mod.Oracle(theta_filter_period=1, **kw)
+    last.set_state(runs[1024].get_state())
+    last.step(3)
+    np.testing.assert_array_equal(runs[3].get_state(), last.get_state())
+    assert not np.array_equal(runs[3].get_state(), runs[1].get_state())
+
+
 def test_filter_removes_photon_sphere_growth(oracle_mod):
     """a = 0.99, s = m = 0, r* in [-100, 400] with 1024 points, k = 20, r* dissipation
     sigma = 2, theta x 32, random data on rows 150..260 (r* from -27 to 27): multipoles
-    l >= 7 are trapped at r ~ 3M by the grid and grow; l_cut = 7 removes them."""
+    l >= 7 are trapped at r ~ 3M by the grid and grow; l_cut = 7 removes them, every outer
+    step or every 8th (about 1 M)."""
     peaks = {}
-    for l_cut in (0, 7):
+    for l_cut, period in ((0, 1), (7, 1), (7, 8)):
         o = oracle_mod.Oracle(M=1.0, a=0.99, s=0, m=0, rstar_min=-100.0, rstar_max=400.0, n_r=1024,
                               n_theta=32, dt=0.0, substeps=20, bits=53, ko_sigma=2.0, row_lo=150,
-                              row_hi=260, theta_filter=l_cut)
+                              row_hi=260, theta_filter=l_cut, theta_filter_period=period)
         rng = np.random.default_rng(3)
         u = rng.standard_normal((4, 1, o.nrow, 32))
         u[:, :, :3] = 0.0
@@ -141,7 +166,8 @@ def test_filter_removes_photon_sphere_growth(oracle_mod):
         for _ in range(8):
             o.step(250 * 20)  # 250 outer steps, 30.5 M
             trace.append(np.abs(o.get_state()).max())
-        peaks[l_cut] = trace
-    assert peaks[0][-1] > 1e6 * peaks[0][1]        # unfiltered: e^{~0.1 t}
-    assert peaks[7][-1] < 0.5 * peaks[7][1]         # filtered: decays
-    assert peaks[0][-1] > 1e6 * peaks[7][-1]
+        peaks[l_cut, period] = trace
+    assert peaks[0, 1][-1] > 1e6 * peaks[0, 1][1]        # unfiltered: e^{~0.1 t}
+    for period in (1, 8):
+        assert peaks[7, period][-1] < 0.5 * peaks[7, period][1]  # filtered: decays
+        assert peaks[0, 1][-1] > 1e6 * peaks[7, period][-1]
