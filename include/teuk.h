@@ -296,7 +296,8 @@ int teuk_batch_destroy(teuk_batch_t b);
  * along theta x rows of theta per thread block, one warp per 32 columns, register budgets)
  * on a copy of the current state; when an outer step is short (under 5 ms) the four fastest
  * are timed again over four outer steps as teuk_step runs them (a replayed CUDA graph), and the
- * persistent launches are tried against them. It keeps the fastest for this handle, restores
+ * persistent launches are tried against them. Grids of up to 2^20 points also try the fused
+ * iterations (variant 10), which allocate a second state-sized buffer kept with the handle. It keeps the fastest for this handle, restores
  * the state and
  * returns in *rows_per_block (may be NULL) the rows per block of the chosen shape, 0 when the
  * one-warp-per-32-columns kernels won (teuk_launch_shape reports the whole shape). Allocates
@@ -308,14 +309,20 @@ int teuk_tune(teuk_t h, int* rows_per_block);
  * 3, 4, 5 = one warp per (row, 32 theta columns) with <= 255, 128, 85 registers;
  * 6, 7, 8 = balanced: as many blocks of threads_theta threads as fit on the GPU at once,
  * each taking the same number of (row, theta) points, budgets as for 0, 1, 2; 9 = persistent
- * (teuk_set_persistent). */
+ * (teuk_set_persistent); 10 = fused iterations: one launch per Lax-Wendroff iteration, each block
+ * forming the R + 1 half-step rows its R full-step rows need (rows_per_block = R) in shared
+ * memory, so one half row per block is formed twice, and writing a second state buffer (the
+ * iterations alternate between the two; a sequence that ends in the second one is copied back,
+ * so the state is in place between calls): the bits of the two-kernel form with half the
+ * launches, for grids whose iterations are shorter than a launch. */
 int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* variant);
 /* Sets the launch shape explicitly (same meaning as above; threads_theta a multiple of 32,
  * threads_theta * rows_per_block <= 256; both ignored for variants 3..5, rows_per_block
  * ignored for 6..8; with variants 2 and 8 the block is cut to 128 threads; on the integer
  * engine only variants 0..2, and rows_per_block rows must fit one block's shared memory,
- * else TEUK_ERR_INVALID_ARG; the autotuner skips such shapes). Results do not depend on the
- * shape. */
+ * else TEUK_ERR_INVALID_ARG; the autotuner skips such shapes; variant 10 needs threads_theta
+ * <= 128, threads_theta * (rows_per_block + 1) <= 256, the FP64-transform engine and a whole
+ * grid, not a slab). Results do not depend on the shape. */
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant);
 /* Persistent launches for small problems (FP64, or the FP64 error-free transforms): teuk_step
  * runs steps_per_launch outer steps (k iterations each, Eqs. lw1, lw2) per cooperative launch

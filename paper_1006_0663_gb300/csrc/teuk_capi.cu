@@ -56,14 +56,35 @@ int dispatch_dissipate(teuk_s* h) {
   }
 }
 
+// Kernel family 4 writes every other iteration into the second state buffer; this copies such
+// a result back (queued on the stream), so that h->u holds the state again.
+int settle_state(teuk_s* h) {
+  if (!h->in_u2) return TEUK_OK;
+  h->in_u2 = false;
+  TEUK_CUDA(h, cudaMemcpyAsync(h->u, h->u2, (size_t)4 * h->W * h->n_r * h->pitch * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h->stream));
+  return TEUK_OK;
+}
+
+// The second state buffer of kernel family 4, zeroed once (its r* boundary rows stay zero).
+int ensure_u2(teuk_s* h) {
+  if (h->u2) return TEUK_OK;
+  const size_t bytes = (size_t)4 * h->W * h->n_r * h->pitch * sizeof(double);
+  TEUK_CUDA(h, cudaMalloc(&h->u2, bytes));
+  TEUK_CUDA(h, cudaMemsetAsync(h->u2, 0, bytes, h->stream));
+  TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return TEUK_OK;
+}
+
 // One Lax-Wendroff iteration, preceded by the r* dissipation step when it is enabled and an
-// outer step begins (the iteration count is a multiple of k).
+// outer step begins (the iteration count is a multiple of k); the state is in h->u after it.
 int iterate(teuk_s* h, bool record, int64_t slot) {
   if (h->dissipating() && h->substeps_done % h->k == 0) {
     int rc = dispatch_dissipate(h);
     if (rc) return rc;
   }
   int rc = dispatch_substep(h, record, slot);
+  if (rc == TEUK_OK) rc = settle_state(h);
   if (rc) return rc;
   ++h->substeps_done;
   return TEUK_OK;
@@ -101,6 +122,9 @@ void free_all(teuk_s* h) {
   h->status = nullptr;
   if (h->d_filter_ctr) cudaFree(h->d_filter_ctr);
   h->d_filter_ctr = nullptr;
+  if (h->u2) cudaFree(h->u2);
+  h->u2 = nullptr;
+  h->in_u2 = false;
   if (h->pflags) cudaFree(h->pflags);
   h->pflags = nullptr;
   h->pflags_cap = 0;
@@ -224,6 +248,8 @@ int build_graph(teuk_s* h, bool record) {
     h->time_this = q == h->k - 1;  // the graph times the last iteration of the outer step only
     rc = dispatch_substep(h, record && q == h->k - 1, -1);
   }
+  if (rc == TEUK_OK) rc = settle_state(h);  // odd k with fused iterations: one copy per outer step
+  h->in_u2 = false;
   h->time_this = true;
   if (rc == TEUK_OK && record) advance_counter_kernel<<<1, 1, 0, h->stream>>>(h->d_ring_counter);
   e = cudaStreamEndCapture(h->stream, &graph);
@@ -506,6 +532,7 @@ int teuk_set_initial(teuk_t h, const double* phi_pi) {
   }
   h->substeps_done = 0;
   h->n_recorded = 0;
+  h->in_u2 = false;
   TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   return sync_filter_counter(h);
@@ -523,6 +550,7 @@ int teuk_set_initial_pulse(teuk_t h, double center, double width, double amp_re,
   }
   h->substeps_done = 0;
   h->n_recorded = 0;
+  h->in_u2 = false;
   if (rc == TEUK_OK) TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
   if (rc == TEUK_OK) rc = sync_filter_counter(h);
   return rc;
@@ -695,7 +723,7 @@ int teuk_step(teuk_t h, int64_t n) {
     for (int64_t t = 0; t < n; ++t) TEUK_CUDA(h, cudaGraphLaunch(h->graph_exec, h->stream));
     if (!h->graph_events.empty()) h->graph_events_fresh = true;
     h->substeps_done += n * h->k;
-    h->launches += n * (2 * h->k + h->outer_op_launches());
+    h->launches += n * (h->iteration_launches() * h->k + h->outer_op_launches());
     if (record) h->n_recorded += n;
     return TEUK_OK;
   }
@@ -810,6 +838,7 @@ int teuk_set_state(teuk_t h, const double* planes, int64_t substeps_done) {
   int rc = copy_planes(h, h->u, planes, nullptr, 4, h->n_r);
   if (rc) return rc;
   h->substeps_done = substeps_done;
+  h->in_u2 = false;
   TEUK_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream));
   return sync_filter_counter(h);
 }
@@ -848,6 +877,16 @@ bool ix_shape_fits(const teuk_s* h, int ty) {
   return b <= (size_t)optin;
 }
 
+// Whether the fused block with R full-step rows fits the shared memory a block can have.
+bool fused_smem_fits(const teuk_s* h, int R) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return teuk::fused_smem(h, R) <= (size_t)optin;
+}
+
 int teuk_tune(teuk_t h, int* rows_per_block) {
   if (!h) return TEUK_ERR_INVALID_ARG;
   const size_t n = (size_t)4 * h->W * h->n_r * h->pitch;
@@ -882,6 +921,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
     cudaEventRecord(e0, h->stream);
     for (int t = 0; t < 4 && rc == TEUK_OK; ++t) rc = dispatch_substep(h, false, 0);
     cudaEventRecord(e1, h->stream);
+    if (rc == TEUK_OK) rc = settle_state(h);
     cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -912,6 +952,17 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
       if (tx == tx_top) break;
     }
   }
+  // fused iterations (one launch each) for grids of up to 2^20 points, threads along theta x
+  // (R + 1) rows, R = 1, 3, 7 full-step rows per block
+  if (rc == TEUK_OK && h->engine == 0 && !h->is_slab() && (int64_t)h->n_r * h->n_th <= ((int64_t)1 << 20) &&
+      (rc = ensure_u2(h)) == TEUK_OK) {
+    const int tx_top = std::min(tx_full, 128);
+    for (int tx = 32; tx <= tx_top && rc == TEUK_OK; tx = (tx * 2 > tx_top && tx < tx_top) ? tx_top : tx * 2) {
+      for (int R = 1; R <= 7 && tx * (R + 1) <= 256 && rc == TEUK_OK; R = 2 * R + 1)
+        if (fused_smem_fits(h, R)) trial(4, 0, tx, R);
+      if (tx == tx_top) break;
+    }
+  }
   int best_p = 1;
   double* ring = h->ring;  // the observer ring is left alone by the steps below
   h->ring = nullptr;
@@ -938,7 +989,7 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
       const int r = dispatch_substep(h, false, 0);
       if (r != TEUK_OK) return r;
     }
-    return TEUK_OK;
+    return settle_state(h);
   };
   // Small problems run as replayed graphs, where launch costs differ from direct launches: the
   // four fastest shapes above are timed again as teuk_step runs them, over four outer steps,
@@ -1051,6 +1102,13 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
   }
   int tx, ty;
   teuk::row_block_shape(h, tx, ty);
+  if (h->kernel_family == 4) {  // fused iterations: reported as variant 10 with R full-step rows
+    teuk::fused_shape(h, tx, ty);
+    if (threads_theta) *threads_theta = tx;
+    if (rows_per_block) *rows_per_block = ty;
+    if (variant) *variant = 10;
+    return TEUK_OK;
+  }
   if (h->kernel_family == 3) {  // the persistent kernel's block (see persist_impl)
     ty = h->rows_per_block;
     tx = std::min(((h->n_th + 31) / 32) * 32, 256 / ty);
@@ -1064,9 +1122,28 @@ int teuk_launch_shape(teuk_t h, int* threads_theta, int* rows_per_block, int* va
 }
 
 int teuk_set_launch_shape(teuk_t h, int threads_theta, int rows_per_block, int variant) {
-  if (!h || variant < 0 || variant > 8) return TEUK_ERR_INVALID_ARG;
+  if (!h || variant < 0 || (variant > 8 && variant != 10)) return TEUK_ERR_INVALID_ARG;
   if (h->engine == 1 && variant >= 3)
     return invalid(h, "launch shape: the integer engine has the rows-per-block kernels only (variants 0..2)");
+  if (variant == 10) {
+    if (h->is_slab()) return invalid(h, "launch shape: fused iterations are not for slabs");
+    if (threads_theta < 32 || threads_theta % 32 != 0 || threads_theta > 128 || rows_per_block < 1 ||
+        threads_theta * (rows_per_block + 1) > 256)
+      return invalid(h, "launch shape: fused iterations need threads_theta a multiple of 32 up to 128 and "
+                        "threads_theta * (rows + 1) <= 256");
+    if (!fused_smem_fits(h, rows_per_block))
+      return invalid(h, "launch shape: the fused block's rows need more shared memory than a block can have");
+    TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
+    int rc = settle_state(h);
+    if (rc == TEUK_OK) rc = ensure_u2(h);
+    if (rc != TEUK_OK) return rc;
+    h->kernel_family = 4;
+    h->kernel_variant = 0;
+    h->threads_theta = threads_theta;
+    h->rows_per_block = rows_per_block;
+    drop_graph(h);
+    return TEUK_OK;
+  }
   if (variant >= 6) {
     if (threads_theta < 32 || threads_theta % 32 != 0 || threads_theta > 256)
       return invalid(h, "launch shape: threads_theta a multiple of 32, at most 256");

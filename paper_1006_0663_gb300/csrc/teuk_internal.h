@@ -21,9 +21,13 @@ struct teuk_s {
   int threads_theta = 0;   // threads along theta per row (0: n_theta rounded up to 32, <= 256)
   int kernel_variant = 0;  // register budget of the step kernels: 0 (<= 255), 1 (<= 128), 2 (rows:
                            // <= 102 in blocks of <= 128 threads; warp segments: <= 85)
+  double* u2 = nullptr;    // second state buffer of kernel family 4 (boundary rows zero)
+  int iteration_launches() const { return kernel_family == 4 && engine == 0 ? 1 : 2; }
+  bool in_u2 = false;      // family 4 left the latest iteration in u2 (settled back by teuk_capi.cu)
   int kernel_family = 0;   // 0: rows per block (half_kernel/full_kernel), 1: one warp per 32 columns,
                            // 2: balanced (every resident block the same number of points),
-                           // 3: persistent (persist_kernel: outer steps per cooperative launch)
+                           // 3: persistent (persist_kernel: outer steps per cooperative launch),
+                           // 4: fused iteration (fused_kernel: one launch per iteration, u <-> u2)
   int persist_steps = 1;   // family 3: outer steps per launch
   int* pflags = nullptr;   // family 3: neighbour counters and abort word of the launch
   int pflags_cap = 0;
@@ -175,6 +179,20 @@ void time_end(teuk_s* h, int kind, cudaEvent_t a);
 // Block shape of the row-family and balanced step kernels for the handle's launch shape:
 // threads along theta (a multiple of 32 up to 256, or the row width) x rows per block. The
 // register budget 2 allows at most 128 threads per block.
+// Block of kernel family 4 (fused iteration): tx threads along theta x (R + 1) rows, R full-step
+// rows per block, tx (R + 1) <= 256.
+inline void fused_shape(const teuk_s* h, int& tx, int& R) {
+  tx = ((h->n_th + 31) / 32) * 32;
+  if (tx > 128) tx = 128;
+  if (h->threads_theta > 0 && h->threads_theta < tx) tx = h->threads_theta;
+  R = h->rows_per_block > 0 ? h->rows_per_block : 1;
+  while (R > 1 && tx * (R + 1) > 256) --R;
+}
+inline size_t fused_smem(const teuk_s* h, int R) {
+  return ((size_t)4 * h->W * (R + 1) * h->pitch + (size_t)(R + 1) * 2 * h->W * (h->n_th + 2 * h->radius)) *
+         sizeof(double);
+}
+
 inline void row_block_shape(const teuk_s* h, int& tx, int& ty) {
   const int cap = h->kernel_variant == 2 ? 128 : 256;
   tx = ((h->n_th + 31) / 32) * 32;

@@ -641,7 +641,14 @@ struct StepArgs {
   long long ring_cap;
   double* ring;            // [cap][2][W][n_th]
   unsigned int* status;    // bit 0: non-finite value produced
+  size_t uh_ws;            // plane stride of uh in doubles (0: the scratch of n_r - 1 rows)
+  int uh_row0;             // half row h is stored at row h - uh_row0 of uh
 };
+
+// Plane stride of the half-step rows uh.
+__device__ __forceinline__ size_t uh_plane(const StepArgs& a) {
+  return a.uh_ws ? a.uh_ws : (size_t)(a.g.n_r - 1) * a.g.pitch;
+}
 
 // Centred theta operator at column j on a ghosted shared-memory row (index j + radius is
 // column j): sum_q w[q][j] f[j + q], combined second-derivative and cot(th) first-derivative
@@ -735,6 +742,7 @@ __device__ __forceinline__ void half_point(const StepArgs& a, int h, int j, cons
   const R LR = theta_op<R, W>(sRj, gstride, a.wts, n_th, rad, j);
   const R LI = theta_op<R, W>(sIj, gstride, a.wts, n_th, rad, j);
   const size_t ci = (size_t)h * pitch + j;
+  const size_t us = uh_plane(a), cu = (size_t)(h - a.uh_row0) * pitch + j;
   const R H0 = ld_r<R>(a.ch + 0 * W * hs + ci, hs), H1 = ld_r<R>(a.ch + 1 * W * hs + ci, hs);
   const R H2 = ld_r<R>(a.ch + 2 * W * hs + ci, hs), H3 = ld_r<R>(a.ch + 3 * W * hs + ci, hs);
   const R H4 = ld_r<R>(a.ch + 4 * W * hs + ci, hs), H5 = ld_r<R>(a.ch + 5 * W * hs + ci, hs);
@@ -752,10 +760,10 @@ __device__ __forceinline__ void half_point(const StepArgs& a, int h, int j, cons
   qi.mac(H3, sQI); qi.mac(v_neg(H4), sQR); qi.mac(H0, uQI1); qi.mac(v_neg(H0), uQI0); qi.mac(H1, dPI);
   qi.mac(v_neg(H2), dPR);
   qi.mac(H5, LI); qi.mac(H6, sPI); qi.mac(H7, sPR);
-  st_r(a.uh + 0 * W * hs + ci, hs, pr.get());
-  st_r(a.uh + 1 * W * hs + ci, hs, pi.get());
-  st_r(a.uh + 2 * W * hs + ci, hs, qr.get());
-  st_r(a.uh + 3 * W * hs + ci, hs, qi.get());
+  st_r(a.uh + 0 * W * us + cu, us, pr.get());
+  st_r(a.uh + 1 * W * us + cu, us, pi.get());
+  st_r(a.uh + 2 * W * us + cu, us, qr.get());
+  st_r(a.uh + 3 * W * us + cu, us, qi.get());
 }
 
 template <int W>
@@ -779,10 +787,11 @@ __device__ __forceinline__ void full_row_prep(const StepArgs& a, int i, int tx, 
   using R = typename RT<W>::T;
   const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
   const int gstride = n_th + 2 * rad;
-  const size_t hs = (size_t)(n_r - 1) * pitch;
+  (void)n_r;
+  const size_t hs = uh_plane(a);
   const double* uh = a.uh;
   for (int j = tx; j < n_th; j += TX) {
-    const size_t p = (size_t)i * pitch + j, m = p - pitch;  // half rows i+1/2 and i-1/2
+    const size_t p = (size_t)(i - a.uh_row0) * pitch + j, m = p - pitch;  // half rows i+1/2 and i-1/2
     const R sPR = v_add(ld_s<R>(uh + 0 * W * hs + p, hs), ld_s<R>(uh + 0 * W * hs + m, hs));
     const R sPI = v_add(ld_s<R>(uh + 1 * W * hs + p, hs), ld_s<R>(uh + 1 * W * hs + m, hs));
     put_ghosted<R>(sR, gstride, n_th, rad, a.g.parity, j, sPR);
@@ -805,10 +814,10 @@ __device__ __forceinline__ bool full_point(const StepArgs& a, int i, int j, cons
   using R = typename RT<W>::T;
   const int n_r = a.g.n_r, n_th = a.g.n_th, pitch = a.g.pitch, rad = a.radius;
   const size_t ws = (size_t)n_r * pitch;
-  const size_t hs = (size_t)(n_r - 1) * pitch;
+  const size_t hs = uh_plane(a);
   const double* uh = a.uh;
   const R h2 = from_words<R>(a.h2);
-  const size_t p = (size_t)i * pitch + j, m = p - pitch;
+  const size_t p = (size_t)(i - a.uh_row0) * pitch + j, m = p - pitch;
   const R hPR1 = ld_s<R>(uh + 0 * W * hs + p, hs), hPR0 = ld_s<R>(uh + 0 * W * hs + m, hs);
   const R hPI1 = ld_s<R>(uh + 1 * W * hs + p, hs), hPI0 = ld_s<R>(uh + 1 * W * hs + m, hs);
   const R hQR1 = ld_s<R>(uh + 2 * W * hs + p, hs), hQR0 = ld_s<R>(uh + 2 * W * hs + m, hs);
@@ -969,6 +978,45 @@ __global__ void __launch_bounds__(RowBounds<V>::threads, RowBounds<V>::blocks) f
   long long slot = -1;
   if (a.record) slot = a.ring_slot >= 0 ? a.ring_slot : (*a.ring_counter) % a.ring_cap;
   if (full_row_out<W>(a, i, threadIdx.x, blockDim.x, sR, sI, slot)) atomicOr(a.status, 1u);
+}
+
+// ---- fused iteration for small problems: one launch per Lax-Wendroff iteration -------------
+// Block b produces the full-step rows i0 .. i1 (i0 = 1 + b R, R = blockDim.y - 1) into u_out,
+// which must be another buffer than u_in: the blocks next to it read the rows beside its own
+// from u_in. It first forms the R + 1 half rows i0 - 1 .. i1 that these rows need (the first
+// one is also formed by the block below; both get the same bits) in its own shared memory,
+// then the full-step rows, with the row bodies of the two-kernel form: the results are the
+// same bits as theirs. One launch per iteration halves the launches of small grids, whose
+// iterations are shorter than the launch cost.
+template <int W>
+__global__ void __launch_bounds__(256, 1) fused_kernel(StepArgs a) {
+  step_dependency();
+  extern __shared__ double sm[];
+  const int R = blockDim.y - 1, n_r = a.g.n_r, pitch = a.g.pitch;
+  const int gstride = a.g.n_th + 2 * a.radius;
+  const int i0 = 1 + blockIdx.x * R;
+  const int i1 = min(i0 + R - 1, n_r - 2);
+  StepArgs b = a;
+  b.uh = sm;  // [4][W][R + 1][pitch]
+  b.uh_ws = (size_t)(R + 1) * pitch;
+  b.uh_row0 = i0 - 1;
+  const int y = threadIdx.y;
+  double* sR = sm + (size_t)4 * W * (R + 1) * pitch + (size_t)y * 2 * W * gstride;
+  double* sI = sR + (size_t)W * gstride;
+  const int h = i0 - 1 + y;
+  const bool hok = h <= i1;
+  if (hok) half_row_prep<W>(b, h, threadIdx.x, blockDim.x, sR, sI);
+  __syncthreads();
+  if (hok) half_row_out<W>(b, h, threadIdx.x, blockDim.x, sR, sI);
+  __syncthreads();
+  const int i = i0 + y;
+  const bool fok = y < R && i <= i1;
+  if (fok) full_row_prep<W>(b, i, threadIdx.x, blockDim.x, sR, sI);
+  __syncthreads();
+  if (!fok) return;
+  long long slot = -1;
+  if (a.record) slot = a.ring_slot >= 0 ? a.ring_slot : (*a.ring_counter) % a.ring_cap;
+  if (full_row_out<W>(b, i, threadIdx.x, blockDim.x, sR, sI, slot)) atomicOr(a.status, 1u);
 }
 
 // ---- balanced kernels: the same number of points for every block ----------------------------

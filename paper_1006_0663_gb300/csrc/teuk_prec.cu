@@ -535,6 +535,32 @@ int launch_pair(teuk_s* h, const StepArgs& sa, dim3 blk, size_t smem) {
   }
 }
 
+// One iteration in one launch (kernel family 4): from the buffer that holds the state into the
+// other one (h->u2 is allocated with zero boundary rows, which no launch writes); the caller
+// copies the state back into h->u when a sequence of iterations ends in h->u2.
+int fused_impl(teuk_s* h, StepArgs sa) {
+  if (!h->u2) {
+    h->last_error = "fused iterations need the second state buffer (teuk_set_launch_shape variant 10)";
+    return TEUK_ERR_INVALID_ARG;
+  }
+  sa.u_in = h->in_u2 ? h->u2 : h->u;
+  sa.u_out = h->in_u2 ? h->u : h->u2;
+  int tx, R;
+  fused_shape(h, tx, R);
+  const size_t smem = fused_smem(h, R);
+  if (smem > 48 * 1024)
+    TEUK_CUDA(h, cudaFuncSetAttribute(fused_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int G = (h->n_r - 2 + R - 1) / R;
+  cudaEvent_t ev = nullptr;
+  time_begin(h, &ev);
+  TEUK_CUDA(h, launch_dep(fused_kernel<W>, dim3(G), dim3(tx, R + 1), smem, h->stream, sa));
+  time_end(h, 1, ev);
+  TEUK_CUDA(h, cudaGetLastError());
+  h->in_u2 = !h->in_u2;
+  h->launches += 1;
+  return TEUK_OK;
+}
+
 int substep_impl(teuk_s* h, bool record, int64_t slot) {
   StepArgs sa{};
   sa.g = Geom{h->n_r, h->n_th, h->pitch, h->parity};
@@ -554,6 +580,7 @@ int substep_impl(teuk_s* h, bool record, int64_t slot) {
   sa.ring_cap = h->ring_cap;
   sa.ring = h->ring;
   sa.status = h->status;
+  if (h->kernel_family == 4 && h->engine == 0) return fused_impl(h, sa);
   dim3 blk;
   step_shape(h, blk);
   const size_t smem = (size_t)blk.y * 2 * W * (h->n_th + 2 * h->radius) * sizeof(double);

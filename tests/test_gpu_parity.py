@@ -254,7 +254,7 @@ def test_autotuner_keeps_state_and_results(W):
         g.set_initial_pulse(10.0, 4.0, 0.8, 0.6, 2)
     before = g2.get_state()
     rows = g2.tune()
-    assert rows in (0, 1, 2, 4, 8)  # 0: the one-warp-per-32-columns kernels won
+    assert rows in (0, 1, 2, 3, 4, 7, 8)  # 0: the one-warp-per-32-columns kernels won
     np.testing.assert_array_equal(g2.get_state(), before)
     g1.step(2)
     g2.step(2)
@@ -262,6 +262,8 @@ def test_autotuner_keeps_state_and_results(W):
     shape = g2.launch_shape()
     if shape["variant"] == 9:  # persistent launches won: one per 1 or 8 outer steps
         assert g2.kernel_launches in (1, 2)
+    elif shape["variant"] == 10:  # fused iterations: one launch each
+        assert g2.kernel_launches == 2 * p["substeps"]
     else:
         assert g2.kernel_launches == 2 * 2 * p["substeps"]
 
@@ -1147,3 +1149,58 @@ def test_c3_bounded_over_its_stated_length():
         peaks.append(float(np.abs(g.get_state()).max()))
     assert all(np.isfinite(peaks))
     assert max(peaks[6:]) < max(peaks[:2]), peaks
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+@pytest.mark.parametrize("k,R", [(3, 1), (4, 3), (3, 7)])
+def test_fused_iterations_bitwise(W, k, R):
+    """Kernel family 4 (one launch per iteration, half rows recomputed per block, the state
+    alternating between two buffers) gives the bits of the two-kernel form: odd and even
+    iteration counts per outer step (the odd ones end with a copy back), with the observer
+    ring, the r* dissipation and the theta filter, through graphs and direct launches."""
+    p = small(s=-1, m=2, n_r=45, n_theta=24, substeps=k)
+    runs = []
+    for fused in (False, True):
+        for graphs in (True, False):
+            g = teuk.Teuk(precision=W, **p)
+            g.set_dissipation(1.0)
+            g.set_theta_filter(6, 2)
+            if fused:
+                g.set_launch_shape(32, R, 10)
+                assert g.launch_shape() == {"threads_theta": 32, "rows_per_block": R, "variant": 10}
+            g.use_graphs(graphs)
+            g.set_observer(5.0, 16)
+            g.set_initial_pulse(5.0, 3.0, 0.8, 0.55, 2)
+            g.step(3)
+            g.substep(2)
+            g.step(2)
+            g.sync()
+            runs.append((g.get_state(), g.read_waveform()))
+    for st, wf in runs[1:]:
+        np.testing.assert_array_equal(st, runs[0][0])
+        np.testing.assert_array_equal(wf, runs[0][1])
+
+
+def test_fused_iterations_rules():
+    """Variant 10 is refused on the integer engine, on slabs and for blocks over 256 threads;
+    the tuner may choose it for small grids, with the same bits as the default shape."""
+    p = small(s=-2, m=2, n_r=41, n_theta=24, substeps=4)
+    g = teuk.Teuk(precision=2, **p)
+    g.set_engine(1)
+    with pytest.raises(teuk.TeukError):
+        g.set_launch_shape(32, 1, 10)
+    s = teuk.Teuk(precision=1, own_rows=(0, 20), **p)
+    with pytest.raises(teuk.TeukError):
+        s.set_launch_shape(32, 1, 10)
+    f = teuk.Teuk(precision=1, **p)
+    with pytest.raises(teuk.TeukError):
+        f.set_launch_shape(128, 3, 10)  # 128 x 4 threads
+    prob = workloads.CONFIGS["c1"]
+    a = teuk.Teuk.from_problem(prob, precision=1)
+    a.tune()
+    b = teuk.Teuk.from_problem(prob, precision=1)
+    ar, ai = prob.amps
+    for h in (a, b):
+        h.set_initial_pulse(prob.center, prob.width, ar, ai, prob.ell)
+        h.step(5)
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
