@@ -325,11 +325,13 @@ def run_e2e(prob, words, steps, torch, teuk, flush, engine=0):
     g.observe(prob.rstar_obs)
     torch.cuda.synchronize()
     total = 0.0
-    for _ in range(steps):
+    for t in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g.set_state(host)
+        # the iteration count continues as in one run (outer-step operators with a period,
+        # such as c3's theta filter, then run where they would in the device-timed loop)
+        g.set_state(host, substeps_done=(t + 1) * prob.substeps)
         g.step(1)
         obs, _ = g.observe(prob.rstar_obs)
         total += time.perf_counter() - t0
