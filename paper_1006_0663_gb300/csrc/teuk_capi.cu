@@ -90,10 +90,11 @@ int iterate(teuk_s* h, bool record, int64_t slot) {
   return TEUK_OK;
 }
 
-// The theta filter's outer-step count restarts from the state's iteration count.
+// The theta filter's outer-step count restarts from the state's iteration count: the index of
+// the next outer step to begin (the current one's when the count is a multiple of k).
 int sync_filter_counter(teuk_s* h) {
   if (!h->d_filter_ctr) return TEUK_OK;
-  const long long v[2] = {(long long)(h->substeps_done / h->k), 0};
+  const long long v[2] = {(long long)((h->substeps_done + h->k - 1) / h->k), 0};
   TEUK_CUDA(h, cudaMemcpyAsync(h->d_filter_ctr, v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
   TEUK_CUDA(h, cudaStreamSynchronize(h->stream));
   return TEUK_OK;

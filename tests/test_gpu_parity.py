@@ -1077,6 +1077,15 @@ def test_theta_filter_rules(W):
     e.step(1)  # outer step 2 projects
     f.step(1)
     assert np.abs(e.get_state() - f.get_state()).max() > 0
+    # resumed in the middle of an outer step, the count goes on as in the uninterrupted run
+    whole = teuk.Teuk(precision=W, theta_filter=6, theta_filter_period=2, **p)
+    part = teuk.Teuk(precision=W, theta_filter=6, theta_filter_period=2, **p)
+    whole.set_state(u0)
+    whole.substep(p["substeps"] + 1)
+    part.set_state(whole.get_state(), substeps_done=p["substeps"] + 1)
+    for h in (whole, part):
+        h.substep(3 * p["substeps"])
+    np.testing.assert_array_equal(whole.get_state(), part.get_state())
     with pytest.raises(teuk.TeukError):
         teuk.Teuk(precision=W, theta_filter=2, **p)
     with pytest.raises(teuk.TeukError):
