@@ -993,12 +993,34 @@ int teuk_tune(teuk_t h, int* rows_per_block) {
     return settle_state(h);
   };
   // Small problems run as replayed graphs, where launch costs differ from direct launches: the
-  // four fastest shapes above are timed again as teuk_step runs them, over four outer steps,
-  // when an outer step is short.
-  if (rc == TEUK_OK && graphs_possible(h) && best_ms / 4 * h->k < 5.0f) {
+  // four fastest shapes of the two-kernel families above and the two fastest fused ones are
+  // timed again as teuk_step runs them, over four outer steps, when an outer step is short
+  // (timed by direct launches, the fused shapes' single launch per iteration ranks them above
+  // two-kernel shapes that replay faster).
+  const bool rerank = rc == TEUK_OK && graphs_possible(h) && best_ms / 4 * h->k < 5.0f;
+  if (rc == TEUK_OK && graphs_possible(h) && !rerank && best_f == 4) {
+    // not re-timed as graphs: keep the fastest two-kernel shape rather than a fused one ranked
+    // first by its launch count
+    float two_ms = 1e30f;
+    for (const Cand& c : cands)
+      if (c.f != 4 && c.ms < two_ms) {
+        two_ms = c.ms;
+        best_f = c.f;
+        best_v = c.v;
+        best_tx = c.tx;
+        best = c.ty;
+      }
+  }
+  if (rerank) {
     std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+    std::vector<Cand> pick;
+    int n_two = 0, n_fused = 0;
+    for (const Cand& c : cands) {
+      if (c.f == 4 ? n_fused++ < 2 : n_two++ < 4) pick.push_back(c);
+    }
+    cands.swap(pick);
     float graph_best = 1e30f;
-    for (size_t c = 0; c < cands.size() && c < 4 && rc == TEUK_OK; ++c) {
+    for (size_t c = 0; c < cands.size() && rc == TEUK_OK; ++c) {
       h->kernel_family = cands[c].f;
       h->kernel_variant = cands[c].v;
       h->threads_theta = cands[c].tx;
